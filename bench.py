@@ -1,0 +1,356 @@
+#!/usr/bin/env python
+"""Benchmark of the Proportional Similarity hot path on one GB300 per rank.
+
+Default workload: 2-way metrics over all pairs of nv=32768 vectors of nf=8192
+FP32 fields (seeded zero-inflated -log10 p-value stand-ins), packed FP32
+upper-triangular output.  A step is one full pass of the path: FP64 vector
+sums + the FP32 min-product kernel with the fused ratio epilogue.
+
+Metric: elementwise comparisons per second (one comparison = one min plus one
+add per element pair, the paper's count).  Prints ONE JSON line on rank 0.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+Multi-GPU (torchrun): every rank computes its own instance of the workload
+(seed + rank), no collective on the data path; value = all ranks'
+comparisons / max-over-ranks time ("scaling": "weak").
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "elementwise comparisons/sec (2-way, 3-way) at 1 GB300; % of min+add peak; INT8-TC vs FP32"
+UNIT = "comparisons/s"
+WORKLOADS = {
+    "2way_32768x8192_f32": dict(way=2, nv=32768, nf=8192, number=2),
+    "3way_2048x4096_f32": dict(way=3, nv=2048, nf=4096, number=3),
+    "2way_1024x512_f64": dict(way=2, nv=1024, nf=512, number=1),
+}
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+
+
+def comparisons(w):
+    nv, nf = w["nv"], w["nf"]
+    if w["way"] == 2:
+        return nf * nv * (nv - 1) // 2
+    return nf * nv * (nv - 1) * (nv - 2) // 6
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.path = os.path.join("/tmp", f"ps_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(V_fm: np.ndarray, w, n_sample: int):
+    """The plain FP64 oracle on the first n_sample vectors, all host cores."""
+    import oracle
+    nf = V_fm.shape[0]
+    sub = np.ascontiguousarray(V_fm[:, :n_sample].T).astype(np.float64)
+    t0 = time.perf_counter()
+    if w["way"] == 2:
+        oracle.c2_packed(sub)
+        cmp = nf * n_sample * (n_sample - 1) // 2
+        what = f"c2 over all pairs of the first {n_sample} vectors ({cmp:.3e} comparisons)"
+    else:
+        oracle.c3_slab(sub, 0, n_sample)
+        cmp = nf * n_sample * (n_sample - 1) * (n_sample - 2) // 6
+        what = f"c3 over all triples of the first {n_sample} vectors ({cmp:.3e} comparisons)"
+    dt = time.perf_counter() - t0
+    return {"value": cmp / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": what, "seconds": round(dt, 3)}
+
+
+def run_reference(args, w, ws, rank):
+    """--impl reference: the FP64 CPU oracle, timed as it stands."""
+    if rank != 0:
+        return
+    from paper_1705_08210_gb300 import synth
+    n_sample = 2048 if w["way"] == 2 else 128
+    V = synth.zero_inflated(n_sample, w["nf"], synth.seed_for(w["number"]))
+    times = []
+    cb = None
+    for s in range(args.warmup + args.steps):
+        cb = cpu_baseline(V, w, n_sample)
+        if s >= args.warmup:
+            times.append(cb["seconds"])
+    cmp = cb["value"] * cb["seconds"]
+    ms = 1e3 * statistics.mean(times)
+    value = cmp / (ms / 1e3)
+    cb["value"] = value
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "nv": w["nv"], "nf": w["nf"],
+                       "sample_vectors": n_sample, "l2": "CPU run"},
+            "cpu_baseline": cb,
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="2way_32768x8192_f32", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-secondary", action="store_true")
+    args = ap.parse_args()
+    w = WORKLOADS[args.workload]
+    ws, rank, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, w, ws, rank)
+        return
+
+    import torch
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_1705_08210_gb300 import ps, synth
+
+    h = ps.Handle(local)
+    nv, nf = w["nv"], w["nf"]
+    dtype = np.float64 if args.workload.endswith("f64") else np.float32
+    V = synth.zero_inflated(nv, nf, synth.seed_for(w["number"], rank), dtype=dtype)
+    X = torch.from_numpy(V).cuda()
+    m = ps.matrix(X)
+    stream = torch.cuda.current_stream()
+    sptr = stream.cuda_stream
+    if w["way"] == 2:
+        out_dtype = 1 if dtype == np.float64 else 0
+        out = torch.empty(nv * (nv - 1) // 2, dtype=torch.float64 if out_dtype else torch.float32, device="cuda")
+        main_kernel = "mgemm2"
+        launches_per_step = 2
+
+        def step():
+            ps.check(ps.ps_metrics_2way(h.h, ctypes.byref(m), ps.PS_PATH_FP32, 0, out.data_ptr(), out_dtype, sptr), h.h)
+    else:
+        out = torch.empty(ps.ps_slab_size(nv, 0, nv), dtype=torch.float32, device="cuda")
+        main_kernel = "mgemm3"
+        launches_per_step = 4  # sums, n2 table, pivot prefix, 3-way
+
+        def step():
+            ps.check(ps.ps_metrics_3way(h.h, ctypes.byref(m), 0, nv, out.data_ptr(), sptr), h.h)
+
+    out_bytes = out.numel() * out.element_size()
+    cmp_per_step = comparisons(w)
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    # ---- device-timed region ----
+    ps.check(ps.ps_timing_enable(h.h, 1), h.h)
+    clocks = ClockSampler(local)
+    clocks.start()
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    ms_total = e0.elapsed_time(e1)
+    n_launch = ctypes.c_int64()
+    k_ms = ctypes.c_double()
+    ps.check(ps.ps_timing_read(h.h, main_kernel.encode(), ctypes.byref(n_launch), ctypes.byref(k_ms)), h.h)
+    ps.check(ps.ps_timing_enable(h.h, 0), h.h)
+    if ws > 1:
+        t = torch.tensor([ms_total], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_total = float(t.item())
+    ms_step = ms_total / args.steps
+    value = ws * cmp_per_step / (ms_step / 1e3)
+
+    # ---- roofline of the dominant kernel ----
+    k_avg_ms = k_ms.value / max(n_launch.value, 1)
+    achieved = cmp_per_step / (k_avg_ms / 1e3)
+    peaks = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else {}
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    props = torch.cuda.get_device_properties(local)
+    n_sm = props.multi_processor_count
+    # CUDA-core issue bound of the inner loop: per SM and clock 4 schedulers
+    # x 32 lanes issue one warp instruction each; a comparison pair takes two
+    # FMNMX and one packed f32x2 FADD = 1.5 issue slots per comparison.
+    peak_cmp = n_sm * 128 / 1.5 * sm_max * 1e6
+    probe = ctypes.c_double()
+    ps.check(ps.ps_probe_minadd_peak(h.h, 1, ctypes.byref(probe)), h.h)
+    probe0 = ctypes.c_double()
+    ps.check(ps.ps_probe_minadd_peak(h.h, 0, ctypes.byref(probe0)), h.h)
+    roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_cmp / 1e12, "unit": "Tcmp/s",
+                "frac": achieved / peak_cmp, "traffic": None,
+                "kernel": main_kernel, "kernel_ms": k_avg_ms,
+                "peak_basis": f"{n_sm} SMs x 128 lanes / 1.5 issue slots per comparison x {sm_max:.0f} MHz (max clock)",
+                "probe_minadd_f32x2": probe.value / 1e12, "probe_minadd_scalar": probe0.value / 1e12}
+
+    # ---- end to end through the C ABI with host buffers ----
+    e2e = None
+    if not args.no_e2e:
+        Vh = torch.from_numpy(V).pin_memory()
+        outh = torch.empty(out.numel(), dtype=out.dtype).pin_memory()
+        mh = ps.matrix(Vh)
+        if w["way"] == 2:
+            def hstep():
+                ps.check(ps.ps_metrics_2way(h.h, ctypes.byref(mh), ps.PS_PATH_FP32, 0, outh.data_ptr(),
+                                            out_dtype, sptr), h.h)
+        else:
+            def hstep():
+                ps.check(ps.ps_metrics_3way(h.h, ctypes.byref(mh), 0, nv, outh.data_ptr(), sptr), h.h)
+        hstep()
+        if ws > 1:
+            torch.distributed.barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            hstep()
+        dt = (time.perf_counter() - t0) / args.steps
+        if ws > 1:
+            t = torch.tensor([dt], device="cuda", dtype=torch.float64)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            dt = float(t.item())
+        e2e = {"value": ws * cmp_per_step / dt, "unit": UNIT, "ms_per_step": dt * 1e3,
+               "h2d_bytes_per_step": int(Vh.numel() * Vh.element_size()),
+               "d2h_bytes_per_step": int(outh.numel() * outh.element_size())}
+        del Vh, outh
+
+    # ---- sampled parity of the timed output ----
+    import oracle
+    torch.cuda.synchronize()
+    if w["way"] == 2:
+        pairs = synth.sample_pairs(nv, 2000, seed=11)
+        idx = torch.from_numpy(oracle.pair_index(nv, pairs[:, 0], pairs[:, 1])).cuda()
+        got = out[idx].double().cpu().numpy()
+        ref = oracle.c2_pairs(oracle.to_vector_major(V), pairs)
+    else:
+        t3 = synth.sample_triples(nv, 2000, seed=11)
+        F = lambda x: (nv - 1) * (x * (x - 1) // 2) - (x - 1) * x * (2 * x - 1) // 6  # noqa: E731
+        pos = F(t3[:, 1]) + t3[:, 0] * (nv - 1 - t3[:, 1]) + (t3[:, 2] - t3[:, 1] - 1)
+        got = out[torch.from_numpy(pos).cuda()].double().cpu().numpy()
+        ref = oracle.c3_triples(oracle.to_vector_major(V), t3)
+    nz = ref != 0
+    max_rel = float(np.max(np.abs(got[nz] - ref[nz]) / ref[nz])) if nz.any() else 0.0
+
+    # ---- secondary: the 3-way workload ----
+    secondary = None
+    if not args.no_secondary and w["way"] == 2 and ws == 1:
+        del out
+        torch.cuda.empty_cache()
+        w3 = WORKLOADS["3way_2048x4096_f32"]
+        V3 = synth.zero_inflated(w3["nv"], w3["nf"], synth.seed_for(3))
+        X3 = torch.from_numpy(V3).cuda()
+        m3 = ps.matrix(X3)
+        o3 = torch.empty(ps.ps_slab_size(w3["nv"], 0, w3["nv"]), dtype=torch.float32, device="cuda")
+        for _ in range(2):
+            ps.check(ps.ps_metrics_3way(h.h, ctypes.byref(m3), 0, w3["nv"], o3.data_ptr(), sptr), h.h)
+        ps.check(ps.ps_timing_enable(h.h, 1), h.h)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(3):
+            ps.check(ps.ps_metrics_3way(h.h, ctypes.byref(m3), 0, w3["nv"], o3.data_ptr(), sptr), h.h)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms3 = e0.elapsed_time(e1) / 3
+        ps.check(ps.ps_timing_read(h.h, b"mgemm3", ctypes.byref(n_launch), ctypes.byref(k_ms)), h.h)
+        ps.check(ps.ps_timing_enable(h.h, 0), h.h)
+        k3 = k_ms.value / max(n_launch.value, 1)
+        c3 = comparisons(w3)
+        secondary = {"3way_2048x4096_f32": {"value": c3 / (ms3 / 1e3), "unit": UNIT, "ms_per_step": ms3,
+                                            "mgemm3_ms": k3, "frac_of_peak": c3 / (k3 / 1e3) / peak_cmp}}
+        del o3, X3
+
+    cb = None
+    if rank == 0 and not args.no_cpu_baseline and ws == 1:
+        cb = cpu_baseline(V, w, 8192 if w["way"] == 2 else 256)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32" if dtype == np.float32 else "f64", "data": "synthetic",
+                "config": {"workload": args.workload, "nv": nv, "nf": nf, "way": w["way"],
+                           "comparisons_per_step": cmp_per_step, "path": "fp32 CUDA-core min+add",
+                           "l2": f"inputs larger than L2 ({V.nbytes / 1e9:.2f} GB in, "
+                                 f"{out_bytes / 1e9:.2f} GB out)",
+                           "parallelism": f"independent instance per rank x{ws}"},
+                "roofline": roofline, "cpu_baseline": cb, "e2e": e2e, "clocks": clk,
+                "gpu_launches": launches_per_step * args.steps,
+                "sampled_max_rel_err": max_rel, "secondary": secondary}
+        print(json.dumps(line), flush=True)
+    h.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

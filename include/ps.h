@@ -1,0 +1,241 @@
+/*
+ * ps.h -- C ABI of the GB300 (sm_103a) Proportional Similarity library.
+ *
+ * Computes the 2-way and 3-way Proportional Similarity (Czekanowski)
+ * metrics of Joubert, Nance, Weighill and Jacobson, "Parallel Accelerated
+ * Vector Similarity Calculations for Genomics Applications" (arXiv
+ * 1705.08210):
+ *
+ *   Section 2.1:  c2(u,v) = 2 n2(u,v) / d2(u,v),
+ *                 n2 = sum_q min(u_q, v_q),  d2 = sum_q u_q + sum_q v_q
+ *   Section 2.2:  c3(u,v,w) = (3/2) n3(u,v,w) / d3(u,v,w),   eq. (1):
+ *                 n3 = n2(u,v) + n2(u,w) + n2(v,w) - n3'(u,v,w),
+ *                 n3' = sum_q min(u_q, v_q, w_q),  d3 = sum_q (u_q+v_q+w_q)
+ *
+ * The numerators are computed as a "min-product" matrix product
+ * M = V^T (min) V (Section 3.1); the 3-way term as B_j = X_j^T (min) V with
+ * X_j = min(V, v_j) (Section 3.2).  Only non-redundant blocks are computed:
+ * the upper triangle for pairs, the i<j<k tetrahedron for triples.
+ *
+ * ---------------------------------------------------------------------------
+ * Conventions shared by every entry point
+ *
+ * Matrix V.  nv vectors of nf fields each, values finite and >= 0 (the paper
+ *   assumes v_{i,q} >= 0, Section 2.1; negative or NaN input is undefined).
+ *   layout PS_LAYOUT_FIELD_MAJOR  : element (i,q) at data[i + q*ld], ld >= nv
+ *                                   ("column-major nv x nf"; default)
+ *   layout PS_LAYOUT_VECTOR_MAJOR : element (i,q) at data[q + i*ld], ld >= nf
+ *                                   (the paper's column-major n_f x n_v file)
+ *   dtype PS_F32 or PS_F64.  FP64 input is rounded to FP32 for the numerator
+ *   products of the FP32 paths; the denominators always use the original
+ *   values summed in FP64.
+ *
+ * Pointers.  Every data pointer may be DEVICE memory (cudaMalloc, torch CUDA
+ *   tensors, managed memory) or HOST memory (pinned or pageable).  The kind
+ *   is detected with cudaPointerGetAttributes.  Host buffers are staged
+ *   through library-owned device memory inside the call, and a call that
+ *   touches any host buffer synchronises `stream` before returning.  A call
+ *   on device buffers only is asynchronous on `stream`.  The caller owns all
+ *   buffers it passes; the library owns only its workspace (grown on demand,
+ *   freed by ps_destroy).
+ *
+ * Errors.  Every entry point returns a ps_status.  Argument errors are
+ *   detected before any launch and leave outputs untouched.  CUDA errors are
+ *   reported as PS_ERR_CUDA; ps_last_error() gives the message.  No
+ *   exception, abort or exit crosses this boundary.
+ *
+ * Threads.  A handle may be used by one host thread at a time.  Calls that
+ *   overlap on the GPU (different streams, same handle) race on the handle's
+ *   workspace: serialise them or use one handle per stream.
+ *
+ * Readings where the paper is silent:
+ *   - a pair/triple whose denominator is 0 (all-zero vectors) gets metric 0;
+ *   - FP32 outputs are round-to-nearest of the ratio; on integer-valued input
+ *     whose sums stay below 2^24 every FP32 output equals the FP32 rounding
+ *     of the exact FP64 ratio (2*n2)/(S_i+S_j) or (1.5*n3)/((S_i+S_j)+S_k).
+ */
+#ifndef PS_H
+#define PS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* A cudaStream_t (struct CUstream_st*).  NULL means the legacy default
+ * stream. */
+struct CUstream_st;
+typedef struct CUstream_st* ps_stream;
+
+typedef struct ps_ctx* ps_handle;
+
+typedef enum {
+  PS_OK = 0,
+  PS_ERR_INVALID_ARG = 1,
+  PS_ERR_OOM = 2,
+  PS_ERR_CUDA = 3,
+  PS_ERR_CAPACITY = 4,
+  PS_ERR_TIMEOUT = 5,
+  PS_ERR_UNSUPPORTED = 6
+} ps_status;
+
+typedef enum { PS_F32 = 0, PS_F64 = 1 } ps_dtype;
+
+typedef enum {
+  /* FP32 min + FP32 add on the CUDA cores, chunked and compensated
+   * accumulation (relative error <= ~4e-6). */
+  PS_PATH_FP32 = 0,
+  /* FP64 min + FP64 add on the CUDA cores (small problems). */
+  PS_PATH_FP64 = 1,
+  /* Quantize to `levels` levels, thermometer-encode, and run the numerator
+   * product on the tensor cores (exact on the quantized data). */
+  PS_PATH_THERMO = 2
+} ps_path;
+
+typedef enum { PS_LAYOUT_FIELD_MAJOR = 0, PS_LAYOUT_VECTOR_MAJOR = 1 } ps_layout;
+
+/* Field matrix descriptor (see "Matrix V" above). */
+typedef struct {
+  const void* data;
+  int64_t nv;     /* number of vectors   (n_v in the paper) */
+  int64_t nf;     /* fields per vector   (n_f in the paper) */
+  int64_t ld;     /* leading dimension in elements */
+  int32_t dtype;  /* ps_dtype */
+  int32_t layout; /* ps_layout */
+} ps_matrix;
+
+/* One thresholded 3-way result: indices i<j<k and c3 (FP32). */
+typedef struct {
+  int32_t i, j, k;
+  float value;
+} ps_triple;
+
+/* ---------------------------------------------------------------------------
+ * Handle.  ps_create binds a handle to CUDA device `device` (the device is
+ * made current inside each call).  Returns PS_ERR_INVALID_ARG for a null
+ * `out` or an invalid device, PS_ERR_CUDA if the device cannot be used. */
+ps_status ps_create(ps_handle* out, int device);
+/* Frees the handle and its workspace (synchronises the device first).
+ * NULL is accepted. */
+ps_status ps_destroy(ps_handle h);
+
+/* Static string for a status code (never NULL). */
+const char* ps_status_string(ps_status s);
+/* Message of the last failing call on `h` ("" if none); valid until the next
+ * call on `h`.  NULL handle gives the last message of any handle. */
+const char* ps_last_error(ps_handle h);
+/* Library version string. */
+const char* ps_version(void);
+
+/* ---------------------------------------------------------------------------
+ * Per-vector sums S_i = sum_q v_{i,q} in FP64 (Section 2.1: the denominator
+ * d2 = S_i + S_j needs only these O(n_f n_v) adds; Section 2.2: d3 likewise).
+ *   S : nv doubles, device or host.
+ * Errors: PS_ERR_INVALID_ARG for a null/invalid matrix or null S. */
+ps_status ps_vector_sums(ps_handle h, const ps_matrix* V, double* S,
+                         ps_stream stream);
+
+/* ---------------------------------------------------------------------------
+ * All 2-way metrics c2(v_i, v_j), i < j (Section 2.1; the numerators are the
+ * strict upper triangle of M = V^T (min) V, Section 3.1).
+ *   path      : ps_path.
+ *   levels    : PS_PATH_THERMO only, number of quantization levels L in
+ *               [2, 16]; ignored otherwise.
+ *   out       : nv*(nv-1)/2 values of out_dtype (PS_F32 or PS_F64), packed
+ *               strict upper triangle, row-major:
+ *                 out[i*(2*nv-i-1)/2 + (j-i-1)] = c2(v_i, v_j),  i < j.
+ *               For PS_PATH_THERMO the metric is that of the quantized
+ *               levels (the scale cancels in the ratio).
+ * Errors: PS_ERR_INVALID_ARG for nv < 2, nf < 0, a bad ld/layout/dtype/path,
+ *   levels out of range, or null pointers; PS_ERR_OOM if the workspace
+ *   cannot grow. */
+ps_status ps_metrics_2way(ps_handle h, const ps_matrix* V, int32_t path,
+                          int32_t levels, void* out, int32_t out_dtype,
+                          ps_stream stream);
+
+/* Size in elements of the pivot slab [j_begin, j_end) written by
+ * ps_metrics_3way: sum over j of j*(nv-1-j).  Returns -1 on bad arguments. */
+int64_t ps_slab_size(int64_t nv, int64_t j_begin, int64_t j_end);
+
+/* ---------------------------------------------------------------------------
+ * 3-way metrics c3(v_i, v_j, v_k), i < j < k, for the pivots j in
+ * [j_begin, j_end) (Section 2.2 eq. (1); n3' via B_j = X_j^T (min) V with
+ * X_j = min(V, v_j), Section 3.2, computing only i < j < k).
+ *   out_slab : ps_slab_size(nv, j_begin, j_end) floats.  Pivot j owns a
+ *              j x (nv-1-j) row-major block (rows i in [0,j), columns k in
+ *              (j,nv)); blocks follow in increasing j:
+ *                out_slab[off(j) + i*(nv-1-j) + (k-j-1)] = c3(v_i,v_j,v_k),
+ *                off(j) = ps_slab_size(nv, j_begin, j).
+ *              Computing a campaign in slabs is the paper's staging
+ *              (Section 4.2): a run can resume from any pivot.
+ * Only PS_PATH_FP32 arithmetic is used (FP32 min/add, FP64 sums).
+ * Errors: PS_ERR_INVALID_ARG for nv < 3, 0 <= j_begin <= j_end <= nv
+ *   violated, or null pointers. */
+ps_status ps_metrics_3way(ps_handle h, const ps_matrix* V, int64_t j_begin,
+                          int64_t j_end, float* out_slab, ps_stream stream);
+
+/* ---------------------------------------------------------------------------
+ * Thresholded 3-way search: every triple i<j<k with c3 >= tau, sorted
+ * lexicographically by (i,j,k).
+ *   use_proposal : 0 = exhaustive; 1 = only blocks proposed by the learned
+ *                  encoder loaded with ps_proposal_load (see below);
+ *                  2 = only blocks that the exact 2-way bound cannot rule
+ *                  out (lossless).
+ *   out          : `capacity` ps_triple slots (device or host).
+ *   count        : one int64 (device or host) receiving the total number of
+ *                  triples found, also when it exceeds `capacity`.
+ * Returns PS_ERR_CAPACITY when the total exceeds `capacity`; the first
+ * `capacity` triples in sorted order are then written.
+ * Errors: PS_ERR_INVALID_ARG for nv < 3, capacity < 0, null pointers;
+ *   PS_ERR_INVALID_ARG for use_proposal 1 without a loaded encoder. */
+ps_status ps_threshold_3way(ps_handle h, const ps_matrix* V, float tau,
+                            int32_t use_proposal, ps_triple* out,
+                            int64_t capacity, int64_t* count,
+                            ps_stream stream);
+
+/* ---------------------------------------------------------------------------
+ * Quantizer of the thermometer path (not in the paper).
+ *   P      : the nearest-rank 99.9th percentile of the nonzero entries
+ *            (rank ceil(0.999*m) of m nonzeros, ascending, 1-based);
+ *            0 if all entries are zero.
+ *   level  : 0 for a zero entry, else
+ *            min(L-1, floor(fl32(fl32(x * r) + 0.5))),  r = fl32((L-1)/P),
+ *            all in IEEE single precision.
+ *   P_out  : one float (device or host).
+ *   q_out  : nv*nf bytes, field-major with leading dimension nv (device or
+ *            host); may be NULL to compute P only.
+ * Errors: PS_ERR_INVALID_ARG for levels outside [2,16] or null P_out. */
+ps_status ps_quantize(ps_handle h, const ps_matrix* V, int32_t levels,
+                      float* P_out, uint8_t* q_out, ps_stream stream);
+
+/* ---------------------------------------------------------------------------
+ * Kernel timing for benchmarks (no counterpart in the paper, which reads
+ * kernel times from the CUDA profiler, Section 6.2).  While enabled, every
+ * launch of a library kernel is bracketed by two CUDA events recorded on the
+ * stream the kernel is launched on.  ps_timing_enable clears the records
+ * (it waits for recorded events first).
+ * ps_timing_read synchronises on the recorded events of `kernel` and returns
+ * their number and summed duration.  Kernel names: "vector_sums", "pack",
+ * "mgemm2", "mgemm2_f64", "mgemm2_n2", "mgemm3", "quantize", "thermo_encode",
+ * "thermo_gemm", "threshold3", "sort".
+ * Errors: PS_ERR_INVALID_ARG for null arguments. */
+ps_status ps_timing_enable(ps_handle h, int32_t enable);
+ps_status ps_timing_read(ps_handle h, const char* kernel, int64_t* launches,
+                         double* total_ms);
+
+/* ---------------------------------------------------------------------------
+ * Measured CUDA-core issue rate of the paper's inner operation (one min plus
+ * one add per element pair, Section 3.1), from a register-only kernel of
+ * independent min/add chains over the whole GPU.  variant 0: scalar FP32
+ * min + scalar FP32 add; variant 1: FP32 min + packed f32x2 add.
+ *   cmp_per_s : comparisons (min+add pairs) per second.
+ * Synchronises the device.  Errors: PS_ERR_INVALID_ARG for a bad variant. */
+ps_status ps_probe_minadd_peak(ps_handle h, int32_t variant,
+                               double* cmp_per_s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PS_H */

@@ -1,0 +1,464 @@
+// ps_api.cu -- the extern "C" boundary declared in include/ps.h.
+//
+// Argument checking, pointer-kind detection (device vs host), host staging
+// through the handle's workspace, and dispatch to the kernels.
+#include "ps_internal.cuh"
+
+#include <algorithm>
+#include <cstdarg>
+#include <cstring>
+#include <mutex>
+#include <new>
+
+namespace ps {
+
+static std::mutex g_err_mu;
+static std::string g_last_error;
+
+ps_status fail(ps_ctx* h, ps_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  if (h) h->last_error = buf;
+  std::lock_guard<std::mutex> g(g_err_mu);
+  g_last_error = buf;
+  return st;
+}
+
+ps_status cuda_fail(ps_ctx* h, cudaError_t e, const char* where) {
+  cudaGetLastError();  // clear a sticky launch error where possible
+  if (e == cudaErrorMemoryAllocation)
+    return fail(h, PS_ERR_OOM, "%s: %s", where, cudaGetErrorString(e));
+  return fail(h, PS_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+void* ws_get(ps_ctx* h, WsSlot slot, size_t bytes) {
+  Workspace& w = h->ws;
+  if (bytes == 0) bytes = 256;
+  if (w.bytes[slot] >= bytes) return w.ptr[slot];
+  if (w.ptr[slot]) {
+    cudaDeviceSynchronize();  // the old buffer may still be in use by queued work
+    cudaFree(w.ptr[slot]);
+    w.ptr[slot] = nullptr;
+    w.bytes[slot] = 0;
+  }
+  const size_t sz = (size_t)round_up((int64_t)bytes, 256);
+  void* p = nullptr;
+  cudaError_t e = cudaMalloc(&p, sz);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    fail(h, PS_ERR_OOM, "workspace slot %d: cudaMalloc(%zu) failed: %s", (int)slot, sz,
+         cudaGetErrorString(e));
+    return nullptr;
+  }
+  w.ptr[slot] = p;
+  w.bytes[slot] = sz;
+  return p;
+}
+
+ScopedTimer::ScopedTimer(ps_ctx* h_, const char* name, cudaStream_t st_) : h(h_), st(st_) {
+  if (!h || !h->timing) return;
+  TimingRec r{name, nullptr, nullptr};
+  if (cudaEventCreate(&r.a) != cudaSuccess || cudaEventCreate(&r.b) != cudaSuccess) {
+    cudaGetLastError();
+    return;
+  }
+  cudaEventRecord(r.a, st);
+  h->trecs.push_back(r);
+  idx = (int)h->trecs.size() - 1;
+}
+
+ScopedTimer::~ScopedTimer() {
+  if (idx >= 0) cudaEventRecord(h->trecs[idx].b, st);
+}
+
+static void timing_clear(ps_ctx* h) {
+  for (auto& r : h->trecs) {
+    cudaEventSynchronize(r.b);
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  h->trecs.clear();
+}
+
+namespace {
+
+// Memory kind of a caller pointer.
+enum PtrKind { PK_DEVICE, PK_HOST };
+
+ps_status ptr_kind(ps_ctx* h, const void* p, PtrKind* kind) {
+  cudaPointerAttributes a;
+  cudaError_t e = cudaPointerGetAttributes(&a, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *kind = PK_HOST;  // unregistered pageable host memory on older runtimes
+    return PS_OK;
+  }
+  switch (a.type) {
+    case cudaMemoryTypeDevice:
+      if (a.device != h->device)
+        return fail(h, PS_ERR_INVALID_ARG, "device pointer belongs to device %d, handle uses %d",
+                    a.device, h->device);
+      *kind = PK_DEVICE;
+      return PS_OK;
+    case cudaMemoryTypeManaged:
+      *kind = PK_DEVICE;
+      return PS_OK;
+    default:
+      *kind = PK_HOST;
+      return PS_OK;
+  }
+}
+
+size_t dtype_size(int32_t dt) { return dt == PS_F64 ? 8 : 4; }
+
+// Elements spanned by the matrix in its own layout.
+int64_t matrix_span(const ps_matrix& V) {
+  if (V.nv == 0 || V.nf == 0) return 0;
+  if (V.layout == PS_LAYOUT_FIELD_MAJOR) return (V.nf - 1) * V.ld + V.nv;
+  return (V.nv - 1) * V.ld + V.nf;
+}
+
+ps_status check_matrix(ps_ctx* h, const ps_matrix* V, int64_t min_nv) {
+  if (!V) return fail(h, PS_ERR_INVALID_ARG, "null matrix descriptor");
+  if (V->dtype != PS_F32 && V->dtype != PS_F64)
+    return fail(h, PS_ERR_INVALID_ARG, "dtype %d is not PS_F32/PS_F64", V->dtype);
+  if (V->layout != PS_LAYOUT_FIELD_MAJOR && V->layout != PS_LAYOUT_VECTOR_MAJOR)
+    return fail(h, PS_ERR_INVALID_ARG, "layout %d is not a ps_layout", V->layout);
+  if (V->nv < min_nv) return fail(h, PS_ERR_INVALID_ARG, "nv=%lld < %lld", (long long)V->nv, (long long)min_nv);
+  if (V->nf < 0) return fail(h, PS_ERR_INVALID_ARG, "nf=%lld < 0", (long long)V->nf);
+  if (V->nv > (int64_t)1 << 30 || V->nf > (int64_t)1 << 30)
+    return fail(h, PS_ERR_INVALID_ARG, "nv or nf exceeds 2^30");
+  const int64_t need = V->layout == PS_LAYOUT_FIELD_MAJOR ? V->nv : V->nf;
+  if (V->ld < need || V->ld < 1)
+    return fail(h, PS_ERR_INVALID_ARG, "ld=%lld smaller than the contiguous extent %lld",
+                (long long)V->ld, (long long)need);
+  if (V->nv > 0 && V->nf > 0 && !V->data) return fail(h, PS_ERR_INVALID_ARG, "null data pointer");
+  return PS_OK;
+}
+
+struct Guard {  // makes the handle's device current for the call
+  int prev = -1;
+  explicit Guard(int dev) {
+    cudaGetDevice(&prev);
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~Guard() {
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+// Resolve V to a device-resident descriptor (copying host data into the
+// workspace) and build the FP32 field-major view the kernels read.
+struct Prepared {
+  ps_matrix dev;   // device-resident version of the caller matrix
+  VF32 f32;        // FP32 field-major view (may alias dev)
+  double* S = nullptr;
+  bool host_input = false;
+};
+
+ps_status prepare(ps_ctx* h, const ps_matrix& V, cudaStream_t st, bool need_f32, Prepared* P) {
+  P->dev = V;
+  PtrKind k = PK_DEVICE;
+  if (V.nv > 0 && V.nf > 0) {
+    ps_status s = ptr_kind(h, V.data, &k);
+    if (s != PS_OK) return s;
+  }
+  if (k == PK_HOST) {
+    const size_t bytes = (size_t)matrix_span(V) * dtype_size(V.dtype);
+    void* d = ws_get(h, WS_INPUT, bytes);
+    if (!d) return PS_ERR_OOM;
+    if (bytes) PS_CUDA_TRY(h, cudaMemcpyAsync(d, V.data, bytes, cudaMemcpyHostToDevice, st));
+    P->dev.data = d;
+    P->host_input = true;
+  }
+  P->S = static_cast<double*>(ws_get(h, WS_SUMS, (size_t)std::max<int64_t>(V.nv, 1) * 8));
+  if (!P->S) return PS_ERR_OOM;
+  {
+    ScopedTimer tm(h, "vector_sums", st);
+    PS_CUDA_TRY(h, launch_vector_sums(P->dev, P->S, st));
+  }
+  if (!need_f32) return PS_OK;
+  const bool direct = V.dtype == PS_F32 && V.layout == PS_LAYOUT_FIELD_MAJOR && V.ld % 4 == 0 &&
+                      ((uintptr_t)P->dev.data % 16) == 0;
+  if (direct) {
+    P->f32 = VF32{static_cast<const float*>(P->dev.data), V.ld, (int)V.nv, (int)V.nf};
+  } else {
+    const int64_t ldp = round_up(V.nv, 4);
+    float* d = static_cast<float*>(ws_get(h, WS_PACKED, (size_t)std::max<int64_t>(V.nf * ldp, 1) * 4));
+    if (!d) return PS_ERR_OOM;
+    {
+      ScopedTimer tm(h, "pack", st);
+      PS_CUDA_TRY(h, launch_pack_f32(P->dev, d, ldp, st));
+    }
+    P->f32 = VF32{d, ldp, (int)V.nv, (int)V.nf};
+  }
+  return PS_OK;
+}
+
+// Output buffer: caller device memory, or workspace staging for host memory.
+struct OutBuf {
+  void* dev = nullptr;
+  void* user = nullptr;
+  size_t bytes = 0;
+  bool host = false;
+};
+
+ps_status resolve_out(ps_ctx* h, void* user, size_t bytes, WsSlot slot, OutBuf* o) {
+  o->user = user;
+  o->bytes = bytes;
+  PtrKind k;
+  ps_status s = ptr_kind(h, user, &k);
+  if (s != PS_OK) return s;
+  if (k == PK_DEVICE) {
+    o->dev = user;
+    return PS_OK;
+  }
+  o->host = true;
+  o->dev = ws_get(h, slot, bytes);
+  return o->dev ? PS_OK : PS_ERR_OOM;
+}
+
+ps_status finish(ps_ctx* h, const OutBuf& o, bool any_host, cudaStream_t st) {
+  if (o.host && o.bytes)
+    PS_CUDA_TRY(h, cudaMemcpyAsync(o.user, o.dev, o.bytes, cudaMemcpyDeviceToHost, st));
+  if (any_host) PS_CUDA_TRY(h, cudaStreamSynchronize(st));
+  PS_CUDA_TRY(h, cudaGetLastError());
+  return PS_OK;
+}
+
+}  // namespace
+}  // namespace ps
+
+using namespace ps;
+
+extern "C" {
+
+const char* ps_version(void) { return "ps-gb300 0.1 (sm_103a)"; }
+
+const char* ps_status_string(ps_status s) {
+  switch (s) {
+    case PS_OK: return "PS_OK";
+    case PS_ERR_INVALID_ARG: return "PS_ERR_INVALID_ARG";
+    case PS_ERR_OOM: return "PS_ERR_OOM";
+    case PS_ERR_CUDA: return "PS_ERR_CUDA";
+    case PS_ERR_CAPACITY: return "PS_ERR_CAPACITY";
+    case PS_ERR_TIMEOUT: return "PS_ERR_TIMEOUT";
+    case PS_ERR_UNSUPPORTED: return "PS_ERR_UNSUPPORTED";
+  }
+  return "PS_ERR_UNKNOWN";
+}
+
+const char* ps_last_error(ps_handle h) {
+  if (h) return h->last_error.c_str();
+  std::lock_guard<std::mutex> g(g_err_mu);
+  return g_last_error.c_str();
+}
+
+ps_status ps_create(ps_handle* out, int device) {
+  if (!out) return fail(nullptr, PS_ERR_INVALID_ARG, "ps_create: null out");
+  *out = nullptr;
+  int n = 0;
+  cudaError_t e = cudaGetDeviceCount(&n);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(nullptr, PS_ERR_CUDA, "cudaGetDeviceCount: %s", cudaGetErrorString(e));
+  }
+  if (device < 0 || device >= n)
+    return fail(nullptr, PS_ERR_INVALID_ARG, "device %d not in [0,%d)", device, n);
+  ps_ctx* h = new (std::nothrow) ps_ctx();
+  if (!h) return fail(nullptr, PS_ERR_OOM, "ps_create: out of host memory");
+  h->device = device;
+  Guard g(device);
+  cudaDeviceProp prop;
+  e = cudaGetDeviceProperties(&prop, device);
+  if (e != cudaSuccess) {
+    delete h;
+    return fail(nullptr, PS_ERR_CUDA, "cudaGetDeviceProperties: %s", cudaGetErrorString(e));
+  }
+  h->num_sms = prop.multiProcessorCount;
+  h->cc_major = prop.major;
+  h->cc_minor = prop.minor;
+  h->smem_optin = prop.sharedMemPerBlockOptin;
+  if (prop.major < 10) {
+    delete h;
+    return fail(nullptr, PS_ERR_UNSUPPORTED, "device %d is sm_%d%d; this library is built for sm_103a",
+                device, prop.major, prop.minor);
+  }
+  *out = h;
+  return PS_OK;
+}
+
+ps_status ps_destroy(ps_handle h) {
+  if (!h) return PS_OK;
+  {
+    Guard g(h->device);
+    cudaDeviceSynchronize();
+    timing_clear(h);
+    for (int s = 0; s < WS_NUM_SLOTS; ++s)
+      if (h->ws.ptr[s]) cudaFree(h->ws.ptr[s]);
+  }
+  delete h;
+  return PS_OK;
+}
+
+int64_t ps_slab_size(int64_t nv, int64_t j_begin, int64_t j_end) {
+  if (nv < 0 || j_begin < 0 || j_end < j_begin || j_end > nv) return -1;
+  auto F = [nv](int64_t x) { return (nv - 1) * (x * (x - 1) / 2) - (x - 1) * x * (2 * x - 1) / 6; };
+  return F(j_end) - F(j_begin);
+}
+
+ps_status ps_vector_sums(ps_handle h, const ps_matrix* V, double* S, ps_stream stream) {
+  if (!h) return fail(nullptr, PS_ERR_INVALID_ARG, "null handle");
+  ps_status s = check_matrix(h, V, 0);
+  if (s != PS_OK) return s;
+  if (!S && V->nv > 0) return fail(h, PS_ERR_INVALID_ARG, "null S");
+  if (V->nv == 0) return PS_OK;
+  Guard g(h->device);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  Prepared P;
+  s = prepare(h, *V, st, false, &P);
+  if (s != PS_OK) return s;
+  OutBuf o;
+  s = resolve_out(h, S, (size_t)V->nv * 8, WS_OUTPUT, &o);
+  if (s != PS_OK) return s;
+  PS_CUDA_TRY(h, cudaMemcpyAsync(o.dev, P.S, (size_t)V->nv * 8, cudaMemcpyDeviceToDevice, st));
+  return finish(h, o, P.host_input || o.host, st);
+}
+
+ps_status ps_metrics_2way(ps_handle h, const ps_matrix* V, int32_t path, int32_t levels, void* out,
+                          int32_t out_dtype, ps_stream stream) {
+  if (!h) return fail(nullptr, PS_ERR_INVALID_ARG, "null handle");
+  ps_status s = check_matrix(h, V, 2);
+  if (s != PS_OK) return s;
+  if (!out) return fail(h, PS_ERR_INVALID_ARG, "null out");
+  if (out_dtype != PS_F32 && out_dtype != PS_F64)
+    return fail(h, PS_ERR_INVALID_ARG, "out_dtype %d is not PS_F32/PS_F64", out_dtype);
+  if (path != PS_PATH_FP32 && path != PS_PATH_FP64 && path != PS_PATH_THERMO)
+    return fail(h, PS_ERR_INVALID_ARG, "path %d is not a ps_path", path);
+  if (path == PS_PATH_THERMO && (levels < 2 || levels > 16))
+    return fail(h, PS_ERR_INVALID_ARG, "levels=%d outside [2,16]", levels);
+  if (path == PS_PATH_THERMO)
+    return fail(h, PS_ERR_UNSUPPORTED, "thermometer path not built yet");
+  Guard g(h->device);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const int64_t npairs = V->nv * (V->nv - 1) / 2;
+  const size_t obytes = (size_t)npairs * dtype_size(out_dtype);
+  OutBuf o;
+  s = resolve_out(h, out, obytes, WS_OUTPUT, &o);
+  if (s != PS_OK) return s;
+  Prepared P;
+  if (path == PS_PATH_FP32) {
+    s = prepare(h, *V, st, true, &P);
+    if (s != PS_OK) return s;
+    ScopedTimer tm(h, "mgemm2", st);
+    PS_CUDA_TRY(h, launch_mgemm2(h, P.f32, P.S, o.dev,
+                                 out_dtype == PS_F64 ? OUT2_C2_F64 : OUT2_C2_F32, st));
+  } else {  // PS_PATH_FP64: FP64 field-major operand
+    s = prepare(h, *V, st, false, &P);
+    if (s != PS_OK) return s;
+    const double* X;
+    int64_t ld;
+    if (V->dtype == PS_F64 && V->layout == PS_LAYOUT_FIELD_MAJOR) {
+      X = static_cast<const double*>(P.dev.data);
+      ld = V->ld;
+    } else {  // exact widening / transpose into an FP64 field-major copy
+      const int64_t ldp = round_up(V->nv, 4);
+      double* d = static_cast<double*>(ws_get(h, WS_PACKED, (size_t)std::max<int64_t>(V->nf * ldp, 1) * 8));
+      if (!d) return PS_ERR_OOM;
+      PS_CUDA_TRY(h, launch_pack_f64(P.dev, d, ldp, st));
+      X = d;
+      ld = ldp;
+    }
+    ScopedTimer tm(h, "mgemm2_f64", st);
+    PS_CUDA_TRY(h, launch_mgemm2_f64(h, X, ld, (int)V->nv, (int)V->nf, P.S, o.dev,
+                                     out_dtype == PS_F64, st));
+  }
+  return finish(h, o, P.host_input || o.host, st);
+}
+
+ps_status ps_metrics_3way(ps_handle h, const ps_matrix* V, int64_t j_begin, int64_t j_end,
+                          float* out_slab, ps_stream stream) {
+  if (!h) return fail(nullptr, PS_ERR_INVALID_ARG, "null handle");
+  ps_status s = check_matrix(h, V, 3);
+  if (s != PS_OK) return s;
+  if (j_begin < 0 || j_end < j_begin || j_end > V->nv)
+    return fail(h, PS_ERR_INVALID_ARG, "pivot range [%lld,%lld) not inside [0,%lld]",
+                (long long)j_begin, (long long)j_end, (long long)V->nv);
+  const int64_t n = ps_slab_size(V->nv, j_begin, j_end);
+  if (n > 0 && !out_slab) return fail(h, PS_ERR_INVALID_ARG, "null out_slab");
+  if (n == 0) return PS_OK;
+  Guard g(h->device);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  OutBuf o;
+  s = resolve_out(h, out_slab, (size_t)n * 4, WS_OUTPUT, &o);
+  if (s != PS_OK) return s;
+  Prepared P;
+  s = prepare(h, *V, st, true, &P);
+  if (s != PS_OK) return s;
+  float* n2 = static_cast<float*>(ws_get(h, WS_N2, (size_t)V->nv * V->nv * 4));
+  if (!n2) return PS_ERR_OOM;
+  {
+    ScopedTimer tm(h, "mgemm2_n2", st);
+    PS_CUDA_TRY(h, launch_mgemm2(h, P.f32, P.S, n2, OUT2_N2_SQUARE_F32, st));
+  }
+  {
+    ScopedTimer tm(h, "mgemm3", st);
+    PS_CUDA_TRY(h, launch_mgemm3(h, P.f32, P.S, n2, j_begin, j_end, static_cast<float*>(o.dev), st));
+  }
+  return finish(h, o, P.host_input || o.host, st);
+}
+
+ps_status ps_threshold_3way(ps_handle h, const ps_matrix* V, float tau, int32_t use_proposal,
+                            ps_triple* out, int64_t capacity, int64_t* count, ps_stream stream) {
+  (void)V; (void)tau; (void)use_proposal; (void)out; (void)capacity; (void)count; (void)stream;
+  return fail(h, PS_ERR_UNSUPPORTED, "ps_threshold_3way not built yet");
+}
+
+ps_status ps_quantize(ps_handle h, const ps_matrix* V, int32_t levels, float* P_out, uint8_t* q_out,
+                      ps_stream stream) {
+  (void)V; (void)levels; (void)P_out; (void)q_out; (void)stream;
+  return fail(h, PS_ERR_UNSUPPORTED, "ps_quantize not built yet");
+}
+
+ps_status ps_timing_enable(ps_handle h, int32_t enable) {
+  if (!h) return fail(nullptr, PS_ERR_INVALID_ARG, "null handle");
+  Guard g(h->device);
+  timing_clear(h);
+  h->timing = enable != 0;
+  return PS_OK;
+}
+
+ps_status ps_timing_read(ps_handle h, const char* kernel, int64_t* launches, double* total_ms) {
+  if (!h || !kernel || !launches || !total_ms)
+    return fail(h, PS_ERR_INVALID_ARG, "ps_timing_read: null argument");
+  Guard g(h->device);
+  int64_t n = 0;
+  double ms = 0.0;
+  for (auto& r : h->trecs) {
+    if (strcmp(r.name, kernel) != 0) continue;
+    PS_CUDA_TRY(h, cudaEventSynchronize(r.b));
+    float t = 0.f;
+    PS_CUDA_TRY(h, cudaEventElapsedTime(&t, r.a, r.b));
+    ms += t;
+    ++n;
+  }
+  *launches = n;
+  *total_ms = ms;
+  return PS_OK;
+}
+
+ps_status ps_probe_minadd_peak(ps_handle h, int32_t variant, double* cmp_per_s) {
+  if (!h) return fail(nullptr, PS_ERR_INVALID_ARG, "null handle");
+  if (variant != 0 && variant != 1) return fail(h, PS_ERR_INVALID_ARG, "variant %d", variant);
+  if (!cmp_per_s) return fail(h, PS_ERR_INVALID_ARG, "null cmp_per_s");
+  Guard g(h->device);
+  PS_CUDA_TRY(h, probe_minadd(h, variant, cmp_per_s));
+  return PS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,157 @@
+"""Thin ctypes binding of libps.so (include/ps.h); argument marshalling only.
+
+Every computation runs in the CUDA library.  Importing this module loads
+``_build/libps.so`` and raises ``ImportError`` if it has not been built
+(``python -m paper_1705_08210_gb300.build_lib``) -- there is no fallback.
+
+Function names follow the C ABI.  ``ps_*`` functions take raw integers /
+pointers exactly like the C calls; ``matrix()`` builds a ``ps_matrix`` from a
+torch tensor or numpy array, and ``check()`` turns a status into an
+exception.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libps.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"libps.so not built at {LIB_PATH}; run paper_1705_08210_gb300.build_lib.build()")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+PS_OK, PS_ERR_INVALID_ARG, PS_ERR_OOM, PS_ERR_CUDA, PS_ERR_CAPACITY, PS_ERR_TIMEOUT, PS_ERR_UNSUPPORTED = range(7)
+PS_F32, PS_F64 = 0, 1
+PS_PATH_FP32, PS_PATH_FP64, PS_PATH_THERMO = 0, 1, 2
+PS_LAYOUT_FIELD_MAJOR, PS_LAYOUT_VECTOR_MAJOR = 0, 1
+
+
+class ps_matrix(ctypes.Structure):
+    _fields_ = [("data", ctypes.c_void_p), ("nv", ctypes.c_int64), ("nf", ctypes.c_int64),
+                ("ld", ctypes.c_int64), ("dtype", ctypes.c_int32), ("layout", ctypes.c_int32)]
+
+
+class ps_triple(ctypes.Structure):
+    _fields_ = [("i", ctypes.c_int32), ("j", ctypes.c_int32), ("k", ctypes.c_int32),
+                ("value", ctypes.c_float)]
+
+
+_h = ctypes.c_void_p
+_p = ctypes.c_void_p
+_i32, _i64 = ctypes.c_int32, ctypes.c_int64
+_M = ctypes.POINTER(ps_matrix)
+
+
+def _sig(name, res, args):
+    f = getattr(_lib, name)
+    f.restype = res
+    f.argtypes = args
+    return f
+
+
+ps_create = _sig("ps_create", ctypes.c_int, [ctypes.POINTER(_h), ctypes.c_int])
+ps_destroy = _sig("ps_destroy", ctypes.c_int, [_h])
+ps_status_string = _sig("ps_status_string", ctypes.c_char_p, [ctypes.c_int])
+ps_last_error = _sig("ps_last_error", ctypes.c_char_p, [_h])
+ps_version = _sig("ps_version", ctypes.c_char_p, [])
+ps_vector_sums = _sig("ps_vector_sums", ctypes.c_int, [_h, _M, _p, _p])
+ps_metrics_2way = _sig("ps_metrics_2way", ctypes.c_int, [_h, _M, _i32, _i32, _p, _i32, _p])
+ps_slab_size = _sig("ps_slab_size", _i64, [_i64, _i64, _i64])
+ps_metrics_3way = _sig("ps_metrics_3way", ctypes.c_int, [_h, _M, _i64, _i64, _p, _p])
+ps_threshold_3way = _sig("ps_threshold_3way", ctypes.c_int,
+                         [_h, _M, ctypes.c_float, _i32, _p, _i64, _p, _p])
+ps_quantize = _sig("ps_quantize", ctypes.c_int, [_h, _M, _i32, _p, _p, _p])
+ps_timing_enable = _sig("ps_timing_enable", ctypes.c_int, [_h, _i32])
+ps_timing_read = _sig("ps_timing_read", ctypes.c_int,
+                      [_h, ctypes.c_char_p, ctypes.POINTER(_i64), ctypes.POINTER(ctypes.c_double)])
+ps_probe_minadd_peak = _sig("ps_probe_minadd_peak", ctypes.c_int,
+                            [_h, _i32, ctypes.POINTER(ctypes.c_double)])
+
+EXPORTED = [n for n in globals() if n.startswith("ps_") and callable(globals()[n])
+            and n not in ("ps_matrix", "ps_triple")]
+
+
+class PSError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{ps_status_string(status).decode()}: {msg}")
+        self.status = status
+
+
+def check(status: int, handle=None) -> int:
+    if status != PS_OK:
+        raise PSError(status, ps_last_error(handle).decode(errors="replace"))
+    return status
+
+
+class Handle:
+    """Owns a ps_handle for one CUDA device."""
+
+    def __init__(self, device: int = 0):
+        self.h = _h()
+        check(ps_create(ctypes.byref(self.h), int(device)))
+
+    def close(self):
+        if self.h:
+            ps_destroy(self.h)
+            self.h = _h()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def _ptr_of(x) -> int:
+    if x is None:
+        return 0
+    if hasattr(x, "data_ptr"):
+        return int(x.data_ptr())
+    if hasattr(x, "ctypes"):
+        return int(x.ctypes.data)
+    return int(x)
+
+
+def _dtype_of(x) -> int:
+    name = str(x.dtype)
+    if "float32" in name:
+        return PS_F32
+    if "float64" in name:
+        return PS_F64
+    raise TypeError(f"unsupported dtype {name}")
+
+
+def matrix(X, layout: int = PS_LAYOUT_FIELD_MAJOR) -> ps_matrix:
+    """ps_matrix for a 2-D array.
+
+    layout FIELD_MAJOR: X has shape (nf, nv) (row q = field q of every vector);
+    layout VECTOR_MAJOR: X has shape (nv, nf).  Rows may be padded (stride)."""
+    if X.ndim != 2:
+        raise ValueError("matrix must be 2-D")
+    if hasattr(X, "stride") and callable(X.stride):
+        s0, s1 = X.stride()
+    else:
+        s0, s1 = (st // X.itemsize for st in X.strides)
+    if s1 != 1:
+        raise ValueError("inner dimension must be contiguous")
+    if layout == PS_LAYOUT_FIELD_MAJOR:
+        nf, nv = X.shape
+    else:
+        nv, nf = X.shape
+    return ps_matrix(_ptr_of(X), nv, nf, max(int(s0), 1), _dtype_of(X), layout)
+
+
+def stream_ptr(stream) -> int:
+    if stream is None:
+        return 0
+    if hasattr(stream, "cuda_stream"):
+        return int(stream.cuda_stream)
+    return int(stream)

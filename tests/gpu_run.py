@@ -1,0 +1,73 @@
+"""Helpers for the GPU parity tests: call the C ABI with torch buffers."""
+import ctypes
+
+import numpy as np
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def metrics_2way(ps, handle, V, path=0, out_dtype=np.float32, layout=0, levels=0,
+                 on_host=False, stream=None):
+    """Run ps_metrics_2way on a numpy matrix (shape per `layout`); returns numpy."""
+    torch = _torch()
+    if layout == 0:
+        nf, nv = V.shape
+    else:
+        nv, nf = V.shape
+    npairs = nv * (nv - 1) // 2
+    if on_host:
+        X = np.ascontiguousarray(V)
+        out = np.empty(npairs, dtype=out_dtype)
+        m = ps.matrix(X, layout)
+        optr = out.ctypes.data
+    else:
+        X = torch.from_numpy(np.ascontiguousarray(V)).cuda()
+        out_t = torch.empty(npairs, dtype=torch.float32 if out_dtype == np.float32 else torch.float64,
+                            device="cuda")
+        m = ps.matrix(X, layout)
+        optr = out_t.data_ptr()
+    st = torch.cuda.current_stream() if stream is None else stream
+    ps.check(ps.ps_metrics_2way(handle.h, ctypes.byref(m), path, levels, optr,
+                                0 if out_dtype == np.float32 else 1, st.cuda_stream), handle.h)
+    torch.cuda.synchronize()
+    return out if on_host else out_t.cpu().numpy()
+
+
+def metrics_3way(ps, handle, V, jb=None, je=None, layout=0):
+    torch = _torch()
+    nv = V.shape[1] if layout == 0 else V.shape[0]
+    jb = 0 if jb is None else jb
+    je = nv if je is None else je
+    n = ps.ps_slab_size(nv, jb, je)
+    X = torch.from_numpy(np.ascontiguousarray(V)).cuda()
+    out = torch.empty(max(n, 1), dtype=torch.float32, device="cuda")
+    m = ps.matrix(X, layout)
+    ps.check(ps.ps_metrics_3way(handle.h, ctypes.byref(m), jb, je, out.data_ptr(),
+                                torch.cuda.current_stream().cuda_stream), handle.h)
+    torch.cuda.synchronize()
+    return out[:n].cpu().numpy()
+
+
+def assert_rel(got, ref, rtol, what=""):
+    """|got - ref| <= rtol * |ref| elementwise (zeros must be exact)."""
+    got = np.asarray(got, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    assert got.shape == ref.shape, (got.shape, ref.shape)
+    err = np.abs(got - ref)
+    bad = err > rtol * np.abs(ref)
+    if bad.any():
+        idx = np.flatnonzero(bad)[:5]
+        raise AssertionError(f"{what}: {bad.sum()} of {bad.size} outside rtol={rtol}; first "
+                             f"{[(int(t), float(got[t]), float(ref[t])) for t in idx]}")
+    nz = ref != 0
+    return float((err[nz] / np.abs(ref[nz])).max()) if nz.any() else 0.0
+
+
+def slab_index(nv, jb, i, j, k):
+    """Position of (i, j, k) in the pivot-slab layout starting at pivot jb."""
+    i, j, k = (np.asarray(x, dtype=np.int64) for x in (i, j, k))
+    F = lambda x: (nv - 1) * (x * (x - 1) // 2) - (x - 1) * x * (2 * x - 1) // 6  # noqa: E731
+    return F(j) - F(np.int64(jb)) + i * (nv - 1 - j) + (k - j - 1)

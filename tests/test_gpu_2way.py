@@ -1,0 +1,128 @@
+"""GPU parity of the 2-way path (Section 2.1, Section 3.1) against the oracle.
+
+Tolerance: FP32 paths 1e-5 relative (the accumulation carries at most 64
+roundings of a 64-term partial sum, 64 * 2^-24 = 3.8e-6, plus the FP32
+rounding of the operands and of the ratio); the FP64 path 1e-12; integer
+data bit-exact."""
+import ctypes
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1705_08210_gb300 import synth
+from gpu_run import assert_rel, metrics_2way
+
+pytestmark = pytest.mark.gpu
+RTOL32 = 1e-5
+
+
+def test_config1_all_pairs_fp32_path(ps, handle):
+    # 1024 x 512 FP64, packed FP64 output, FP32 min/add numerators
+    V = synth.zero_inflated(1024, 512, synth.seed_for(1), dtype=np.float64)
+    ref = oracle.c2_packed(oracle.to_vector_major(V))
+    got = metrics_2way(ps, handle, V, path=ps.PS_PATH_FP32, out_dtype=np.float64)
+    err = assert_rel(got, ref, RTOL32, "config1 fp32 path")
+    print(f"config1 fp32 path max rel err {err:.3e}")
+
+
+def test_config1_all_pairs_fp64_path(ps, handle):
+    V = synth.zero_inflated(1024, 512, synth.seed_for(1), dtype=np.float64)
+    ref = oracle.c2_packed(oracle.to_vector_major(V))
+    got = metrics_2way(ps, handle, V, path=ps.PS_PATH_FP64, out_dtype=np.float64)
+    assert_rel(got, ref, 1e-12, "config1 fp64 path")
+
+
+@pytest.mark.parametrize("nv", [2, 3, 5, 127, 128, 129, 300])
+@pytest.mark.parametrize("nf", [0, 1, 15, 17, 100, 1000])
+def test_ragged_shapes(ps, handle, nv, nf):
+    V = synth.zero_inflated(nv, nf, synth.seed_for(1, nv * 7 + nf), dtype=np.float32)
+    ref = oracle.c2_packed(oracle.to_vector_major(V))
+    got = metrics_2way(ps, handle, V)
+    assert_rel(got, ref, RTOL32, f"nv={nv} nf={nf}")
+
+
+def test_integer_data_bit_exact(ps, handle):
+    V = synth.integer_levels(700, 3000, synth.seed_for(1, 99))
+    ref = oracle.c2_packed(oracle.to_vector_major(V))
+    got32 = metrics_2way(ps, handle, V)
+    np.testing.assert_array_equal(got32, ref.astype(np.float32))
+    got64 = metrics_2way(ps, handle, V, out_dtype=np.float64)
+    np.testing.assert_array_equal(got64, ref)
+    got64p = metrics_2way(ps, handle, V, path=ps.PS_PATH_FP64, out_dtype=np.float64)
+    np.testing.assert_array_equal(got64p, ref)
+
+
+def test_all_zero_vectors_and_duplicates(ps, handle):
+    V = synth.zero_inflated(200, 64, synth.seed_for(1, 5))
+    V[:, 3] = 0.0          # all-zero vector
+    V[:, 4] = 0.0
+    V[:, 10] = V[:, 11]    # duplicate pair
+    got = metrics_2way(ps, handle, V, out_dtype=np.float64)
+    ref = oracle.c2_packed(oracle.to_vector_major(V))
+    assert got[oracle.pair_index(200, 3, 4)] == 0.0
+    assert_rel(got, ref, RTOL32, "zeros/duplicates")
+    assert abs(got[oracle.pair_index(200, 10, 11)] - 1.0) < 1e-6
+
+
+def test_layouts_strides_and_host_buffers(ps, handle):
+    nv, nf = 333, 257
+    V32 = synth.zero_inflated(nv, nf, synth.seed_for(1, 6))
+    base = metrics_2way(ps, handle, V32)
+    ref = oracle.c2_packed(oracle.to_vector_major(V32))
+    assert_rel(base, ref, RTOL32, "base")
+    # vector-major copy of the same data
+    np.testing.assert_array_equal(metrics_2way(ps, handle, np.ascontiguousarray(V32.T), layout=1), base)
+    # padded leading dimension with NaN garbage in the padding
+    P = np.full((nf, nv + 13), np.nan, dtype=np.float32)
+    P[:, :nv] = V32
+    np.testing.assert_array_equal(metrics_2way(ps, handle, P[:, :nv]), base)
+    # host (pageable numpy) input and output
+    np.testing.assert_array_equal(metrics_2way(ps, handle, V32, on_host=True), base)
+    # FP64 input rounded to the same FP32 values gives the same numerators
+    got64 = metrics_2way(ps, handle, V32.astype(np.float64), out_dtype=np.float64)
+    assert_rel(got64, ref, RTOL32, "f64 input")
+
+
+def test_invalid_arguments(ps, handle):
+    import torch
+    X = torch.zeros(4, 10, device="cuda")
+    out = torch.zeros(100, device="cuda")
+    m = ps.matrix(X)
+    st = 0
+    bad = ps.ps_matrix(m.data, 1, 4, 10, 0, 0)  # nv = 1
+    assert ps.ps_metrics_2way(handle.h, ctypes.byref(bad), 0, 0, out.data_ptr(), 0, st) == ps.PS_ERR_INVALID_ARG
+    bad = ps.ps_matrix(m.data, 10, 4, 5, 0, 0)  # ld < nv
+    assert ps.ps_metrics_2way(handle.h, ctypes.byref(bad), 0, 0, out.data_ptr(), 0, st) == ps.PS_ERR_INVALID_ARG
+    bad = ps.ps_matrix(m.data, 10, 4, 10, 0, 7)  # layout
+    assert ps.ps_metrics_2way(handle.h, ctypes.byref(bad), 0, 0, out.data_ptr(), 0, st) == ps.PS_ERR_INVALID_ARG
+    assert ps.ps_metrics_2way(handle.h, ctypes.byref(m), 0, 0, None, 0, st) == ps.PS_ERR_INVALID_ARG
+    assert ps.ps_metrics_2way(handle.h, ctypes.byref(m), 9, 0, out.data_ptr(), 0, st) == ps.PS_ERR_INVALID_ARG
+    assert ps.ps_metrics_2way(handle.h, ctypes.byref(m), 2, 1, out.data_ptr(), 0, st) == ps.PS_ERR_INVALID_ARG
+    assert b"levels" in ps.ps_last_error(handle.h)
+
+
+def test_config2_full_size_sampled(ps, handle):
+    """32768 x 8192 FP32 in the benchmark's launch configuration; 20000 sampled
+    pairs against the oracle, all values in [0, 1]."""
+    import torch
+    nv, nf = 32768, 8192
+    V = synth.zero_inflated(nv, nf, synth.seed_for(2))
+    X = torch.from_numpy(V).cuda()
+    out = torch.empty(nv * (nv - 1) // 2, dtype=torch.float32, device="cuda")
+    m = ps.matrix(X)
+    ps.check(ps.ps_metrics_2way(handle.h, ctypes.byref(m), 0, 0, out.data_ptr(), 0,
+                                torch.cuda.current_stream().cuda_stream), handle.h)
+    torch.cuda.synchronize()
+    assert float(out.min()) >= 0.0 and float(out.max()) <= 1.0
+    pairs = synth.sample_pairs(nv, 20000, seed=7)
+    # include tile corners and the last pair
+    pairs = np.concatenate([pairs, [[0, 1], [127, 128], [0, nv - 1], [nv - 2, nv - 1], [128, 255]]])
+    idx = torch.from_numpy(oracle.pair_index(nv, pairs[:, 0], pairs[:, 1])).cuda()
+    got = out[idx].cpu().numpy()
+    Vv = np.ascontiguousarray(V[:, np.unique(pairs)].T).astype(np.float64)
+    remap = {v: t for t, v in enumerate(np.unique(pairs))}
+    rp = np.vectorize(remap.get)(pairs)
+    ref = oracle.c2_pairs(Vv, rp)
+    err = assert_rel(got, ref, RTOL32, "config2 sampled")
+    print(f"config2 sampled max rel err {err:.3e}")
