@@ -38,6 +38,9 @@ WORKLOADS = {
     "2way_32768x8192_f32": dict(way=2, nv=32768, nf=8192, number=2),
     "3way_2048x4096_f32": dict(way=3, nv=2048, nf=4096, number=3),
     "2way_1024x512_f64": dict(way=2, nv=1024, nf=512, number=1),
+    # small cases of the same kernels for profiler captures
+    "2way_8192x8192_f32": dict(way=2, nv=8192, nf=8192, number=2),
+    "3way_1024x4096_f32": dict(way=3, nv=1024, nf=4096, number=3),
 }
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 
@@ -242,10 +245,12 @@ def main():
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     props = torch.cuda.get_device_properties(local)
     n_sm = props.multi_processor_count
-    # CUDA-core issue bound of the inner loop: per SM and clock 4 schedulers
-    # x 32 lanes issue one warp instruction each; a comparison pair takes two
-    # FMNMX and one packed f32x2 FADD = 1.5 issue slots per comparison.
-    peak_cmp = n_sm * 128 / 1.5 * sm_max * 1e6
+    # ALU-pipe bound of the inner loop: FP32 min (FMNMX) executes on the ALU
+    # pipe at 16 lanes per clock per SM sub-partition (two pipe cycles per
+    # warp instruction, measured with ncu), so an SM retires at most
+    # 4 x 16 = 64 comparisons per clock whatever the add form; the adds run on
+    # the FMA pipe in parallel.
+    peak_cmp = n_sm * 64 * sm_max * 1e6
     probe = ctypes.c_double()
     ps.check(ps.ps_probe_minadd_peak(h.h, 1, ctypes.byref(probe)), h.h)
     probe0 = ctypes.c_double()
@@ -253,7 +258,7 @@ def main():
     roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_cmp / 1e12, "unit": "Tcmp/s",
                 "frac": achieved / peak_cmp, "traffic": None,
                 "kernel": main_kernel, "kernel_ms": k_avg_ms,
-                "peak_basis": f"{n_sm} SMs x 128 lanes / 1.5 issue slots per comparison x {sm_max:.0f} MHz (max clock)",
+                "peak_basis": f"{n_sm} SMs x 64 FP32 min lanes/clock (ALU pipe) x {sm_max:.0f} MHz max clock",
                 "probe_minadd_f32x2": probe.value / 1e12, "probe_minadd_scalar": probe0.value / 1e12}
 
     # ---- end to end through the C ABI with host buffers ----

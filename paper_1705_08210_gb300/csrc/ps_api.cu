@@ -6,6 +6,7 @@
 
 #include <algorithm>
 #include <cstdarg>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -284,6 +285,11 @@ ps_status ps_create(ps_handle* out, int device) {
   h->cc_major = prop.major;
   h->cc_minor = prop.minor;
   h->smem_optin = prop.sharedMemPerBlockOptin;
+  if (const char* v = getenv("PS_MGEMM_ADD")) h->mgemm_packed_add = strcmp(v, "scalar") != 0;
+  if (const char* v = getenv("PS_MGEMM_KU")) {
+    const int ku = atoi(v);
+    if (ku == 4 || ku == 8 || ku == 16) h->mgemm_ku = ku;
+  }
   if (prop.major < 10) {
     delete h;
     return fail(nullptr, PS_ERR_UNSUPPORTED, "device %d is sm_%d%d; this library is built for sm_103a",

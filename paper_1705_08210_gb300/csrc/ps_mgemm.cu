@@ -139,8 +139,15 @@ __device__ __forceinline__ float2 f2_unpack(unsigned long long v) {
   return r;
 }
 
-// Per-thread accumulator block: 8 x 8 outputs as 8 x 4 packed pairs.
-struct Acc {
+// Per-thread accumulator block for 8 x 8 outputs.  "lo" accumulates up to 64
+// fields; fold() moves it into "hi" with an exact TwoSum and leaves the
+// rounding residual in "lo".  PACKED adds pairs of accumulators with one
+// add.rn.f32x2; otherwise every accumulator takes a scalar FP32 add.
+template <bool PACKED>
+struct Acc;
+
+template <>
+struct Acc<true> {
   unsigned long long hi[8][4];
   unsigned long long lo[8][4];
   __device__ __forceinline__ void zero() {
@@ -149,7 +156,13 @@ struct Acc {
 #pragma unroll
       for (int c = 0; c < 4; ++c) hi[r][c] = lo[r][c] = 0ull;
   }
-  // Exact TwoSum (hi, lo) <- (fl(hi+lo), residual), elementwise on pairs.
+  __device__ __forceinline__ void step(const float (&a)[8], const float (&b)[8]) {
+#pragma unroll
+    for (int r = 0; r < 8; ++r)
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+        lo[r][c] = f2_add(lo[r][c], fminf(a[r], b[2 * c]), fminf(a[r], b[2 * c + 1]));
+  }
   __device__ __forceinline__ void fold() {
 #pragma unroll
     for (int r = 0; r < 8; ++r)
@@ -163,14 +176,55 @@ struct Acc {
         lo[r][c] = e;
       }
   }
+  // (hi, lo) of output (r, c)
+  __device__ __forceinline__ float2 hl(int r, int c) const {
+    const float2 h = f2_unpack(hi[r][c >> 1]);
+    const float2 l = f2_unpack(lo[r][c >> 1]);
+    return (c & 1) ? make_float2(h.y, l.y) : make_float2(h.x, l.x);
+  }
 };
 
-// 16 k steps of the 8 x 8 min-sum micro-kernel on ring buffer `buf`.
+template <>
+struct Acc<false> {
+  float hi[8][8];
+  float lo[8][8];
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int r = 0; r < 8; ++r)
+#pragma unroll
+      for (int c = 0; c < 8; ++c) hi[r][c] = lo[r][c] = 0.0f;
+  }
+  __device__ __forceinline__ void step(const float (&a)[8], const float (&b)[8]) {
+#pragma unroll
+    for (int r = 0; r < 8; ++r)
+#pragma unroll
+      for (int c = 0; c < 8; ++c) lo[r][c] = __fadd_rn(lo[r][c], fminf(a[r], b[c]));
+  }
+  __device__ __forceinline__ void fold() {
+#pragma unroll
+    for (int r = 0; r < 8; ++r)
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        const float s = __fadd_rn(hi[r][c], lo[r][c]);
+        const float bp = __fsub_rn(s, hi[r][c]);
+        const float ap = __fsub_rn(s, bp);
+        const float e = __fadd_rn(__fsub_rn(hi[r][c], ap), __fsub_rn(lo[r][c], bp));
+        hi[r][c] = s;
+        lo[r][c] = e;
+      }
+  }
+  __device__ __forceinline__ float2 hl(int r, int c) const { return make_float2(hi[r][c], lo[r][c]); }
+};
+
+// 16 k steps of the 8 x 8 min-sum micro-kernel on ring buffer `buf`,
+// unrolled KU steps at a time (smaller KU keeps the hot loop in the
+// instruction cache).
+template <bool PACKED, int KU>
 __device__ __forceinline__ void compute_slice(const SmemF32& sm, int buf, int am, int bn,
-                                              Acc& acc) {
+                                              Acc<PACKED>& acc) {
   const float* As = &sm.A[buf][0][am];
   const float* Bs = &sm.B[buf][0][bn];
-#pragma unroll
+#pragma unroll KU
   for (int kk = 0; kk < BK; ++kk) {
     const float4 a0 = *reinterpret_cast<const float4*>(As + kk * BM);
     const float4 a1 = *reinterpret_cast<const float4*>(As + kk * BM + 32);
@@ -178,18 +232,14 @@ __device__ __forceinline__ void compute_slice(const SmemF32& sm, int buf, int am
     const float4 b1 = *reinterpret_cast<const float4*>(Bs + kk * BN + 16);
     const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
     const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
-#pragma unroll
-    for (int r = 0; r < 8; ++r)
-#pragma unroll
-      for (int c = 0; c < 4; ++c)
-        acc.lo[r][c] = f2_add(acc.lo[r][c], fminf(a[r], b[2 * c]), fminf(a[r], b[2 * c + 1]));
+    acc.step(a, b);
   }
 }
 
 // Full k loop over n_f for one (row0, col0) tile, with optional pivot j.
-template <bool PIVOT>
+template <bool PIVOT, bool PACKED, int KU>
 __device__ __forceinline__ void tile_minsum(SmemF32& sm, const VF32& V, int row0, int col0,
-                                            int jpiv, int am, int bn, Acc& acc) {
+                                            int jpiv, int am, int bn, Acc<PACKED>& acc) {
   acc.zero();
   const int nst = (V.nf + BK - 1) / BK;
 #pragma unroll
@@ -208,7 +258,7 @@ __device__ __forceinline__ void tile_minsum(SmemF32& sm, const VF32& V, int row0
     const int sn = s + STAGES - 1;
     if (sn < nst) issue_slice<PIVOT>(sm, sn % STAGES, V, row0, col0, sn * BK, jpiv);
     cp_async_commit();
-    compute_slice(sm, buf, am, bn, acc);
+    compute_slice<PACKED, KU>(sm, buf, am, bn, acc);
     if ((s + 1) % FOLD == 0) acc.fold();
   }
   acc.fold();
@@ -245,32 +295,22 @@ __device__ __forceinline__ void tri_tile(int64_t t, int T, int& I, int& J) {
   J = i + (int)(t - ((int64_t)i * T - (int64_t)i * (i - 1) / 2));
 }
 
-__device__ __forceinline__ float2 final_pair(const Acc& acc, int r, int c) {
-  const float2 h = f2_unpack(acc.hi[r][c]);
-  const float2 l = f2_unpack(acc.lo[r][c]);
-  return make_float2(__fadd_rn(h.x, l.x), __fadd_rn(h.y, l.y));
-}
-__device__ __forceinline__ double final_pair_f64(const Acc& acc, int r, int c, int which) {
-  const float2 h = f2_unpack(acc.hi[r][c]);
-  const float2 l = f2_unpack(acc.lo[r][c]);
-  return which ? (double)h.y + (double)l.y : (double)h.x + (double)l.x;
-}
-
 // ---------------------------------------------------------------------------
 // 2-way: all c2 (or the n2 table) over the upper triangle of tiles.
+template <bool PACKED, int KU>
 __global__ void __launch_bounds__(NT, 1)
     mgemm2_kernel(VF32 V, const double* __restrict__ S, void* __restrict__ out, int mode,
                   int T, int64_t ntiles) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   SmemF32& sm = *reinterpret_cast<SmemF32*>(smem_raw);
   const Lanes L;
-  Acc acc;
+  Acc<PACKED> acc;
   const int64_t nv = V.nv;
   for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
     int I, J;
     tri_tile(t, T, I, J);
     const int row0 = I * BM, col0 = J * BN;
-    tile_minsum<false>(sm, V, row0, col0, 0, L.am, L.bn, acc);
+    tile_minsum<false, PACKED, KU>(sm, V, row0, col0, 0, L.am, L.bn, acc);
 #pragma unroll
     for (int r = 0; r < 8; ++r) {
       const int i = row0 + L.row(r);
@@ -280,19 +320,18 @@ __global__ void __launch_bounds__(NT, 1)
       for (int c = 0; c < 8; ++c) {
         const int j = col0 + L.col(c);
         if (j <= i || j >= nv) continue;
+        const float2 hl = acc.hl(r, c);
         if (mode == OUT2_C2_F32) {
-          const float2 n = final_pair(acc, r, c >> 1);
-          const float n2 = (c & 1) ? n.y : n.x;
+          const float n2 = __fadd_rn(hl.x, hl.y);
           const float d = (float)(Si + S[j]);
           const float v = (d == 0.0f) ? 0.0f : __fdiv_rn(2.0f * n2, d);
           static_cast<float*>(out)[pair_index(nv, i, j)] = v;
         } else if (mode == OUT2_C2_F64) {
-          const double n2 = final_pair_f64(acc, r, c >> 1, c & 1);
+          const double n2 = (double)hl.x + (double)hl.y;
           const double d = Si + S[j];
           static_cast<double*>(out)[pair_index(nv, i, j)] = (d == 0.0) ? 0.0 : (2.0 * n2) / d;
         } else {
-          const float2 n = final_pair(acc, r, c >> 1);
-          const float n2 = (c & 1) ? n.y : n.x;
+          const float n2 = __fadd_rn(hl.x, hl.y);
           float* tab = static_cast<float*>(out);
           tab[(int64_t)i * nv + j] = n2;
           tab[(int64_t)j * nv + i] = n2;
@@ -312,6 +351,7 @@ __device__ __forceinline__ int64_t slab_offset(int64_t n, int64_t jb, int64_t j)
   return F(j) - F(jb);
 }
 
+template <bool PACKED, int KU>
 __global__ void __launch_bounds__(NT, 1)
     mgemm3_kernel(VF32 V, const double* __restrict__ S, const float* __restrict__ n2sq,
                   const int64_t* __restrict__ pref, int npiv, int jb, float* __restrict__ out,
@@ -319,7 +359,7 @@ __global__ void __launch_bounds__(NT, 1)
   extern __shared__ __align__(16) unsigned char smem_raw[];
   SmemF32& sm = *reinterpret_cast<SmemF32*>(smem_raw);
   const Lanes L;
-  Acc acc;
+  Acc<PACKED> acc;
   const int nv = V.nv;
   const int Tk = (nv + BN - 1) / BN;
   for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
@@ -335,7 +375,7 @@ __global__ void __launch_bounds__(NT, 1)
     const int nK = Tk - k0t;
     const int ti = (int)(local / nK), tk = k0t + (int)(local % nK);
     const int row0 = ti * BM, col0 = tk * BN;
-    tile_minsum<true>(sm, V, row0, col0, j, L.am, L.bn, acc);
+    tile_minsum<true, PACKED, KU>(sm, V, row0, col0, j, L.am, L.bn, acc);
     const int64_t w = nv - 1 - j;
     const int64_t base = slab_offset(nv, jb, j);
     const double Sj = S[j];
@@ -349,7 +389,8 @@ __global__ void __launch_bounds__(NT, 1)
       for (int c = 0; c < 8; ++c) {
         const int k = col0 + L.col(c);
         if (k <= j || k >= nv) continue;
-        const double n3p = final_pair_f64(acc, r, c >> 1, c & 1);
+        const float2 hl = acc.hl(r, c);
+        const double n3p = (double)hl.x + (double)hl.y;
         const double n3 = ((n2ij + (double)n2sq[(int64_t)i * nv + k]) +
                            (double)n2sq[(int64_t)j * nv + k]) - n3p;
         const float d = (float)(Sij + S[k]);
@@ -483,18 +524,48 @@ __global__ void __launch_bounds__(1024) pivot_prefix_kernel(int nv, int jb, int 
   }
 }
 
-int g_mgemm_attr_set_device = -1;
+uint64_t g_mgemm_attr_devices = 0;  // bit d: attributes set on device d
+
+template <bool PACKED, int KU>
+cudaError_t set_attrs_one() {
+  const int sm = (int)sizeof(SmemF32);
+  cudaError_t e = cudaFuncSetAttribute(mgemm2_kernel<PACKED, KU>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(mgemm3_kernel<PACKED, KU>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              sm);
+}
 
 cudaError_t ensure_attrs(ps_ctx* h) {
-  if (g_mgemm_attr_set_device == h->device) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(mgemm2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)sizeof(SmemF32));
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(mgemm3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)sizeof(SmemF32));
-  if (e != cudaSuccess) return e;
-  g_mgemm_attr_set_device = h->device;
+  const uint64_t bit = 1ull << (h->device & 63);
+  if (g_mgemm_attr_devices & bit) return cudaSuccess;
+  cudaError_t e;
+  if ((e = set_attrs_one<true, 16>()) || (e = set_attrs_one<true, 8>()) ||
+      (e = set_attrs_one<true, 4>()) || (e = set_attrs_one<false, 16>()) ||
+      (e = set_attrs_one<false, 8>()) || (e = set_attrs_one<false, 4>()))
+    return e;
+  g_mgemm_attr_devices |= bit;
   return cudaSuccess;
+}
+
+// Kernel variant of the handle: accumulate form x k-unroll depth.
+template <bool PACKED, int KU>
+void launch2_v(unsigned grid, cudaStream_t st, const VF32& V, const double* S, void* out, int mode,
+               int T, int64_t ntiles) {
+  mgemm2_kernel<PACKED, KU><<<grid, NT, sizeof(SmemF32), st>>>(V, S, out, mode, T, ntiles);
+}
+template <bool PACKED, int KU>
+void launch3_v(unsigned grid, cudaStream_t st, const VF32& V, const double* S, const float* n2sq,
+               const int64_t* pref, int npiv, int jb, float* out, int64_t ntiles) {
+  mgemm3_kernel<PACKED, KU><<<grid, NT, sizeof(SmemF32), st>>>(V, S, n2sq, pref, npiv, jb, out,
+                                                               ntiles);
+}
+
+template <typename F16, typename F8, typename F4>
+void by_ku(int ku, F16 f16, F8 f8, F4 f4) {
+  if (ku == 16) f16();
+  else if (ku == 4) f4();
+  else f8();
 }
 
 }  // namespace
@@ -507,7 +578,15 @@ cudaError_t launch_mgemm2(ps_ctx* h, const VF32& V, const double* S, void* out, 
   const int64_t ntiles = (int64_t)T * (T + 1) / 2;
   if (ntiles == 0) return cudaSuccess;
   const int64_t grid = std::min<int64_t>(ntiles, (int64_t)h->num_sms);
-  mgemm2_kernel<<<(unsigned)grid, NT, sizeof(SmemF32), st>>>(V, S, out, mode, T, ntiles);
+  const unsigned g = (unsigned)grid;
+  if (h->mgemm_packed_add)
+    by_ku(h->mgemm_ku, [&] { launch2_v<true, 16>(g, st, V, S, out, mode, T, ntiles); },
+          [&] { launch2_v<true, 8>(g, st, V, S, out, mode, T, ntiles); },
+          [&] { launch2_v<true, 4>(g, st, V, S, out, mode, T, ntiles); });
+  else
+    by_ku(h->mgemm_ku, [&] { launch2_v<false, 16>(g, st, V, S, out, mode, T, ntiles); },
+          [&] { launch2_v<false, 8>(g, st, V, S, out, mode, T, ntiles); },
+          [&] { launch2_v<false, 4>(g, st, V, S, out, mode, T, ntiles); });
   return cudaGetLastError();
 }
 
@@ -526,8 +605,16 @@ cudaError_t launch_mgemm3(ps_ctx* h, const VF32& V, const double* S, const float
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const int64_t grid = std::min<int64_t>(ntiles, (int64_t)h->num_sms);
-  mgemm3_kernel<<<(unsigned)grid, NT, sizeof(SmemF32), st>>>(V, S, n2sq, dpref, npiv, (int)jb,
-                                                             out, ntiles);
+  const unsigned g = (unsigned)grid;
+  const int j0 = (int)jb;
+  if (h->mgemm_packed_add)
+    by_ku(h->mgemm_ku, [&] { launch3_v<true, 16>(g, st, V, S, n2sq, dpref, npiv, j0, out, ntiles); },
+          [&] { launch3_v<true, 8>(g, st, V, S, n2sq, dpref, npiv, j0, out, ntiles); },
+          [&] { launch3_v<true, 4>(g, st, V, S, n2sq, dpref, npiv, j0, out, ntiles); });
+  else
+    by_ku(h->mgemm_ku, [&] { launch3_v<false, 16>(g, st, V, S, n2sq, dpref, npiv, j0, out, ntiles); },
+          [&] { launch3_v<false, 8>(g, st, V, S, n2sq, dpref, npiv, j0, out, ntiles); },
+          [&] { launch3_v<false, 4>(g, st, V, S, n2sq, dpref, npiv, j0, out, ntiles); });
   return cudaGetLastError();
 }
 

@@ -140,13 +140,16 @@ def matrix(X, layout: int = PS_LAYOUT_FIELD_MAJOR) -> ps_matrix:
         s0, s1 = X.stride()
     else:
         s0, s1 = (st // X.itemsize for st in X.strides)
-    if s1 != 1:
+    rows, cols = X.shape
+    if rows * cols == 0 or rows == 1:
+        s0, s1 = cols, 1  # strides of empty / single-row arrays carry no layout
+    if s1 != 1 and cols > 1:
         raise ValueError("inner dimension must be contiguous")
     if layout == PS_LAYOUT_FIELD_MAJOR:
         nf, nv = X.shape
     else:
         nv, nf = X.shape
-    return ps_matrix(_ptr_of(X), nv, nf, max(int(s0), 1), _dtype_of(X), layout)
+    return ps_matrix(_ptr_of(X), nv, nf, max(int(s0), cols, 1), _dtype_of(X), layout)
 
 
 def stream_ptr(stream) -> int:
