@@ -234,6 +234,37 @@ ps_status ps_timing_read(ps_handle h, const char* kernel, int64_t* launches,
 ps_status ps_probe_minadd_peak(ps_handle h, int32_t variant,
                                double* cmp_per_s);
 
+/* ---------------------------------------------------------------------------
+ * 2-way metrics without any device allocation.  The paper has no counterpart:
+ * this entry point exists for callers that cannot let a library call
+ * cudaMalloc -- services whose device memory is owned in full by their own
+ * allocator or by a fixed budget set at start-up (a framework caching
+ * allocator that must account for every byte, a long-running service that
+ * forbids cudaMalloc/cudaFree after warm-up because they can synchronise the
+ * device and fragment memory).
+ *
+ * Same result as ps_metrics_2way(..., PS_PATH_FP32, ...) on the current CUDA
+ * device, with these limits:
+ *   - V must be PS_F32, PS_LAYOUT_FIELD_MAJOR, ld a multiple of 4, data
+ *     16-byte aligned, 2 <= nv <= PS_STATIC_MAX_NV (65536);
+ *   - V->data and out must be DEVICE memory (no host staging);
+ *   - out: nv*(nv-1)/2 values of out_dtype (PS_F32 or PS_F64), packed as in
+ *     ps_metrics_2way.
+ * Its only scratch (nv FP64 sums) lives in a 512 KiB array inside the
+ * library's device image, held on every GPU that loads the library until the
+ * process exits.  No handle is used and nothing is allocated.  The first call
+ * on a device looks up that array's device address (cudaGetSymbolAddress) and
+ * sets kernel attributes; make that first call before any stream capture.
+ * All calls share the array and it keeps the last call's contents; every call
+ * rewrites the entries it reads, so nothing needs clearing.  Calls that
+ * overlap on the GPU (other streams or host threads) race on the array:
+ * serialise them.  Asynchronous on `stream`.
+ * Errors: PS_ERR_INVALID_ARG for any violated limit (message via
+ * ps_last_error(NULL)); PS_ERR_CUDA for a CUDA failure. */
+#define PS_STATIC_MAX_NV 65536
+ps_status ps_metrics_2way_static(const ps_matrix* V, void* out,
+                                 int32_t out_dtype, ps_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -66,6 +66,7 @@ ps_quantize = _sig("ps_quantize", ctypes.c_int, [_h, _M, _i32, _p, _p, _p])
 ps_timing_enable = _sig("ps_timing_enable", ctypes.c_int, [_h, _i32])
 ps_timing_read = _sig("ps_timing_read", ctypes.c_int,
                       [_h, ctypes.c_char_p, ctypes.POINTER(_i64), ctypes.POINTER(ctypes.c_double)])
+ps_metrics_2way_static = _sig("ps_metrics_2way_static", ctypes.c_int, [_M, _p, _i32, _p])
 ps_probe_minadd_peak = _sig("ps_probe_minadd_peak", ctypes.c_int,
                             [_h, _i32, ctypes.POINTER(ctypes.c_double)])
 
