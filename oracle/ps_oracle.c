@@ -275,8 +275,9 @@ void oracle_quantize(const float* x, int64_t n, int levels, float P,
     volatile float prod = v * r32;
     volatile float shifted = prod + 0.5f;
     float f = floorf(shifted);
-    int32_t l = (int32_t)f;
-    if (l > levels - 1) l = levels - 1;
+    /* min(L-1, .) taken before the integer conversion, which is undefined
+     * for values beyond the int32 range */
+    int32_t l = (f >= (float)(levels - 1)) ? levels - 1 : (int32_t)f;
     if (l < 0) l = 0;
     q[t] = l;
   }
