@@ -52,6 +52,12 @@ def comparisons(w):
     return nf * nv * (nv - 1) * (nv - 2) // 6
 
 
+def oracle_pair_index(nv, i, j):
+    i = np.asarray(i, dtype=np.int64)
+    j = np.asarray(j, dtype=np.int64)
+    return i * (2 * nv - i - 1) // 2 + (j - i - 1)
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -165,6 +171,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-secondary", action="store_true")
+    ap.add_argument("--no-thermo", action="store_true")
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
     ws, rank, local = dist_env()
@@ -307,6 +314,51 @@ def main():
     nz = ref != 0
     max_rel = float(np.max(np.abs(got[nz] - ref[nz]) / ref[nz])) if nz.any() else 0.0
 
+    # ---- thermometer tensor-core path on the same input (2-way only) ----
+    thermo = None
+    if not args.no_thermo and w["way"] == 2 and ws == 1:
+        L = 16
+        def tstep():
+            ps.check(ps.ps_metrics_2way(h.h, ctypes.byref(m), ps.PS_PATH_THERMO, L, out.data_ptr(), out_dtype,
+                                        sptr), h.h)
+        for _ in range(2):
+            tstep()
+        torch.cuda.synchronize()
+        ps.check(ps.ps_timing_enable(h.h, 1), h.h)
+        e0.record(stream)
+        for _ in range(args.steps):
+            tstep()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        tms = e0.elapsed_time(e1) / args.steps
+        kt = {}
+        for name in ("quantize", "thermo_encode", "thermo_gemm"):
+            ps.check(ps.ps_timing_read(h.h, name.encode(), ctypes.byref(n_launch), ctypes.byref(k_ms)), h.h)
+            kt[name] = k_ms.value / max(n_launch.value, 1)
+        ps.check(ps.ps_timing_enable(h.h, 0), h.h)
+        flops = 2.0 * nf * (L - 1) * (nv * (nv - 1) // 2)
+        fp8_peak = 2.0 * float(peaks.get("bf16_tflops", 1900.0)) * 1e12
+        tach = flops / (kt["thermo_gemm"] / 1e3)
+        # quantization error against the FP64 oracle on the original values,
+        # all pairs of the first 4096 vectors
+        ns = 4096
+        ii = np.concatenate([np.full(ns - 1 - i, i) for i in range(ns - 1)])
+        jj = np.concatenate([np.arange(i + 1, ns) for i in range(ns - 1)])
+        gq = out[torch.from_numpy(oracle_pair_index(nv, ii, jj)).cuda()].double().cpu().numpy()
+        import oracle as _or
+        ref = _or.c2_packed(_or.to_vector_major(V[:, :ns]))
+        qerr = np.abs(gq - ref)
+        thermo = {"value": cmp_per_step / (tms / 1e3), "unit": UNIT, "ms_per_step": tms, "levels": L,
+                  "speedup_vs_fp32": ms_step / tms, "kernel_ms": kt,
+                  "roofline": {"bound": "tensor", "achieved": tach / 1e12, "peak": fp8_peak / 1e12,
+                               "unit": "TFLOP/s", "frac": tach / fp8_peak, "traffic": None,
+                               "kernel": "thermo_gemm", "dtype": "fp8 e4m3 0/1, fp32 accumulate",
+                               "peak_basis": "measured bf16 dense burst x 2 (nominal fp8/bf16 ratio), of measured"},
+                  "quantization_error_vs_fp64_oracle": {
+                      "sample": f"all {ns * (ns - 1) // 2} pairs of the first {ns} vectors",
+                      "max_abs": float(qerr.max()), "mean_abs": float(qerr.mean()),
+                      "p99_abs": float(np.percentile(qerr, 99))}}
+
     # ---- secondary: the 3-way workload ----
     secondary = None
     if not args.no_secondary and w["way"] == 2 and ws == 1:
@@ -350,7 +402,7 @@ def main():
                            "parallelism": f"independent instance per rank x{ws}"},
                 "roofline": roofline, "cpu_baseline": cb, "e2e": e2e, "clocks": clk,
                 "gpu_launches": launches_per_step * args.steps,
-                "sampled_max_rel_err": max_rel, "secondary": secondary}
+                "sampled_max_rel_err": max_rel, "thermo_tensor_core": thermo, "secondary": secondary}
         print(json.dumps(line), flush=True)
     h.close()
     if ws > 1:

@@ -162,7 +162,8 @@ struct Prepared {
   bool host_input = false;
 };
 
-ps_status prepare(ps_ctx* h, const ps_matrix& V, cudaStream_t st, bool need_f32, Prepared* P) {
+ps_status prepare(ps_ctx* h, const ps_matrix& V, cudaStream_t st, bool need_f32, Prepared* P,
+                  bool need_sums = true) {
   P->dev = V;
   PtrKind k = PK_DEVICE;
   if (V.nv > 0 && V.nf > 0) {
@@ -177,9 +178,9 @@ ps_status prepare(ps_ctx* h, const ps_matrix& V, cudaStream_t st, bool need_f32,
     P->dev.data = d;
     P->host_input = true;
   }
-  P->S = static_cast<double*>(ws_get(h, WS_SUMS, (size_t)std::max<int64_t>(V.nv, 1) * 8));
-  if (!P->S) return PS_ERR_OOM;
-  {
+  if (need_sums) {
+    P->S = static_cast<double*>(ws_get(h, WS_SUMS, (size_t)std::max<int64_t>(V.nv, 1) * 8));
+    if (!P->S) return PS_ERR_OOM;
     ScopedTimer tm(h, "vector_sums", st);
     PS_CUDA_TRY(h, launch_vector_sums(P->dev, P->S, st));
   }
@@ -229,6 +230,45 @@ ps_status finish(ps_ctx* h, const OutBuf& o, bool any_host, cudaStream_t st) {
     PS_CUDA_TRY(h, cudaMemcpyAsync(o.user, o.dev, o.bytes, cudaMemcpyDeviceToHost, st));
   if (any_host) PS_CUDA_TRY(h, cudaStreamSynchronize(st));
   PS_CUDA_TRY(h, cudaGetLastError());
+  return PS_OK;
+}
+
+// Percentile P of the nonzero entries into the handle's select state.
+ps_status run_percentile(ps_ctx* h, const VF32& v, cudaStream_t st, SelectState** state) {
+  auto* sel = static_cast<unsigned char*>(ws_get(h, WS_AUX1, 2048 * 8 + 256));
+  if (!sel) return PS_ERR_OOM;
+  *state = reinterpret_cast<SelectState*>(sel + 2048 * 8);
+  ScopedTimer tm(h, "quantize", st);
+  PS_CUDA_TRY(h, launch_percentile_nonzero(h, v, 0.999, *state,
+                                           reinterpret_cast<unsigned long long*>(sel), st));
+  return PS_OK;
+}
+
+// Thermometer path of ps_metrics_2way (quantize, encode, tensor-core GEMM).
+ps_status thermo_2way(ps_ctx* h, const VF32& v, int levels, void* out, int out_f64, cudaStream_t st) {
+  SelectState* sel = nullptr;
+  ps_status s = run_percentile(h, v, st, &sel);
+  if (s != PS_OK) return s;
+  const int nv_pad = (int)round_up(v.nv, 256);
+  const int64_t Kpad = thermo_kpad(v.nf, levels);
+  uint8_t* T = static_cast<uint8_t*>(ws_get(h, WS_QUANT, (size_t)nv_pad * Kpad));
+  int* SQ = static_cast<int*>(ws_get(h, WS_AUX2, (size_t)nv_pad * sizeof(int)));
+  int* err = static_cast<int*>(ws_get(h, WS_AUX3, 256));
+  if (!T || !SQ || !err) return PS_ERR_OOM;
+  PS_CUDA_TRY(h, cudaMemsetAsync(err, 0, sizeof(int), st));
+  {
+    ScopedTimer tm(h, "thermo_encode", st);
+    PS_CUDA_TRY(h, launch_level_sums(v, levels, sel, SQ, st));
+    PS_CUDA_TRY(h, launch_thermo_encode(v, levels, sel, T, Kpad, nv_pad, st));
+  }
+  {
+    ScopedTimer tm(h, "thermo_gemm", st);
+    PS_CUDA_TRY(h, launch_thermo_gemm(h, T, Kpad, v.nv, nv_pad, SQ, out, out_f64, err, st));
+  }
+  int herr = 0;
+  PS_CUDA_TRY(h, cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  PS_CUDA_TRY(h, cudaStreamSynchronize(st));
+  if (herr) return fail(h, PS_ERR_TIMEOUT, "tensor-core pipeline wait timed out");
   return PS_OK;
 }
 
@@ -348,8 +388,6 @@ ps_status ps_metrics_2way(ps_handle h, const ps_matrix* V, int32_t path, int32_t
     return fail(h, PS_ERR_INVALID_ARG, "path %d is not a ps_path", path);
   if (path == PS_PATH_THERMO && (levels < 2 || levels > 16))
     return fail(h, PS_ERR_INVALID_ARG, "levels=%d outside [2,16]", levels);
-  if (path == PS_PATH_THERMO)
-    return fail(h, PS_ERR_UNSUPPORTED, "thermometer path not built yet");
   Guard g(h->device);
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   const int64_t npairs = V->nv * (V->nv - 1) / 2;
@@ -358,7 +396,12 @@ ps_status ps_metrics_2way(ps_handle h, const ps_matrix* V, int32_t path, int32_t
   s = resolve_out(h, out, obytes, WS_OUTPUT, &o);
   if (s != PS_OK) return s;
   Prepared P;
-  if (path == PS_PATH_FP32) {
+  if (path == PS_PATH_THERMO) {
+    s = prepare(h, *V, st, true, &P, false);
+    if (s != PS_OK) return s;
+    s = thermo_2way(h, P.f32, levels, o.dev, out_dtype == PS_F64, st);
+    if (s != PS_OK) return s;
+  } else if (path == PS_PATH_FP32) {
     s = prepare(h, *V, st, true, &P);
     if (s != PS_OK) return s;
     ScopedTimer tm(h, "mgemm2", st);
@@ -427,8 +470,31 @@ ps_status ps_threshold_3way(ps_handle h, const ps_matrix* V, float tau, int32_t 
 
 ps_status ps_quantize(ps_handle h, const ps_matrix* V, int32_t levels, float* P_out, uint8_t* q_out,
                       ps_stream stream) {
-  (void)V; (void)levels; (void)P_out; (void)q_out; (void)stream;
-  return fail(h, PS_ERR_UNSUPPORTED, "ps_quantize not built yet");
+  if (!h) return fail(nullptr, PS_ERR_INVALID_ARG, "null handle");
+  ps_status s = check_matrix(h, V, 1);
+  if (s != PS_OK) return s;
+  if (levels < 2 || levels > 16) return fail(h, PS_ERR_INVALID_ARG, "levels=%d outside [2,16]", levels);
+  if (!P_out) return fail(h, PS_ERR_INVALID_ARG, "null P_out");
+  Guard g(h->device);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  Prepared P;
+  s = prepare(h, *V, st, true, &P, false);
+  if (s != PS_OK) return s;
+  SelectState* sel = nullptr;
+  s = run_percentile(h, P.f32, st, &sel);
+  if (s != PS_OK) return s;
+  OutBuf oP;
+  s = resolve_out(h, P_out, sizeof(float), WS_AUX3, &oP);
+  if (s != PS_OK) return s;
+  PS_CUDA_TRY(h, cudaMemcpyAsync(oP.dev, &sel->value, sizeof(float), cudaMemcpyDeviceToDevice, st));
+  OutBuf oq;
+  if (q_out) {
+    s = resolve_out(h, q_out, (size_t)V->nv * V->nf, WS_OUTPUT, &oq);
+    if (s != PS_OK) return s;
+    PS_CUDA_TRY(h, launch_quantize(P.f32, levels, sel, static_cast<uint8_t*>(oq.dev), V->nv, st));
+  }
+  if (oP.host) PS_CUDA_TRY(h, cudaMemcpyAsync(P_out, oP.dev, sizeof(float), cudaMemcpyDeviceToHost, st));
+  return finish(h, oq, P.host_input || oP.host || oq.host, st);
 }
 
 ps_status ps_timing_enable(ps_handle h, int32_t enable) {

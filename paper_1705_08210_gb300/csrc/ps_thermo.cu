@@ -1,0 +1,394 @@
+// ps_thermo.cu -- thermometer-coded min-product on the 5th-generation tensor
+// cores (tcgen05), for quantized data.
+//
+// Not in the paper: with levels a, b in [0, L-1] and the thermometer code of
+// ps_quant.cu, n2(i,j) = sum_q min(a_iq, a_jq) = T_i . T_j, where T is an
+// nv x n_f(L-1) matrix of 0/1.  0 and 1 are exact in FP8 E4M3 and every
+// partial sum is an integer below 2^24, so tcgen05.mma kind::f8f6f4 with FP32
+// accumulation computes n2 exactly.  (kind::i8 does not exist on sm_103a.)
+//
+// Kernel structure (one CTA per SM, persistent, 6 warps):
+//   warp 0        TMA producer: 128 x 128-byte tile of T for rows I and a
+//                 256 x 128-byte tile for rows J per stage (128-byte swizzle),
+//                 4-stage ring guarded by full/empty mbarriers;
+//   warp 1        TMEM owner and MMA issuer: per stage four
+//                 tcgen05.mma (M=128, N=256, K=32) into one of two 256-column
+//                 FP32 accumulators in TMEM; tcgen05.commit frees the stage;
+//   warps 2..5    epilogue: tcgen05.ld of the finished accumulator (each warp
+//                 its TMEM lane quadrant), c2 = 2 n2 / (S_i + S_j) with the
+//                 integer level sums, transposed through shared memory so
+//                 that each store instruction writes one contiguous row
+//                 segment of the packed upper-triangular output.
+// The two accumulators let the epilogue of one tile overlap the MMAs of the
+// next.  Tiles: 128-row block I and 256-column block J with I*128 <
+// (J+1)*256, i.e. only blocks that hold some i < j (Section 3.1's triangle).
+// Every mbarrier wait is bounded (PS_WAIT_NS); on timeout the CTA raises
+// `err`, lets in-flight copies drain, frees its TMEM and returns.
+#include "ps_internal.cuh"
+
+#include <cuda.h>
+
+#include <algorithm>
+#include <mutex>
+
+namespace ps {
+namespace {
+
+constexpr int TM = 128, TN = 256, TKB = 128;  // tile rows, tile cols, K bytes per stage
+constexpr int TSTAGES = 4;
+constexpr int A_BYTES = TM * TKB, B_BYTES = TN * TKB;
+constexpr int NTHREADS = 192;
+constexpr uint32_t TMEM_COLS = 512;  // two 256-column FP32 accumulators
+constexpr unsigned long long PS_WAIT_NS = 2000000000ull;  // 2 s per wait
+
+struct __align__(1024) SmemTC {
+  uint8_t A[TSTAGES][A_BYTES];
+  uint8_t B[TSTAGES][B_BYTES];
+  float xpose[4][32][33];
+  unsigned long long full[TSTAGES];
+  unsigned long long empty[TSTAGES];
+  unsigned long long tfull[2];
+  unsigned long long tempty[2];
+  uint32_t tmem_base;
+  int abort;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ unsigned long long globaltimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(unsigned long long* b, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(unsigned long long* b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b)) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long* b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* b, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait: true when the phase with `parity` completed; false when the
+// CTA is aborting or the time limit passed (then the abort flag is raised).
+__device__ __forceinline__ bool mbar_wait(SmemTC& sm, unsigned long long* b, uint32_t parity,
+                                          int* err) {
+  if (mbar_try_wait(b, parity)) return true;
+  const unsigned long long t0 = globaltimer();
+  for (uint32_t it = 0;; ++it) {
+    if (mbar_try_wait(b, parity)) return true;
+    if ((it & 63) == 0) {
+      if (*(volatile int*)&sm.abort) return false;
+      if (globaltimer() - t0 > PS_WAIT_NS) {
+        *(volatile int*)&sm.abort = 1;
+        atomicExch(err, 1);
+        return false;
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y,
+                                            unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, "
+      "%3}], [%4];" ::"r"(smem_u32(dst)),
+      "l"(map), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// UMMA shared-memory descriptor, K-major operand written by TMA with the
+// 128-byte swizzle: 8-row x 128-byte atoms, 1024 bytes apart (SBO).
+__device__ __forceinline__ uint64_t umma_desc_sw128(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFF);
+  d |= (uint64_t)(1) << 16;                    // LBO (unused for swizzled K-major)
+  d |= (uint64_t)((1024 >> 4) & 0x3FFF) << 32;  // SBO
+  d |= (uint64_t)1 << 46;                      // descriptor version (sm_100)
+  d |= (uint64_t)2 << 61;                      // 128-byte swizzle
+  return d;
+}
+
+// Instruction descriptor: kind::f8f6f4, A = B = E4M3, D = F32, both K-major,
+// M = 128, N = 256.
+constexpr uint32_t IDESC = (1u << 4)                 // D format F32
+                           | (0u << 7) | (0u << 10)  // A, B format E4M3
+                           | ((uint32_t)(TN >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
+
+__device__ __forceinline__ void umma_f8(uint32_t tmem_d, uint64_t ad, uint64_t bd, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+      "l"(ad), "l"(bd), "r"(IDESC), "r"(acc)
+      : "memory");
+}
+__device__ __forceinline__ void umma_commit(unsigned long long* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// 32 lanes x 32 columns of FP32 from TMEM: thread t gets row (lane base + t).
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+      "%12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, "
+      "%30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]),
+        "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]),
+        "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int t = 0; t < 32; ++t) v[t] = __uint_as_float(r[t]);
+}
+
+// Tiles before column block J: sum_{J'<J} min(TI, 2J'+2).
+__device__ __forceinline__ int64_t tiles_before(int J, int TI) {
+  const int64_t c = min(J, TI / 2);
+  return c * (c + 1) + (int64_t)(J - c) * TI;
+}
+__device__ __forceinline__ void tile_of(int64_t t, int TI, int TJ, int& I, int& J) {
+  int lo = 0, hi = TJ;  // largest J with tiles_before(J) <= t
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (tiles_before(mid, TI) <= t) lo = mid; else hi = mid;
+  }
+  J = lo;
+  I = (int)(t - tiles_before(lo, TI));
+}
+
+__device__ __forceinline__ int64_t pair_index(int64_t nv, int64_t i, int64_t j) {
+  return i * (2 * nv - i - 1) / 2 + (j - i - 1);
+}
+
+__global__ void __launch_bounds__(NTHREADS, 1)
+    thermo_gemm_kernel(const __grid_constant__ CUtensorMap mapA,
+                       const __grid_constant__ CUtensorMap mapB, int nkb, int nv, int TI, int TJ,
+                       int64_t ntiles, const int* __restrict__ SQ, void* __restrict__ out,
+                       int out_f64, int* __restrict__ err) {
+  extern __shared__ unsigned char smem_raw[];
+  SmemTC& sm = *reinterpret_cast<SmemTC*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < TSTAGES; ++s) {
+      mbar_init(&sm.full[s], 1);
+      mbar_init(&sm.empty[s], 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(&sm.tfull[a], 1);
+      mbar_init(&sm.tempty[a], 128);
+    }
+    sm.abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&sm.tmem_base)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = sm.tmem_base;
+
+  if (warp == 0) {
+    if (lane == 0) {  // ---------------- TMA producer ----------------
+      int stage = 0;
+      uint32_t phase = 0;
+      bool ok = true;
+      for (int64_t t = blockIdx.x; ok && t < ntiles; t += gridDim.x) {
+        int I, J;
+        tile_of(t, TI, TJ, I, J);
+        for (int kb = 0; kb < nkb; ++kb) {
+          if (!mbar_wait(sm, &sm.empty[stage], phase ^ 1, err)) { ok = false; break; }
+          mbar_arrive_expect_tx(&sm.full[stage], A_BYTES + B_BYTES);
+          tma_load_2d(sm.A[stage], &mapA, kb * TKB, I * TM, &sm.full[stage]);
+          tma_load_2d(sm.B[stage], &mapB, kb * TKB, J * TN, &sm.full[stage]);
+          if (++stage == TSTAGES) { stage = 0; phase ^= 1; }
+        }
+      }
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    if (lane == 0) {  // ---------------- MMA issuer ----------------
+      int stage = 0;
+      uint32_t phase = 0;
+      int acc = 0;
+      uint32_t aphase = 0;
+      bool ok = true;
+      for (int64_t t = blockIdx.x; ok && t < ntiles; t += gridDim.x) {
+        if (!mbar_wait(sm, &sm.tempty[acc], aphase ^ 1, err)) break;
+        tc_fence_after();
+        const uint32_t dcol = tmem + (uint32_t)(acc * TN);
+        for (int kb = 0; kb < nkb; ++kb) {
+          if (!mbar_wait(sm, &sm.full[stage], phase, err)) { ok = false; break; }
+          tc_fence_after();
+          const uint32_t a0 = smem_u32(sm.A[stage]), b0 = smem_u32(sm.B[stage]);
+#pragma unroll
+          for (int kk = 0; kk < TKB / 32; ++kk)
+            umma_f8(dcol, umma_desc_sw128(a0 + kk * 32), umma_desc_sw128(b0 + kk * 32),
+                    (kb | kk) ? 1u : 0u);
+          umma_commit(&sm.empty[stage]);
+          if (++stage == TSTAGES) { stage = 0; phase ^= 1; }
+        }
+        if (!ok) break;
+        umma_commit(&sm.tfull[acc]);
+        if (++acc == 2) { acc = 0; aphase ^= 1; }
+      }
+    }
+    __syncwarp();
+  } else {  // ---------------- epilogue: warps 2..5 ----------------
+    const int quad = warp & 3;  // TMEM lane quadrant this warp may access
+    float(*xp)[33] = sm.xpose[warp - 2];
+    int acc = 0;
+    uint32_t aphase = 0;
+    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+      int I, J;
+      tile_of(t, TI, TJ, I, J);
+      // warp-uniform wait: lane 0 polls, the warp follows its verdict
+      int ok = 0;
+      if (lane == 0) ok = mbar_wait(sm, &sm.tfull[acc], aphase, err) ? 1 : 0;
+      ok = __shfl_sync(0xffffffffu, ok, 0);
+      if (!ok) break;
+      tc_fence_after();
+      const int row0 = I * TM + quad * 32;
+      const int my_row = row0 + lane;
+      const int sq_row = my_row < nv ? SQ[my_row] : 0;
+      for (int ch = 0; ch < TN / 32; ++ch) {
+        float v[32];
+        tmem_ld32(tmem + (uint32_t)(acc * TN + ch * 32) + ((uint32_t)(quad * 32) << 16), v);
+        const int col0 = J * TN + ch * 32;
+        // transpose through shared memory: lane <-> column for the stores
+#pragma unroll
+        for (int c = 0; c < 32; ++c) xp[lane][c] = v[c];
+        __syncwarp();
+        const int j = col0 + lane;
+        const int sq_j = j < nv ? SQ[j] : 0;
+        for (int r = 0; r < 32; ++r) {
+          const int si = __shfl_sync(0xffffffffu, sq_row, r);
+          const int i = row0 + r;
+          if (i >= nv || j >= nv || j <= i) continue;
+          const float n2 = xp[r][lane];
+          const int64_t o = pair_index(nv, i, j);
+          if (out_f64) {
+            const double d = (double)si + (double)sq_j;
+            static_cast<double*>(out)[o] = d == 0.0 ? 0.0 : (2.0 * (double)n2) / d;
+          } else {
+            const float d = (float)(si + sq_j);
+            static_cast<float*>(out)[o] = d == 0.0f ? 0.0f : __fdiv_rn(2.0f * n2, d);
+          }
+        }
+        __syncwarp();
+      }
+      tc_fence_before();
+      mbar_arrive(&sm.tempty[acc]);
+      if (++acc == 2) { acc = 0; aphase ^= 1; }
+    }
+  }
+  __syncthreads();
+  if (*(volatile int*)&sm.abort) {
+    // let copies and MMAs already issued finish before the memory goes away
+    const unsigned long long t0 = globaltimer();
+    while (globaltimer() - t0 < 1000000ull) {
+    }
+  }
+  tc_fence_after();
+  if (warp == 1)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(TMEM_COLS)
+                 : "memory");
+}
+
+// ---- host: tensor maps through the driver entry point ----
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                   const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                   const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn get_encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+    cudaGetLastError();
+  });
+  return fn;
+}
+
+bool make_map(CUtensorMap* m, const uint8_t* T, int64_t Kpad, int rows, int box_rows) {
+  EncodeTiledFn enc = get_encode_fn();
+  if (!enc) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)Kpad, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)Kpad};
+  const cuuint32_t box[2] = {(cuuint32_t)TKB, (cuuint32_t)box_rows};
+  const cuuint32_t estr[2] = {1, 1};
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<uint8_t*>(T), dims, strides, box, estr,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+uint64_t g_thermo_attr_devices = 0;
+
+}  // namespace
+
+cudaError_t launch_thermo_gemm(ps_ctx* h, const uint8_t* T, int64_t Kpad, int nv, int nv_pad,
+                               const int* SQ, void* out, int out_f64, int* err, cudaStream_t s) {
+  if (Kpad % TKB != 0 || nv_pad % TN != 0 || ((uintptr_t)T % 16) != 0)
+    return cudaErrorInvalidValue;
+  const uint64_t bit = 1ull << (h->device & 63);
+  const size_t smem = sizeof(SmemTC) + 1024;
+  if (!(g_thermo_attr_devices & bit)) {
+    cudaError_t e = cudaFuncSetAttribute(thermo_gemm_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    g_thermo_attr_devices |= bit;
+  }
+  CUtensorMap mA, mB;
+  if (!make_map(&mA, T, Kpad, nv_pad, TM) || !make_map(&mB, T, Kpad, nv_pad, TN))
+    return cudaErrorInvalidValue;
+  const int TI = nv_pad / TM, TJ = nv_pad / TN;
+  int64_t ntiles = 0;
+  for (int J = 0; J < TJ; ++J) ntiles += std::min(TI, 2 * J + 2);
+  const int nkb = (int)(Kpad / TKB);
+  const int grid = (int)std::min<int64_t>(ntiles, h->num_sms);
+  thermo_gemm_kernel<<<grid, NTHREADS, smem, s>>>(mA, mB, nkb, nv, TI, TJ, ntiles, SQ, out, out_f64,
+                                                  err);
+  return cudaGetLastError();
+}
+
+}  // namespace ps
