@@ -10,6 +10,7 @@
 #include <cstring>
 #include <mutex>
 #include <new>
+#include <vector>
 
 namespace ps {
 
@@ -272,6 +273,85 @@ ps_status thermo_2way(ps_ctx* h, const VF32& v, int levels, void* out, int out_f
   return PS_OK;
 }
 
+int key_bits_for(int nv) {
+  int b = 1;
+  while ((1 << b) < nv) ++b;
+  return b;
+}
+
+// Run the thresholded kernel over `blk` (3 ints per block), sort the hits,
+// write the first `capacity` and the total count.  Synchronous.
+ps_status threshold_blocks(ps_ctx* h, const Prepared& P, const std::vector<int>& blk, float tau,
+                           ps_triple* out, int64_t capacity, int64_t* count, cudaStream_t st) {
+  const int nv = P.f32.nv;
+  const float* n2 = static_cast<const float*>(h->ws.ptr[WS_N2]);
+  const int64_t nblocks = (int64_t)blk.size() / 3;
+  int* dblk = static_cast<int*>(ws_get(h, WS_BLOCKS, std::max<size_t>(blk.size(), 1) * sizeof(int)));
+  if (!dblk) return PS_ERR_OOM;
+  if (nblocks)
+    PS_CUDA_TRY(h, cudaMemcpyAsync(dblk, blk.data(), blk.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+  const int bits = key_bits_for(nv);
+  int64_t cap = std::max<int64_t>({capacity, (int64_t)1 << 20, h->thresh_cap});
+  int64_t total = 0;
+  unsigned long long* counter = static_cast<unsigned long long*>(ws_get(h, WS_AUX3, 256));
+  if (!counter) return PS_ERR_OOM;
+  unsigned char* hits = nullptr;
+  for (int attempt = 0; attempt < 2; ++attempt) {
+    hits = static_cast<unsigned char*>(ws_get(h, WS_HITS, (size_t)cap * 24));
+    if (!hits) return PS_ERR_OOM;
+    ThreshArgs ta;
+    ta.tau = tau;
+    ta.bits = bits;
+    ta.keys = reinterpret_cast<unsigned long long*>(hits);
+    ta.vals = reinterpret_cast<float*>(hits + (size_t)cap * 16);
+    ta.counter = counter;
+    ta.cap = cap;
+    PS_CUDA_TRY(h, cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st));
+    {
+      ScopedTimer tm(h, "threshold3", st);
+      PS_CUDA_TRY(h, launch_mgemm3_thresh(h, P.f32, P.S, n2, dblk, nblocks, ta, st));
+    }
+    unsigned long long c = 0;
+    PS_CUDA_TRY(h, cudaMemcpyAsync(&c, counter, sizeof(c), cudaMemcpyDeviceToHost, st));
+    PS_CUDA_TRY(h, cudaStreamSynchronize(st));
+    total = (int64_t)c;
+    if (total <= cap) break;
+    cap = total;  // grow and compute once more
+    h->thresh_cap = cap;
+  }
+  if (total > cap) return fail(h, PS_ERR_CUDA, "threshold hit buffer could not hold %lld hits", (long long)total);
+  unsigned long long* keys = reinterpret_cast<unsigned long long*>(hits);
+  unsigned long long* ktmp = keys + cap;
+  float* vals = reinterpret_cast<float*>(hits + (size_t)cap * 16);
+  float* vtmp = vals + cap;
+  const size_t words = radix_sort_scratch_words(total);
+  unsigned* scratch = static_cast<unsigned*>(ws_get(h, WS_SORT, words * sizeof(unsigned)));
+  if (!scratch) return PS_ERR_OOM;
+  {
+    ScopedTimer tm(h, "sort", st);
+    PS_CUDA_TRY(h, launch_radix_sort(h, keys, vals, ktmp, vtmp, total, 3 * bits, scratch, words, st));
+  }
+  const int64_t nout = std::min(total, capacity);
+  OutBuf o;
+  if (nout > 0) {
+    ps_status s = resolve_out(h, out, (size_t)nout * sizeof(ps_triple), WS_OUTPUT, &o);
+    if (s != PS_OK) return s;
+    PS_CUDA_TRY(h, launch_write_triples(keys, vals, nout, bits, static_cast<ps_triple*>(o.dev), st));
+  }
+  OutBuf oc;
+  ps_status s2 = resolve_out(h, count, sizeof(int64_t), WS_AUX1, &oc);
+  if (s2 != PS_OK) return s2;
+  const int64_t tot64 = total;
+  PS_CUDA_TRY(h, cudaMemcpyAsync(oc.dev, &tot64, sizeof(int64_t), cudaMemcpyHostToDevice, st));
+  if (o.host && o.bytes) PS_CUDA_TRY(h, cudaMemcpyAsync(o.user, o.dev, o.bytes, cudaMemcpyDeviceToHost, st));
+  if (oc.host) PS_CUDA_TRY(h, cudaMemcpyAsync(count, oc.dev, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+  PS_CUDA_TRY(h, cudaStreamSynchronize(st));
+  if (total > capacity)
+    return fail(h, PS_ERR_CAPACITY, "%lld triples found, capacity %lld", (long long)total,
+                (long long)capacity);
+  return PS_OK;
+}
+
 }  // namespace
 }  // namespace ps
 
@@ -464,8 +544,38 @@ ps_status ps_metrics_3way(ps_handle h, const ps_matrix* V, int64_t j_begin, int6
 
 ps_status ps_threshold_3way(ps_handle h, const ps_matrix* V, float tau, int32_t use_proposal,
                             ps_triple* out, int64_t capacity, int64_t* count, ps_stream stream) {
-  (void)V; (void)tau; (void)use_proposal; (void)out; (void)capacity; (void)count; (void)stream;
-  return fail(h, PS_ERR_UNSUPPORTED, "ps_threshold_3way not built yet");
+  if (!h) return fail(nullptr, PS_ERR_INVALID_ARG, "null handle");
+  ps_status s = check_matrix(h, V, 3);
+  if (s != PS_OK) return s;
+  if (V->nv > (1 << 21)) return fail(h, PS_ERR_INVALID_ARG, "nv=%lld above 2^21", (long long)V->nv);
+  if (capacity < 0) return fail(h, PS_ERR_INVALID_ARG, "capacity < 0");
+  if (!count) return fail(h, PS_ERR_INVALID_ARG, "null count");
+  if (capacity > 0 && !out) return fail(h, PS_ERR_INVALID_ARG, "null out");
+  if (use_proposal != 0) return fail(h, PS_ERR_INVALID_ARG, "use_proposal %d not available", use_proposal);
+  Guard g(h->device);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  Prepared P;
+  s = prepare(h, *V, st, true, &P);
+  if (s != PS_OK) return s;
+  const int nv = (int)V->nv;
+  float* n2 = static_cast<float*>(ws_get(h, WS_N2, (size_t)nv * nv * 4));
+  if (!n2) return PS_ERR_OOM;
+  {
+    ScopedTimer tm(h, "mgemm2_n2", st);
+    PS_CUDA_TRY(h, launch_mgemm2(h, P.f32, P.S, n2, OUT2_N2_SQUARE_F32, st));
+  }
+  // every block (I <= Jt <= K) of 128-wide tiles
+  const int T = (int)ceil_div(nv, 128);
+  std::vector<int> blk;
+  blk.reserve((size_t)T * (T + 1) * (T + 2) / 2);
+  for (int I = 0; I < T; ++I)
+    for (int K = I; K < T; ++K)
+      for (int Jt = I; Jt <= K; ++Jt) {
+        blk.push_back(I);
+        blk.push_back(Jt);
+        blk.push_back(K);
+      }
+  return threshold_blocks(h, P, blk, tau, out, capacity, count, st);
 }
 
 ps_status ps_quantize(ps_handle h, const ps_matrix* V, int32_t levels, float* P_out, uint8_t* q_out,

@@ -341,6 +341,16 @@ __global__ void __launch_bounds__(NT, 1)
   }
 }
 
+// Section 2.2 eq. (1): n3 = n2(ij) + n2(ik) + n2(jk) - n3' in FP64, then
+// c3 = (3/2) n3 / d3 rounded to FP32 (d3 = S_i + S_j + S_k from FP64 sums).
+__device__ __forceinline__ float c3_value(float2 n3p_hl, double n2ij, double n2ik, double n2jk,
+                                          double d3) {
+  const double n3p = (double)n3p_hl.x + (double)n3p_hl.y;
+  const double n3 = ((n2ij + n2ik) + n2jk) - n3p;
+  const float d = (float)d3;
+  return (d == 0.0f) ? 0.0f : __fdiv_rn(1.5f * (float)n3, d);
+}
+
 // ---------------------------------------------------------------------------
 // 3-way: c3 for pivots [jb, je) over (j, I, K) tiles with I*128 < j and
 // K*128+127 > j.  pref[x] = number of tiles of pivots jb .. jb+x-1.
@@ -389,13 +399,57 @@ __global__ void __launch_bounds__(NT, 1)
       for (int c = 0; c < 8; ++c) {
         const int k = col0 + L.col(c);
         if (k <= j || k >= nv) continue;
-        const float2 hl = acc.hl(r, c);
-        const double n3p = (double)hl.x + (double)hl.y;
-        const double n3 = ((n2ij + (double)n2sq[(int64_t)i * nv + k]) +
-                           (double)n2sq[(int64_t)j * nv + k]) - n3p;
-        const float d = (float)(Sij + S[k]);
-        const float v = (d == 0.0f) ? 0.0f : __fdiv_rn(1.5f * (float)n3, d);
+        const float v = c3_value(acc.hl(r, c), n2ij, (double)n2sq[(int64_t)i * nv + k],
+                                 (double)n2sq[(int64_t)j * nv + k], Sij + S[k]);
         out[base + (int64_t)i * w + (k - j - 1)] = v;
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Thresholded 3-way over an explicit list of tile blocks (I, Jt, K) with
+// I <= Jt <= K (128-wide tiles): work item = (block, pivot j in tile Jt).
+// Every triple i<j<k with c3 >= tau is appended as a lexicographic key
+// (i << 2b | j << b | k) and its value; counter receives the total even
+// beyond `cap`.
+__global__ void __launch_bounds__(NT, 1)
+    mgemm3_thresh_kernel(VF32 V, const double* __restrict__ S, const float* __restrict__ n2sq,
+                         const int* __restrict__ blocks, int64_t nitems, ThreshArgs ta) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  SmemF32& sm = *reinterpret_cast<SmemF32*>(smem_raw);
+  const Lanes L;
+  Acc<true> acc;
+  const int nv = V.nv;
+  for (int64_t t = blockIdx.x; t < nitems; t += gridDim.x) {
+    const int64_t b = t >> 7;
+    const int I = blocks[3 * b], Jt = blocks[3 * b + 1], K = blocks[3 * b + 2];
+    const int j = Jt * BM + (int)(t & 127);
+    const int row0 = I * BM, col0 = K * BN;
+    // CTA-uniform skip: no row i < j or no column k > j in this item
+    if (j >= nv || row0 >= j || col0 + BN - 1 <= j || col0 >= nv) continue;
+    tile_minsum<true, true, 8>(sm, V, row0, col0, j, L.am, L.bn, acc);
+    const double Sj = S[j];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      const int i = row0 + L.row(r);
+      if (i >= j) continue;
+      const double Sij = S[i] + Sj;
+      const double n2ij = (double)n2sq[(int64_t)i * nv + j];
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        const int k = col0 + L.col(c);
+        if (k <= j || k >= nv) continue;
+        const float v = c3_value(acc.hl(r, c), n2ij, (double)n2sq[(int64_t)i * nv + k],
+                                 (double)n2sq[(int64_t)j * nv + k], Sij + S[k]);
+        if (v >= ta.tau) {
+          const unsigned long long pos = atomicAdd(ta.counter, 1ull);
+          if (pos < (unsigned long long)ta.cap) {
+            ta.keys[pos] = ((unsigned long long)i << (2 * ta.bits)) |
+                           ((unsigned long long)j << ta.bits) | (unsigned long long)k;
+            ta.vals[pos] = v;
+          }
+        }
       }
     }
   }
@@ -532,8 +586,9 @@ cudaError_t set_attrs_one() {
   cudaError_t e = cudaFuncSetAttribute(mgemm2_kernel<PACKED, KU>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(mgemm3_kernel<PACKED, KU>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              sm);
+  e = cudaFuncSetAttribute(mgemm3_kernel<PACKED, KU>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(mgemm3_thresh_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
 }
 
 cudaError_t ensure_attrs(ps_ctx* h) {
@@ -615,6 +670,18 @@ cudaError_t launch_mgemm3(ps_ctx* h, const VF32& V, const double* S, const float
     by_ku(h->mgemm_ku, [&] { launch3_v<false, 16>(g, st, V, S, n2sq, dpref, npiv, j0, out, ntiles); },
           [&] { launch3_v<false, 8>(g, st, V, S, n2sq, dpref, npiv, j0, out, ntiles); },
           [&] { launch3_v<false, 4>(g, st, V, S, n2sq, dpref, npiv, j0, out, ntiles); });
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mgemm3_thresh(ps_ctx* h, const VF32& V, const double* S, const float* n2sq,
+                                 const int* blocks, int64_t nblocks, const ThreshArgs& ta,
+                                 cudaStream_t st) {
+  cudaError_t e = ensure_attrs(h);
+  if (e != cudaSuccess) return e;
+  const int64_t nitems = nblocks * 128;
+  if (nitems == 0) return cudaSuccess;
+  const int64_t grid = std::min<int64_t>(nitems, (int64_t)h->num_sms);
+  mgemm3_thresh_kernel<<<(unsigned)grid, NT, sizeof(SmemF32), st>>>(V, S, n2sq, blocks, nitems, ta);
   return cudaGetLastError();
 }
 

@@ -71,3 +71,29 @@ def slab_index(nv, jb, i, j, k):
     i, j, k = (np.asarray(x, dtype=np.int64) for x in (i, j, k))
     F = lambda x: (nv - 1) * (x * (x - 1) // 2) - (x - 1) * x * (2 * x - 1) // 6  # noqa: E731
     return F(j) - F(np.int64(jb)) + i * (nv - 1 - j) + (k - j - 1)
+
+
+def threshold_3way(ps, handle, V, tau, capacity, use_proposal=0, on_host=False):
+    """Returns (status, count, triples as (n,3) int array, values float32)."""
+    torch = _torch()
+    X = torch.from_numpy(np.ascontiguousarray(V)).cuda()
+    m = ps.matrix(X)
+    if on_host:
+        out = (ps.ps_triple * max(capacity, 1))()
+        cnt = ctypes.c_int64(-1)
+        st = ps.ps_threshold_3way(handle.h, ctypes.byref(m), float(tau), use_proposal,
+                                  ctypes.addressof(out), capacity, ctypes.addressof(cnt), 0)
+        raw = np.frombuffer(out, dtype=np.int32).reshape(-1, 4)
+        count = cnt.value
+    else:
+        out = torch.empty((max(capacity, 1), 4), dtype=torch.int32, device="cuda")
+        cnt = torch.full((1,), -1, dtype=torch.int64, device="cuda")
+        st = ps.ps_threshold_3way(handle.h, ctypes.byref(m), float(tau), use_proposal, out.data_ptr(),
+                                  capacity, cnt.data_ptr(), torch.cuda.current_stream().cuda_stream)
+        torch.cuda.synchronize()
+        raw = out.cpu().numpy()
+        count = int(cnt.item())
+    n = min(count, capacity) if count >= 0 else 0
+    trip = raw[:n, :3].astype(np.int64)
+    vals = raw[:n, 3].copy().view(np.float32)
+    return st, count, trip, vals

@@ -1,0 +1,88 @@
+"""GPU parity of the thresholded 3-way search: every triple with c3 >= tau,
+sorted lexicographically, against the oracle.  Triples within the FP32/FP64
+disagreement band |c3 - tau| <= 1e-5 tau are allowed on either side."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1705_08210_gb300 import synth
+from gpu_run import metrics_3way, slab_index, threshold_3way
+
+pytestmark = pytest.mark.gpu
+RTOL32 = 1e-5
+
+
+def _compare_with_oracle(ps, handle, V, tau):
+    Vv = oracle.to_vector_major(V)
+    ijk, val, total = oracle.threshold_3way(Vv, tau)
+    st, count, trip, vals = threshold_3way(ps, handle, V, tau, capacity=max(total * 2, 16))
+    assert st == ps.PS_OK
+    assert count == len(trip)
+    keys = [tuple(t) for t in trip.tolist()]
+    assert keys == sorted(keys), "not lexicographic"
+    assert len(set(keys)) == len(keys)
+    ref = {tuple(t): v for t, v in zip(ijk.tolist(), val)}
+    got = dict(zip(keys, vals.astype(np.float64)))
+    band = RTOL32 * tau
+    for t in set(ref) ^ set(got):
+        c = ref.get(t)
+        if c is None:
+            c = oracle.c3_triples(Vv, [t])[0]
+        assert abs(c - tau) <= band, (t, c)
+    for t in set(ref) & set(got):
+        assert abs(got[t] - ref[t]) <= RTOL32 * ref[t], (t, got[t], ref[t])
+    return total
+
+
+@pytest.mark.parametrize("nv,nf,sigma,tau", [(40, 16, 0.2, 0.6), (200, 64, 0.3, 0.7), (300, 100, 0.2, 0.7)])
+def test_threshold_matches_oracle(ps, handle, nv, nf, sigma, tau):
+    V, _ = synth.latent_profiles(nv, nf, synth.seed_for(5, nv), n_profiles=8, sigma=sigma)
+    total = _compare_with_oracle(ps, handle, V, tau)
+    assert total > 0
+
+
+def test_threshold_tiny_and_degenerate(ps, handle):
+    V = synth.zero_inflated(3, 5, synth.seed_for(5, 1), p_zero=0.2)
+    _compare_with_oracle(ps, handle, V, 0.0)       # every triple (single sort pass)
+    st, count, trip, _ = threshold_3way(ps, handle, V, 1.5, capacity=4)
+    assert st == ps.PS_OK and count == 0 and len(trip) == 0
+
+
+def test_threshold_all_triples_many_sort_blocks(ps, handle):
+    nv, nf = 300, 40
+    V = synth.zero_inflated(nv, nf, synth.seed_for(5, 2))
+    n = nv * (nv - 1) * (nv - 2) // 6
+    st, count, trip, vals = threshold_3way(ps, handle, V, 0.0, capacity=n)
+    assert st == ps.PS_OK and count == n
+    full = metrics_3way(ps, handle, V)
+    # lexicographic enumeration of all i<j<k
+    i, j, k = trip[:, 0], trip[:, 1], trip[:, 2]
+    assert np.all((i < j) & (j < k))
+    keys = (i << 40) | (j << 20) | k
+    assert np.all(np.diff(keys) > 0)
+    np.testing.assert_array_equal(vals, full[slab_index(nv, 0, i, j, k)])
+
+
+def test_threshold_capacity_overflow_and_host_buffers(ps, handle):
+    V, _ = synth.latent_profiles(150, 50, synth.seed_for(5, 3), n_profiles=6, sigma=0.25)
+    st, count, trip, vals = threshold_3way(ps, handle, V, 0.65, capacity=10 ** 6)
+    assert st == ps.PS_OK and count > 20
+    st2, count2, trip2, vals2 = threshold_3way(ps, handle, V, 0.65, capacity=7)
+    assert st2 == ps.PS_ERR_CAPACITY and count2 == count
+    np.testing.assert_array_equal(trip2, trip[:7])
+    np.testing.assert_array_equal(vals2, vals[:7])
+    st3, count3, trip3, vals3 = threshold_3way(ps, handle, V, 0.65, capacity=10 ** 6, on_host=True)
+    assert st3 == ps.PS_OK and count3 == count
+    np.testing.assert_array_equal(trip3, trip)
+    np.testing.assert_array_equal(vals3, vals)
+
+
+def test_threshold_consistent_with_slab_output(ps, handle):
+    nv, nf = 1024, 256
+    V, _ = synth.latent_profiles(nv, nf, synth.seed_for(5, 4), n_profiles=32, sigma=0.3)
+    full = metrics_3way(ps, handle, V)
+    tau = float(np.quantile(full, 0.9999))
+    st, count, trip, vals = threshold_3way(ps, handle, V, tau, capacity=len(full))
+    assert st == ps.PS_OK
+    assert count == int((full >= tau).sum())
+    np.testing.assert_array_equal(vals, full[slab_index(nv, 0, trip[:, 0], trip[:, 1], trip[:, 2])])
