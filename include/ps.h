@@ -195,6 +195,51 @@ ps_status ps_threshold_3way(ps_handle h, const ps_matrix* V, float tau,
                             ps_stream stream);
 
 /* ---------------------------------------------------------------------------
+ * Batched uneven instances (not in the paper, whose unit of work is one
+ * large decomposed problem, Section 4).  Each problem: */
+typedef struct {
+  ps_matrix V;       /* PS_F32, PS_LAYOUT_FIELD_MAJOR, ld % 4 == 0, 16-byte
+                        aligned DEVICE memory; 2-way nv >= 2, 3-way nv >= 3,
+                        nv <= 2^20 */
+  int32_t way;       /* 2 or 3 */
+  int32_t out_dtype; /* 2-way: PS_F32 or PS_F64; 3-way: PS_F32 */
+  void* out;         /* DEVICE memory: 2-way nv*(nv-1)/2 packed pairs (as
+                        ps_metrics_2way); 3-way ps_slab_size(nv, 0, nv) floats
+                        (all pivots, as ps_metrics_3way) */
+} ps_problem;
+
+#define PS_BATCH_PERSISTENT 0   /* one persistent launch, CUDA graph */
+#define PS_BATCH_PER_INSTANCE 1 /* one ps_metrics_2way/3way call each */
+
+/* All problems of the batch.  PS_BATCH_PERSISTENT: one persistent kernel
+ * whose CTAs take work items (per-vector sum blocks, 2-way tiles, n2-table
+ * tiles, 3-way pivot tiles of every problem, longest first) from an atomic
+ * queue; a tile's epilogue waits for the items it depends on, which sit
+ * earlier in the queue.  The launch is captured once per batch (same
+ * shapes, pointers and kernel variant) into a CUDA graph kept in the handle
+ * and replayed on later calls; the handle also keeps that batch's device
+ * state (sums, n2 tables, work list) until ps_destroy.  Results are
+ * bit-identical to PS_BATCH_PER_INSTANCE, which is the comparison point.
+ * The kernel variant is the one ps_autotune_batched chose for these shapes,
+ * else the default.  Synchronises `stream` (it reads the launch's error flag).
+ * Errors: PS_ERR_INVALID_ARG for a problem outside the limits above;
+ *   PS_ERR_TIMEOUT if a dependency wait inside the launch ran out (2 s). */
+ps_status ps_metrics_batched(ps_handle h, const ps_problem* probs, int32_t n,
+                             int32_t mode, ps_stream stream);
+
+/* Autotuner of the batched launch: times every kernel configuration
+ * (accumulate form: packed f32x2 or scalar adds; k-unroll depth 16, 8 or 4)
+ * on these problems, keeps the fastest for this batch shape in the handle
+ * and appends {"shape_signature", "variant", "ms"} as one JSON line to
+ * cache_path (if not NULL).  If cache_path already holds this shape
+ * signature, its variant is used without measuring.  choice (if not NULL)
+ * receives a readable description of the chosen configuration.
+ * Errors: as ps_metrics_batched. */
+ps_status ps_autotune_batched(ps_handle h, const ps_problem* probs, int32_t n,
+                              const char* cache_path, char* choice,
+                              int32_t choice_len, ps_stream stream);
+
+/* ---------------------------------------------------------------------------
  * Quantizer of the thermometer path (not in the paper).
  *   P      : the nearest-rank 99.9th percentile of the nonzero entries
  *            (rank ceil(0.999*m) of m nonzeros, ascending, 1-based);
@@ -218,7 +263,7 @@ ps_status ps_quantize(ps_handle h, const ps_matrix* V, int32_t levels,
  * ps_timing_read synchronises on the recorded events of `kernel` and returns
  * their number and summed duration.  Kernel names: "vector_sums", "pack",
  * "mgemm2", "mgemm2_f64", "mgemm2_n2", "mgemm3", "quantize", "thermo_encode",
- * "thermo_gemm", "threshold3", "sort".
+ * "thermo_gemm", "threshold3", "sort", "batched".
  * Errors: PS_ERR_INVALID_ARG for null arguments. */
 ps_status ps_timing_enable(ps_handle h, int32_t enable);
 ps_status ps_timing_read(ps_handle h, const char* kernel, int64_t* launches,

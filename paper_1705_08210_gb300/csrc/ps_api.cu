@@ -425,6 +425,7 @@ ps_status ps_destroy(ps_handle h) {
     Guard g(h->device);
     cudaDeviceSynchronize();
     timing_clear(h);
+    batch_state_free(h);
     for (int s = 0; s < WS_NUM_SLOTS; ++s)
       if (h->ws.ptr[s]) cudaFree(h->ws.ptr[s]);
   }

@@ -1,0 +1,350 @@
+// ps_batch.cu -- many independent 2-way / 3-way problems in one persistent
+// launch, captured once per batch in a CUDA graph, and the autotuner that
+// picks the kernel variant of that launch.
+//
+// Not in the paper (its unit of work is one large decomposed problem, §4).
+// Small problems launched one by one leave most SMs idle (a 256-vector 2-way
+// instance has 3 tiles of 128 x 128 for 152 SMs); the batched launch puts the
+// tiles of every problem in one work queue (ps_mgemm.cu, batched_kernel).
+#include "ps_internal.cuh"
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+namespace ps {
+
+struct CachedBatch {
+  cudaGraphExec_t exec = nullptr;
+  void* mem = nullptr;  // S, n2 tables, problem and item arrays, counters
+  int* counters = nullptr;
+  int nprob = 0;
+  int nitems = 0;
+};
+
+struct BatchState {
+  std::map<uint64_t, CachedBatch> graphs;  // key: problems + pointers + variant
+  std::map<uint64_t, int> tuned;           // key: shapes only -> variant code
+};
+
+namespace {
+
+uint64_t fnv(uint64_t h, const void* p, size_t n) {
+  const unsigned char* c = static_cast<const unsigned char*>(p);
+  for (size_t i = 0; i < n; ++i) {
+    h ^= c[i];
+    h *= 1099511628211ull;
+  }
+  return h;
+}
+
+uint64_t shape_signature(const ps_problem* probs, int n) {
+  uint64_t h = 1469598103934665603ull;
+  for (int t = 0; t < n; ++t) {
+    const int64_t f[4] = {probs[t].V.nv, probs[t].V.nf, probs[t].way, probs[t].out_dtype};
+    h = fnv(h, f, sizeof(f));
+  }
+  return h;
+}
+
+uint64_t full_signature(const ps_problem* probs, int n, int variant) {
+  uint64_t h = shape_signature(probs, n);
+  for (int t = 0; t < n; ++t) {
+    const uintptr_t f[3] = {(uintptr_t)probs[t].V.data, (uintptr_t)probs[t].out,
+                            (uintptr_t)probs[t].V.ld};
+    h = fnv(h, f, sizeof(f));
+  }
+  return fnv(h, &variant, sizeof(variant));
+}
+
+// variant code: packed * 100 + ku
+int variant_code(int packed, int ku) { return packed * 100 + ku; }
+const int kVariants[6] = {108, 116, 104, 8, 16, 4};
+
+bool is_device(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+ps_status check_problems(ps_ctx* h, const ps_problem* probs, int n) {
+  if (!probs || n <= 0) return fail(h, PS_ERR_INVALID_ARG, "batched: %d problems", n);
+  for (int t = 0; t < n; ++t) {
+    const ps_problem& p = probs[t];
+    const ps_matrix& V = p.V;
+    if (p.way != 2 && p.way != 3)
+      return fail(h, PS_ERR_INVALID_ARG, "problem %d: way %d", t, p.way);
+    if (V.nv < p.way || V.nv > (1 << 20) || V.nf < 0 || V.nf > (1 << 30))
+      return fail(h, PS_ERR_INVALID_ARG, "problem %d: nv=%lld nf=%lld", t, (long long)V.nv,
+                  (long long)V.nf);
+    if (V.dtype != PS_F32 || V.layout != PS_LAYOUT_FIELD_MAJOR || V.ld < V.nv || V.ld % 4 != 0)
+      return fail(h, PS_ERR_INVALID_ARG,
+                  "problem %d: batched problems need FP32 field-major input, ld %% 4 == 0", t);
+    if (!p.out || (V.nf > 0 && (!V.data || ((uintptr_t)V.data % 16) != 0)))
+      return fail(h, PS_ERR_INVALID_ARG, "problem %d: null or misaligned pointer", t);
+    if ((p.way == 2 && p.out_dtype != PS_F32 && p.out_dtype != PS_F64) ||
+        (p.way == 3 && p.out_dtype != PS_F32))
+      return fail(h, PS_ERR_INVALID_ARG, "problem %d: out_dtype %d", t, p.out_dtype);
+    if ((V.nf > 0 && !is_device(V.data)) || !is_device(p.out))
+      return fail(h, PS_ERR_INVALID_ARG, "problem %d: batched buffers must be device memory", t);
+  }
+  return PS_OK;
+}
+
+int64_t tiles3_of_pivot(int nv, int j) {
+  const int64_t Tk = (nv + 127) / 128;
+  const int64_t nI = (j + 127) / 128;
+  const int64_t nK = (j + 1 < nv) ? (Tk - (j + 1) / 128) : 0;
+  return nI * nK;
+}
+
+// Build the work list and device state of one batch and capture its graph.
+ps_status build_batch(ps_ctx* h, const ps_problem* probs, int n, int variant, CachedBatch* cb) {
+  std::vector<BatchProb> bp(n);
+  size_t off_S = 0, off_n2 = 0;
+  std::vector<size_t> oS(n), oN(n);
+  for (int t = 0; t < n; ++t) {
+    oS[t] = off_S;
+    off_S += (size_t)round_up(probs[t].V.nv, 32);
+    oN[t] = off_n2;
+    if (probs[t].way == 3) off_n2 += (size_t)probs[t].V.nv * probs[t].V.nv;
+  }
+  // items: sums | 2-way tiles + n2 tiles | 3-way tiles; groups longest-first
+  std::vector<BatchItem> sums, mid, tail;
+  for (int t = 0; t < n; ++t) {
+    const int nv = (int)probs[t].V.nv;
+    const int nsb = (int)ceil_div(nv, 32);
+    for (int b = 0; b < nsb; ++b) sums.push_back({t, BK_SUMS, b, 0});
+    const int T = (int)ceil_div(nv, 128);
+    for (int I = 0; I < T; ++I)
+      for (int J = I; J < T; ++J) mid.push_back({t, probs[t].way == 2 ? BK_TILE2 : BK_N2, I, J});
+    if (probs[t].way == 3)
+      for (int j = 0; j < nv; ++j) {
+        const int64_t c = tiles3_of_pivot(nv, j);
+        for (int64_t u = 0; u < c; ++u) tail.push_back({t, BK_TILE3, j, (int)u});
+      }
+  }
+  auto by_cost = [&](const BatchItem& a, const BatchItem& b) {
+    return probs[a.prob].V.nf > probs[b.prob].V.nf;
+  };
+  std::stable_sort(mid.begin(), mid.end(), by_cost);
+  std::stable_sort(tail.begin(), tail.end(), by_cost);
+  std::vector<BatchItem> items;
+  items.reserve(sums.size() + mid.size() + tail.size());
+  items.insert(items.end(), sums.begin(), sums.end());
+  items.insert(items.end(), mid.begin(), mid.end());
+  items.insert(items.end(), tail.begin(), tail.end());
+  if (items.size() > 0x7fffffff) return fail(h, PS_ERR_INVALID_ARG, "batched: too many work items");
+
+  const size_t bytes_S = round_up((int64_t)off_S * 8, 256);
+  const size_t bytes_n2 = round_up((int64_t)off_n2 * 4, 256);
+  const size_t bytes_p = round_up((int64_t)n * sizeof(BatchProb), 256);
+  const size_t bytes_i = round_up((int64_t)items.size() * sizeof(BatchItem), 256);
+  const size_t bytes_c = round_up((int64_t)(2 + 2 * n) * sizeof(int), 256);
+  char* mem = nullptr;
+  cudaError_t e = cudaMalloc(&mem, bytes_S + bytes_n2 + bytes_p + bytes_i + bytes_c);
+  if (e != cudaSuccess) return cuda_fail(h, e, "batched state");
+  cb->mem = mem;
+  double* S = reinterpret_cast<double*>(mem);
+  float* N2 = reinterpret_cast<float*>(mem + bytes_S);
+  BatchProb* dprob = reinterpret_cast<BatchProb*>(mem + bytes_S + bytes_n2);
+  BatchItem* ditems = reinterpret_cast<BatchItem*>(mem + bytes_S + bytes_n2 + bytes_p);
+  int* counters = reinterpret_cast<int*>(mem + bytes_S + bytes_n2 + bytes_p + bytes_i);
+  for (int t = 0; t < n; ++t) {
+    const ps_problem& p = probs[t];
+    BatchProb& q = bp[t];
+    q.v = VF32{static_cast<const float*>(p.V.data), p.V.ld, (int)p.V.nv, (int)p.V.nf};
+    q.S = S + oS[t];
+    q.n2 = p.way == 3 ? N2 + oN[t] : nullptr;
+    q.out = p.out;
+    q.way = p.way;
+    q.out_f64 = p.out_dtype == PS_F64;
+    q.nsum_blocks = (int)ceil_div(p.V.nv, 32);
+    const int64_t T = ceil_div(p.V.nv, 128);
+    q.n2_tiles = p.way == 3 ? (int)(T * (T + 1) / 2) : 0;
+  }
+  PS_CUDA_TRY(h, cudaMemcpy(dprob, bp.data(), n * sizeof(BatchProb), cudaMemcpyHostToDevice));
+  PS_CUDA_TRY(h, cudaMemcpy(ditems, items.data(), items.size() * sizeof(BatchItem),
+                            cudaMemcpyHostToDevice));
+  cb->counters = counters;
+  cb->nprob = n;
+  cb->nitems = (int)items.size();
+
+  // attributes are set outside the capture
+  PS_CUDA_TRY(h, launch_batched(h, variant / 100, variant % 100, dprob, n, ditems, 0, counters, 0));
+  cudaStream_t cs;
+  PS_CUDA_TRY(h, cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  cudaGraph_t g = nullptr;
+  e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    cudaMemsetAsync(counters, 0, (2 + 2 * n) * sizeof(int), cs);
+    launch_batched(h, variant / 100, variant % 100, dprob, n, ditems, cb->nitems, counters, cs);
+    e = cudaStreamEndCapture(cs, &g);
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&cb->exec, g, 0);
+  if (g) cudaGraphDestroy(g);
+  cudaStreamDestroy(cs);
+  if (e != cudaSuccess) return cuda_fail(h, e, "batched graph capture");
+  return PS_OK;
+}
+
+ps_status run_graph(ps_ctx* h, const ps_problem* probs, int n, int variant, cudaStream_t st) {
+  if (!h->batch) h->batch = new BatchState();
+  const uint64_t key = full_signature(probs, n, variant);
+  auto it = h->batch->graphs.find(key);
+  if (it == h->batch->graphs.end()) {
+    CachedBatch cb;
+    ps_status s = build_batch(h, probs, n, variant, &cb);
+    if (s != PS_OK) {
+      if (cb.exec) cudaGraphExecDestroy(cb.exec);
+      if (cb.mem) cudaFree(cb.mem);
+      return s;
+    }
+    it = h->batch->graphs.emplace(key, cb).first;
+  }
+  {
+    ScopedTimer tm(h, "batched", st);
+    PS_CUDA_TRY(h, cudaGraphLaunch(it->second.exec, st));
+  }
+  int herr = 0;
+  PS_CUDA_TRY(h, cudaMemcpyAsync(&herr, it->second.counters + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
+  PS_CUDA_TRY(h, cudaStreamSynchronize(st));
+  if (herr) return fail(h, PS_ERR_TIMEOUT, "batched launch: a dependency wait timed out");
+  return PS_OK;
+}
+
+int default_variant(ps_ctx* h) { return variant_code(h->mgemm_packed_add, h->mgemm_ku); }
+
+}  // namespace
+
+void batch_state_free(ps_ctx* h) {
+  if (!h->batch) return;
+  for (auto& kv : h->batch->graphs) {
+    if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+    if (kv.second.mem) cudaFree(kv.second.mem);
+  }
+  delete h->batch;
+  h->batch = nullptr;
+}
+
+}  // namespace ps
+
+using namespace ps;
+
+extern "C" ps_status ps_metrics_batched(ps_handle h, const ps_problem* probs, int32_t n, int32_t mode,
+                                        ps_stream stream) {
+  if (!h) return fail(nullptr, PS_ERR_INVALID_ARG, "null handle");
+  if (mode != PS_BATCH_PERSISTENT && mode != PS_BATCH_PER_INSTANCE)
+    return fail(h, PS_ERR_INVALID_ARG, "batched mode %d", mode);
+  int prev = -1;
+  cudaGetDevice(&prev);
+  if (prev != h->device) cudaSetDevice(h->device);
+  ps_status s = check_problems(h, probs, n);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (s == PS_OK) {
+    if (mode == PS_BATCH_PER_INSTANCE) {
+      for (int t = 0; t < n && s == PS_OK; ++t) {
+        if (probs[t].way == 2)
+          s = ps_metrics_2way(h, &probs[t].V, PS_PATH_FP32, 0, probs[t].out, probs[t].out_dtype, stream);
+        else
+          s = ps_metrics_3way(h, &probs[t].V, 0, probs[t].V.nv, static_cast<float*>(probs[t].out),
+                              stream);
+      }
+    } else {
+      int variant = default_variant(h);
+      if (h->batch) {
+        auto it = h->batch->tuned.find(shape_signature(probs, n));
+        if (it != h->batch->tuned.end()) variant = it->second;
+      }
+      s = run_graph(h, probs, n, variant, st);
+    }
+  }
+  if (prev >= 0 && prev != h->device) cudaSetDevice(prev);
+  return s;
+}
+
+extern "C" ps_status ps_autotune_batched(ps_handle h, const ps_problem* probs, int32_t n,
+                                         const char* cache_path, char* choice, int32_t choice_len,
+                                         ps_stream stream) {
+  if (!h) return fail(nullptr, PS_ERR_INVALID_ARG, "null handle");
+  ps_status s = check_problems(h, probs, n);
+  if (s != PS_OK) return s;
+  if (!h->batch) h->batch = new BatchState();
+  const uint64_t sig = shape_signature(probs, n);
+  char sigs[32];
+  snprintf(sigs, sizeof(sigs), "%016llx", (unsigned long long)sig);
+  int best = -1;
+  // a cache hit skips the measurement
+  if (cache_path) {
+    if (FILE* f = fopen(cache_path, "r")) {
+      char line[1024];
+      while (fgets(line, sizeof(line), f)) {
+        const char* p = strstr(line, sigs);
+        const char* v = strstr(line, "\"variant\": ");
+        if (p && v) best = atoi(v + 11);
+      }
+      fclose(f);
+    }
+  }
+  std::string detail;
+  if (best < 0) {
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    cudaEvent_t e0, e1;
+    PS_CUDA_TRY(h, cudaEventCreate(&e0));
+    PS_CUDA_TRY(h, cudaEventCreate(&e1));
+    float best_ms = 1e30f;
+    for (int vc : kVariants) {
+      s = run_graph(h, probs, n, vc, st);  // build + warm up
+      if (s != PS_OK) break;
+      float ms_min = 1e30f;
+      for (int rep = 0; rep < 2 && s == PS_OK; ++rep) {
+        cudaEventRecord(e0, st);
+        s = run_graph(h, probs, n, vc, st);
+        cudaEventRecord(e1, st);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        ms_min = std::min(ms_min, ms);
+      }
+      char buf[64];
+      snprintf(buf, sizeof(buf), "%s\"%d\": %.3f", detail.empty() ? "" : ", ", vc, ms_min);
+      detail += buf;
+      if (ms_min < best_ms) {
+        best_ms = ms_min;
+        best = vc;
+      }
+      // keep only the graph of the winner so far
+      for (auto it = h->batch->graphs.begin(); it != h->batch->graphs.end();) {
+        if (it->first == full_signature(probs, n, vc) && vc != best) {
+          cudaGraphExecDestroy(it->second.exec);
+          cudaFree(it->second.mem);
+          it = h->batch->graphs.erase(it);
+        } else {
+          ++it;
+        }
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (s != PS_OK) return s;
+    if (cache_path) {
+      if (FILE* f = fopen(cache_path, "a")) {
+        fprintf(f, "{\"shape_signature\": \"%s\", \"problems\": %d, \"variant\": %d, \"ms\": {%s}}\n",
+                sigs, n, best, detail.c_str());
+        fclose(f);
+      }
+    }
+  }
+  h->batch->tuned[sig] = best;
+  if (choice && choice_len > 0) {
+    snprintf(choice, (size_t)choice_len, "%s add, %d-step unroll%s",
+             best / 100 ? "packed f32x2" : "scalar", best % 100, detail.empty() ? " (cached)" : "");
+  }
+  return PS_OK;
+}

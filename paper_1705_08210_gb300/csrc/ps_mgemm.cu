@@ -456,6 +456,158 @@ __global__ void __launch_bounds__(NT, 1)
 }
 
 // ---------------------------------------------------------------------------
+// Batched persistent kernel: many independent problems of uneven size in one
+// launch.  CTAs take items from an atomic work queue over a list ordered
+//   [sums blocks] [2-way tiles + n2-table tiles] [3-way pivot tiles],
+// each group longest-first.  A tile's epilogue waits (bounded) for its
+// problem's sums, a 3-way tile's epilogue for its problem's n2 table; every
+// item it waits on sits earlier in the queue and has therefore been taken by
+// a running CTA that waits on nothing later, so the waits always end.
+__device__ __forceinline__ int ld_acquire(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Thread 0 waits until *ctr >= target (2 s limit); the CTA follows its verdict.
+__device__ __forceinline__ bool cta_wait_count(const int* ctr, int target, int* err, int* s_flag) {
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    if (ld_acquire(ctr) < target) {
+      unsigned long long t0;
+      asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t0));
+      while (ld_acquire(ctr) < target) {
+        unsigned long long t1;
+        asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t1));
+        if (t1 - t0 > 2000000000ull || *(volatile int*)err) {
+          atomicExch(err, 1);
+          ok = 0;
+          break;
+        }
+        __nanosleep(256);
+      }
+    }
+    *s_flag = ok;
+  }
+  __syncthreads();
+  const bool ok = *s_flag != 0;
+  __syncthreads();
+  return ok;
+}
+
+__device__ __forceinline__ void cta_signal(int* ctr) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(ctr, 1);
+  }
+}
+
+template <bool PACKED, int KU>
+__global__ void __launch_bounds__(NT, 1)
+    batched_kernel(const BatchProb* __restrict__ probs, int nprob, const BatchItem* __restrict__ items,
+                   int nitems, int* __restrict__ counters) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  SmemF32& sm = *reinterpret_cast<SmemF32*>(smem_raw);
+  __shared__ int s_item, s_flag;
+  __shared__ double s_part[8][33];
+  const Lanes L;
+  Acc<PACKED> acc;
+  int* err = counters + 1;
+  int* sums_done = counters + 2;
+  int* n2_done = counters + 2 + nprob;
+  for (;;) {
+    if (threadIdx.x == 0) s_item = atomicAdd(&counters[0], 1);
+    __syncthreads();
+    const int it = s_item;
+    __syncthreads();
+    if (it >= nitems) break;
+    const BatchItem w = items[it];
+    const BatchProb p = probs[w.prob];
+    const VF32 V = p.v;
+    const int nv = V.nv;
+    if (w.kind == BK_SUMS) {
+      // same fixed summation order as vector_sums_fm
+      const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+      const int i = w.a * 32 + lane;
+      double sacc = 0.0;
+      if (i < nv)
+        for (int q = warp; q < V.nf; q += 8) sacc += (double)__ldcg(V.p + (int64_t)q * V.ld + i);
+      s_part[warp][lane] = sacc;
+      __syncthreads();
+      if (warp == 0 && i < nv) {
+        double t = s_part[0][lane];
+#pragma unroll
+        for (int u = 1; u < 8; ++u) t += s_part[u][lane];
+        p.S[i] = t;
+      }
+      cta_signal(&sums_done[w.prob]);
+      continue;
+    }
+    if (w.kind == BK_TILE2 || w.kind == BK_N2) {
+      const int row0 = w.a * BM, col0 = w.b * BN;
+      tile_minsum<false, PACKED, KU>(sm, V, row0, col0, 0, L.am, L.bn, acc);
+      if (!cta_wait_count(&sums_done[w.prob], p.nsum_blocks, err, &s_flag)) continue;
+#pragma unroll
+      for (int r = 0; r < 8; ++r) {
+        const int i = row0 + L.row(r);
+        if (i >= nv) continue;
+        const double Si = __ldcg(p.S + i);
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          const int j = col0 + L.col(c);
+          if (j <= i || j >= nv) continue;
+          const float2 hl = acc.hl(r, c);
+          if (w.kind == BK_N2) {
+            const float n2 = __fadd_rn(hl.x, hl.y);
+            p.n2[(int64_t)i * nv + j] = n2;
+            p.n2[(int64_t)j * nv + i] = n2;
+          } else if (p.out_f64) {
+            const double n2 = (double)hl.x + (double)hl.y;
+            const double d = Si + __ldcg(p.S + j);
+            static_cast<double*>(p.out)[pair_index(nv, i, j)] = (d == 0.0) ? 0.0 : (2.0 * n2) / d;
+          } else {
+            const float n2 = __fadd_rn(hl.x, hl.y);
+            const float d = (float)(Si + __ldcg(p.S + j));
+            static_cast<float*>(p.out)[pair_index(nv, i, j)] =
+                (d == 0.0f) ? 0.0f : __fdiv_rn(2.0f * n2, d);
+          }
+        }
+      }
+      if (w.kind == BK_N2) cta_signal(&n2_done[w.prob]);
+      continue;
+    }
+    // BK_TILE3: pivot j, tile index b inside the pivot
+    const int j = w.a;
+    const int Tk = (nv + BN - 1) / BN;
+    const int k0t = (j + 1) / BN;
+    const int nK = Tk - k0t;
+    const int row0 = (w.b / nK) * BM, col0 = (k0t + w.b % nK) * BN;
+    tile_minsum<true, PACKED, KU>(sm, V, row0, col0, j, L.am, L.bn, acc);
+    if (!cta_wait_count(&n2_done[w.prob], p.n2_tiles, err, &s_flag)) continue;
+    const int64_t wdt = nv - 1 - j;
+    const int64_t base = slab_offset(nv, 0, j);
+    const double Sj = __ldcg(p.S + j);
+    float* out = static_cast<float*>(p.out);
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      const int i = row0 + L.row(r);
+      if (i >= j) continue;
+      const double Sij = __ldcg(p.S + i) + Sj;
+      const double n2ij = (double)__ldcg(p.n2 + (int64_t)i * nv + j);
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        const int k = col0 + L.col(c);
+        if (k <= j || k >= nv) continue;
+        const float v = c3_value(acc.hl(r, c), n2ij, (double)__ldcg(p.n2 + (int64_t)i * nv + k),
+                                 (double)__ldcg(p.n2 + (int64_t)j * nv + k), Sij + __ldcg(p.S + k));
+        out[base + (int64_t)i * wdt + (k - j - 1)] = v;
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
 // FP64 CUDA-core path (small problems): 64 x 64 tiles, 4 x 4 per thread.
 constexpr int DBM = 64, DBK = 16;
 
@@ -588,6 +740,8 @@ cudaError_t set_attrs_one() {
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(mgemm3_kernel<PACKED, KU>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
   if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(batched_kernel<PACKED, KU>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(mgemm3_thresh_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
 }
 
@@ -670,6 +824,24 @@ cudaError_t launch_mgemm3(ps_ctx* h, const VF32& V, const double* S, const float
     by_ku(h->mgemm_ku, [&] { launch3_v<false, 16>(g, st, V, S, n2sq, dpref, npiv, j0, out, ntiles); },
           [&] { launch3_v<false, 8>(g, st, V, S, n2sq, dpref, npiv, j0, out, ntiles); },
           [&] { launch3_v<false, 4>(g, st, V, S, n2sq, dpref, npiv, j0, out, ntiles); });
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batched(ps_ctx* h, int packed, int ku, const BatchProb* probs, int nprob,
+                           const BatchItem* items, int nitems, int* counters, cudaStream_t st) {
+  cudaError_t e = ensure_attrs(h);
+  if (e != cudaSuccess) return e;
+  if (nitems == 0) return cudaSuccess;
+  const unsigned g = (unsigned)std::min(nitems, h->num_sms);
+  const size_t smem = sizeof(SmemF32);
+  if (packed)
+    by_ku(ku, [&] { batched_kernel<true, 16><<<g, NT, smem, st>>>(probs, nprob, items, nitems, counters); },
+          [&] { batched_kernel<true, 8><<<g, NT, smem, st>>>(probs, nprob, items, nitems, counters); },
+          [&] { batched_kernel<true, 4><<<g, NT, smem, st>>>(probs, nprob, items, nitems, counters); });
+  else
+    by_ku(ku, [&] { batched_kernel<false, 16><<<g, NT, smem, st>>>(probs, nprob, items, nitems, counters); },
+          [&] { batched_kernel<false, 8><<<g, NT, smem, st>>>(probs, nprob, items, nitems, counters); },
+          [&] { batched_kernel<false, 4><<<g, NT, smem, st>>>(probs, nprob, items, nitems, counters); });
   return cudaGetLastError();
 }
 

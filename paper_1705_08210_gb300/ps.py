@@ -33,6 +33,14 @@ class ps_matrix(ctypes.Structure):
                 ("ld", ctypes.c_int64), ("dtype", ctypes.c_int32), ("layout", ctypes.c_int32)]
 
 
+class ps_problem(ctypes.Structure):
+    _fields_ = [("V", ps_matrix), ("way", ctypes.c_int32), ("out_dtype", ctypes.c_int32),
+                ("out", ctypes.c_void_p)]
+
+
+PS_BATCH_PERSISTENT, PS_BATCH_PER_INSTANCE = 0, 1
+
+
 class ps_triple(ctypes.Structure):
     _fields_ = [("i", ctypes.c_int32), ("j", ctypes.c_int32), ("k", ctypes.c_int32),
                 ("value", ctypes.c_float)]
@@ -66,12 +74,16 @@ ps_quantize = _sig("ps_quantize", ctypes.c_int, [_h, _M, _i32, _p, _p, _p])
 ps_timing_enable = _sig("ps_timing_enable", ctypes.c_int, [_h, _i32])
 ps_timing_read = _sig("ps_timing_read", ctypes.c_int,
                       [_h, ctypes.c_char_p, ctypes.POINTER(_i64), ctypes.POINTER(ctypes.c_double)])
+ps_metrics_batched = _sig("ps_metrics_batched", ctypes.c_int,
+                          [_h, ctypes.POINTER(ps_problem), _i32, _i32, _p])
+ps_autotune_batched = _sig("ps_autotune_batched", ctypes.c_int,
+                           [_h, ctypes.POINTER(ps_problem), _i32, ctypes.c_char_p, ctypes.c_char_p, _i32, _p])
 ps_metrics_2way_static = _sig("ps_metrics_2way_static", ctypes.c_int, [_M, _p, _i32, _p])
 ps_probe_minadd_peak = _sig("ps_probe_minadd_peak", ctypes.c_int,
                             [_h, _i32, ctypes.POINTER(ctypes.c_double)])
 
 EXPORTED = [n for n in globals() if n.startswith("ps_") and callable(globals()[n])
-            and n not in ("ps_matrix", "ps_triple")]
+            and n not in ("ps_matrix", "ps_triple", "ps_problem")]
 
 
 class PSError(RuntimeError):

@@ -73,7 +73,7 @@ def latent_profiles(nv: int, nf: int, seed: int, n_profiles: int = 64,
     a = rng.uniform(0.5, 1.5, size=nv)
     N = zero_inflated(nv, nf, seed + 11, p_zero=p_zero, dtype=np.float64)
     V = P[:, z] * a[None, :] + sigma * N
-    return V.astype(dtype), z
+    return np.ascontiguousarray(V, dtype=dtype), z
 
 
 def batched_shapes(seed: int, n_instances: int = 64, n_2way: int = 48):
