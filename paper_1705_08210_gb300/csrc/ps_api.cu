@@ -410,6 +410,7 @@ ps_status ps_create(ps_handle* out, int device) {
     const int ku = atoi(v);
     if (ku == 4 || ku == 8 || ku == 16) h->mgemm_ku = ku;
   }
+  if (const char* v = getenv("PS_MGEMM_TILE")) h->mgemm_tile = atoi(v) == 64 ? 64 : 128;
   if (prop.major < 10) {
     delete h;
     return fail(nullptr, PS_ERR_UNSUPPORTED, "device %d is sm_%d%d; this library is built for sm_103a",

@@ -60,9 +60,9 @@ uint64_t full_signature(const ps_problem* probs, int n, int variant) {
   return fnv(h, &variant, sizeof(variant));
 }
 
-// variant code: packed * 100 + ku
-int variant_code(int packed, int ku) { return packed * 100 + ku; }
-const int kVariants[6] = {108, 116, 104, 8, 16, 4};
+// candidate configurations of the autotuner (see mgemm_variant_code):
+// tile 128 or 64 x unroll depth 16, 8, 4, all with packed adds
+const int kVariants[6] = {108, 116, 104, 1108, 1116, 1104};
 
 bool is_device(const void* p) {
   cudaPointerAttributes a;
@@ -97,15 +97,16 @@ ps_status check_problems(ps_ctx* h, const ps_problem* probs, int n) {
   return PS_OK;
 }
 
-int64_t tiles3_of_pivot(int nv, int j) {
-  const int64_t Tk = (nv + 127) / 128;
-  const int64_t nI = (j + 127) / 128;
-  const int64_t nK = (j + 1 < nv) ? (Tk - (j + 1) / 128) : 0;
+int64_t tiles3_of_pivot(int nv, int j, int B) {
+  const int64_t Tk = (nv + B - 1) / B;
+  const int64_t nI = (j + B - 1) / B;
+  const int64_t nK = (j + 1 < nv) ? (Tk - (j + 1) / B) : 0;
   return nI * nK;
 }
 
 // Build the work list and device state of one batch and capture its graph.
 ps_status build_batch(ps_ctx* h, const ps_problem* probs, int n, int variant, CachedBatch* cb) {
+  const int B = mgemm_variant_of(variant)->tile;
   std::vector<BatchProb> bp(n);
   size_t off_S = 0, off_n2 = 0;
   std::vector<size_t> oS(n), oN(n);
@@ -121,12 +122,12 @@ ps_status build_batch(ps_ctx* h, const ps_problem* probs, int n, int variant, Ca
     const int nv = (int)probs[t].V.nv;
     const int nsb = (int)ceil_div(nv, 32);
     for (int b = 0; b < nsb; ++b) sums.push_back({t, BK_SUMS, b, 0});
-    const int T = (int)ceil_div(nv, 128);
+    const int T = (int)ceil_div(nv, B);
     for (int I = 0; I < T; ++I)
       for (int J = I; J < T; ++J) mid.push_back({t, probs[t].way == 2 ? BK_TILE2 : BK_N2, I, J});
     if (probs[t].way == 3)
       for (int j = 0; j < nv; ++j) {
-        const int64_t c = tiles3_of_pivot(nv, j);
+        const int64_t c = tiles3_of_pivot(nv, j, B);
         for (int64_t u = 0; u < c; ++u) tail.push_back({t, BK_TILE3, j, (int)u});
       }
   }
@@ -166,7 +167,7 @@ ps_status build_batch(ps_ctx* h, const ps_problem* probs, int n, int variant, Ca
     q.way = p.way;
     q.out_f64 = p.out_dtype == PS_F64;
     q.nsum_blocks = (int)ceil_div(p.V.nv, 32);
-    const int64_t T = ceil_div(p.V.nv, 128);
+    const int64_t T = ceil_div(p.V.nv, B);
     q.n2_tiles = p.way == 3 ? (int)(T * (T + 1) / 2) : 0;
   }
   PS_CUDA_TRY(h, cudaMemcpy(dprob, bp.data(), n * sizeof(BatchProb), cudaMemcpyHostToDevice));
@@ -177,14 +178,14 @@ ps_status build_batch(ps_ctx* h, const ps_problem* probs, int n, int variant, Ca
   cb->nitems = (int)items.size();
 
   // attributes are set outside the capture
-  PS_CUDA_TRY(h, launch_batched(h, variant / 100, variant % 100, dprob, n, ditems, 0, counters, 0));
+  PS_CUDA_TRY(h, launch_batched(h, variant, dprob, n, ditems, 0, counters, 0));
   cudaStream_t cs;
   PS_CUDA_TRY(h, cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
   cudaGraph_t g = nullptr;
   e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
   if (e == cudaSuccess) {
     cudaMemsetAsync(counters, 0, (2 + 2 * n) * sizeof(int), cs);
-    launch_batched(h, variant / 100, variant % 100, dprob, n, ditems, cb->nitems, counters, cs);
+    launch_batched(h, variant, dprob, n, ditems, cb->nitems, counters, cs);
     e = cudaStreamEndCapture(cs, &g);
   }
   if (e == cudaSuccess) e = cudaGraphInstantiate(&cb->exec, g, 0);
@@ -219,7 +220,7 @@ ps_status run_graph(ps_ctx* h, const ps_problem* probs, int n, int variant, cuda
   return PS_OK;
 }
 
-int default_variant(ps_ctx* h) { return variant_code(h->mgemm_packed_add, h->mgemm_ku); }
+int default_variant(ps_ctx* h) { return mgemm_variant_code(h); }
 
 }  // namespace
 
@@ -343,8 +344,9 @@ extern "C" ps_status ps_autotune_batched(ps_handle h, const ps_problem* probs, i
   }
   h->batch->tuned[sig] = best;
   if (choice && choice_len > 0) {
-    snprintf(choice, (size_t)choice_len, "%s add, %d-step unroll%s",
-             best / 100 ? "packed f32x2" : "scalar", best % 100, detail.empty() ? " (cached)" : "");
+    snprintf(choice, (size_t)choice_len, "tile %d x %d, %s add, %d-step unroll%s",
+             best / 1000 ? 64 : 128, best / 1000 ? 64 : 128, (best / 100) % 10 ? "packed f32x2" : "scalar",
+             best % 100, detail.empty() ? " (cached)" : "");
   }
   return PS_OK;
 }

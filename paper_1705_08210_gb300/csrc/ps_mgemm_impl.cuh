@@ -1,0 +1,665 @@
+// ps_mgemm_impl.cuh -- templated device code of the FP32 min-product kernels.
+//
+// The paper's "mGEMM" (Section 3.1): (A min B)_{ij} = sum_k min(a_ik, b_kj),
+// a GEMM whose multiply is replaced by min.  There is no tensor-core form of
+// min on FP32 data, so the inner loop is one FP32 min (FMNMX, ALU pipe) plus
+// one FP32 add (FMA pipe) per element pair.
+//
+// Design (sm_103a):
+//  * A warp owns a 64 x 32 output block, 8 x 8 outputs per lane (two 4-wide
+//    groups per dimension, so every 128-bit shared load is a conflict-free
+//    broadcast).  Tile shapes: 128 x 128 (2 x 4 warps, 1 CTA/SM) and 64 x 64
+//    (1 x 2 warps, 4 CTAs/SM; less edge waste on small or 3-way problems).
+//  * Operands stream through a 4-stage cp.async (16-byte, zero-filling)
+//    shared-memory ring of 16-field slices; zero fill is exact because
+//    min(0, x) = 0 for the non-negative data of Section 2.1.
+//  * Accumulation: each accumulator sums 64 fields in FP32 ("lo"), then is
+//    folded into a running "hi" with an exact TwoSum, leaving the rounding
+//    residual in "lo"; hi + lo carries at most 63 roundings of a 64-term
+//    non-negative partial sum: relative error <= 64 u (u = 2^-24).
+//  * Pairs: only upper-triangle tiles I <= J (Section 3.1, lower-triangle
+//    blocks skipped).  Triples: (pivot j, I, K) tiles with rows i < j and
+//    columns k > j (Section 3.2: only the part of B_j holding i < j < k); the
+//    pivot column v_j is min-ed into each thread's own A chunks as soon as
+//    they land (X_j = min(V, v_j) is never materialised).
+#pragma once
+
+#include "ps_internal.cuh"
+
+namespace ps {
+namespace mg {
+
+constexpr int BK = 16, STAGES = 4;
+constexpr int FOLD = 4;  // stages (of BK fields) per compensated fold: 64 fields
+
+template <int WM_, int WN_, int MINB_>
+struct TileCfg {
+  static constexpr int WM = WM_, WN = WN_;
+  static constexpr int BM = 64 * WM, BN = 32 * WN;
+  static constexpr int NT = 32 * WM * WN;
+  static constexpr int MINB = MINB_;               // resident CTAs per SM
+  static constexpr int CHA = BK * BM / 4 / NT;    // 16-byte A chunks per thread
+  static constexpr int CHB = BK * BN / 4 / NT;
+  static_assert(BM == BN, "square tiles");
+  static_assert(CHA * NT * 4 == BK * BM && CHB * NT * 4 == BK * BN, "chunking");
+};
+using T128 = TileCfg<2, 4, 1>;
+using T64 = TileCfg<1, 2, 4>;
+
+template <class C>
+struct __align__(16) Smem {
+  float A[STAGES][BK][C::BM];
+  float B[STAGES][BK][C::BN];
+  float P[STAGES][BK];  // pivot value of each slice row
+};
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem, int src_bytes) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem),
+               "r"(src_bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem, int src_bytes) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(s), "l"(gmem),
+               "r"(src_bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// Copies of one BK-field slice of the A rows [row0,row0+BM) and B columns
+// [col0,col0+BN) into ring buffer `buf`; thread t copies the 16-byte chunks
+// t, t+NT, ... of each operand.  With a pivot, the owner of a slice row's
+// first chunk also copies that row's pivot value; a row has BM/4 >= 16
+// consecutive chunks, so all owners of a row sit in one warp.
+template <class C, bool PIVOT>
+__device__ __forceinline__ void issue_slice(Smem<C>& sm, int buf, const VF32& V, int row0,
+                                            int col0, int k0, int jpiv) {
+  const int t = threadIdx.x;
+  constexpr int PA = C::BM / 4, PB = C::BN / 4;  // chunks per slice row
+#pragma unroll
+  for (int h = 0; h < C::CHA; ++h) {
+    const int c = t + h * C::NT;
+    const int r = c / PA, c4 = (c % PA) * 4;
+    const int q = k0 + r;
+    const int i = row0 + c4;
+    const int bytes = (q < V.nf && i < V.nv) ? min(16, 4 * (V.nv - i)) : 0;
+    cp_async16(&sm.A[buf][r][c4], bytes ? V.p + (int64_t)q * V.ld + i : V.p, bytes);
+    if (PIVOT && c % PA == 0) {  // the row's first chunk owner copies its pivot value
+      const int pb = q < V.nf ? 4 : 0;
+      cp_async4(&sm.P[buf][r], pb ? V.p + (int64_t)q * V.ld + jpiv : V.p, pb);
+    }
+  }
+#pragma unroll
+  for (int h = 0; h < C::CHB; ++h) {
+    const int c = t + h * C::NT;
+    const int r = c / PB, c4 = (c % PB) * 4;
+    const int q = k0 + r;
+    const int jx = col0 + c4;
+    const int bytes = (q < V.nf && jx < V.nv) ? min(16, 4 * (V.nv - jx)) : 0;
+    cp_async16(&sm.B[buf][r][c4], bytes ? V.p + (int64_t)q * V.ld + jx : V.p, bytes);
+  }
+}
+
+// X_j = min(V, v_j) on this thread's own A chunks of buffer `buf`.  Every
+// thread has waited for its own copies; the warp barrier makes the pivot
+// values copied by the row owners in this warp visible.
+template <class C>
+__device__ __forceinline__ void pivot_min_slice(Smem<C>& sm, int buf) {
+  const int t = threadIdx.x;
+  constexpr int PA = C::BM / 4;
+  static_assert(PA >= 16 && 32 % (PA > 32 ? 32 : PA) == 0, "row owners share a warp");
+  __syncwarp();
+#pragma unroll
+  for (int h = 0; h < C::CHA; ++h) {
+    const int c = t + h * C::NT;
+    const int r = c / PA, c4 = (c % PA) * 4;
+    const float p = sm.P[buf][r];
+    float4 a = *reinterpret_cast<float4*>(&sm.A[buf][r][c4]);
+    a.x = fminf(a.x, p);
+    a.y = fminf(a.y, p);
+    a.z = fminf(a.z, p);
+    a.w = fminf(a.w, p);
+    *reinterpret_cast<float4*>(&sm.A[buf][r][c4]) = a;
+  }
+}
+
+// Packed FP32 pair add (sm_100+ add.rn.f32x2): two accumulators per issue.
+__device__ __forceinline__ unsigned long long f2_add(unsigned long long acc, float x, float y) {
+  unsigned long long r;
+  asm("{\n\t.reg .b64 t;\n\tmov.b64 t, {%2, %3};\n\tadd.rn.f32x2 %0, %1, t;\n\t}"
+      : "=l"(r)
+      : "l"(acc), "f"(x), "f"(y));
+  return r;
+}
+__device__ __forceinline__ unsigned long long f2_add2(unsigned long long a, unsigned long long b) {
+  unsigned long long r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ unsigned long long f2_sub2(unsigned long long a, unsigned long long b) {
+  unsigned long long r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ float2 f2_unpack(unsigned long long v) {
+  float2 r;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(v));
+  return r;
+}
+
+// Per-thread accumulators for 8 x 8 outputs: "lo" accumulates up to 64
+// fields; fold() moves it into "hi" with an exact TwoSum and leaves the
+// rounding residual in "lo".  PACKED adds pairs with one add.rn.f32x2.
+template <bool PACKED>
+struct Acc;
+
+template <>
+struct Acc<true> {
+  unsigned long long hi[8][4];
+  unsigned long long lo[8][4];
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int r = 0; r < 8; ++r)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) hi[r][c] = lo[r][c] = 0ull;
+  }
+  __device__ __forceinline__ void step(const float (&a)[8], const float (&b)[8]) {
+#pragma unroll
+    for (int r = 0; r < 8; ++r)
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+        lo[r][c] = f2_add(lo[r][c], fminf(a[r], b[2 * c]), fminf(a[r], b[2 * c + 1]));
+  }
+  __device__ __forceinline__ void fold() {
+#pragma unroll
+    for (int r = 0; r < 8; ++r)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const unsigned long long s = f2_add2(hi[r][c], lo[r][c]);
+        const unsigned long long bp = f2_sub2(s, hi[r][c]);
+        const unsigned long long ap = f2_sub2(s, bp);
+        const unsigned long long e = f2_add2(f2_sub2(hi[r][c], ap), f2_sub2(lo[r][c], bp));
+        hi[r][c] = s;
+        lo[r][c] = e;
+      }
+  }
+  __device__ __forceinline__ float2 hl(int r, int c) const {
+    const float2 h = f2_unpack(hi[r][c >> 1]);
+    const float2 l = f2_unpack(lo[r][c >> 1]);
+    return (c & 1) ? make_float2(h.y, l.y) : make_float2(h.x, l.x);
+  }
+};
+
+template <>
+struct Acc<false> {
+  float hi[8][8];
+  float lo[8][8];
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int r = 0; r < 8; ++r)
+#pragma unroll
+      for (int c = 0; c < 8; ++c) hi[r][c] = lo[r][c] = 0.0f;
+  }
+  __device__ __forceinline__ void step(const float (&a)[8], const float (&b)[8]) {
+#pragma unroll
+    for (int r = 0; r < 8; ++r)
+#pragma unroll
+      for (int c = 0; c < 8; ++c) lo[r][c] = __fadd_rn(lo[r][c], fminf(a[r], b[c]));
+  }
+  __device__ __forceinline__ void fold() {
+#pragma unroll
+    for (int r = 0; r < 8; ++r)
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        const float s = __fadd_rn(hi[r][c], lo[r][c]);
+        const float bp = __fsub_rn(s, hi[r][c]);
+        const float ap = __fsub_rn(s, bp);
+        const float e = __fadd_rn(__fsub_rn(hi[r][c], ap), __fsub_rn(lo[r][c], bp));
+        hi[r][c] = s;
+        lo[r][c] = e;
+      }
+  }
+  __device__ __forceinline__ float2 hl(int r, int c) const { return make_float2(hi[r][c], lo[r][c]); }
+};
+
+// BK k-steps of the micro-kernel on ring buffer `buf`, KU steps per loop
+// iteration (smaller KU keeps the hot loop in the instruction cache).
+template <class C, bool PACKED, int KU>
+__device__ __forceinline__ void compute_slice(const Smem<C>& sm, int buf, int am, int bn,
+                                              Acc<PACKED>& acc) {
+  const float* As = &sm.A[buf][0][am];
+  const float* Bs = &sm.B[buf][0][bn];
+#pragma unroll KU
+  for (int kk = 0; kk < BK; ++kk) {
+    const float4 a0 = *reinterpret_cast<const float4*>(As + kk * C::BM);
+    const float4 a1 = *reinterpret_cast<const float4*>(As + kk * C::BM + 32);
+    const float4 b0 = *reinterpret_cast<const float4*>(Bs + kk * C::BN);
+    const float4 b1 = *reinterpret_cast<const float4*>(Bs + kk * C::BN + 16);
+    const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+    const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+    acc.step(a, b);
+  }
+}
+
+// Full k loop over n_f for one (row0, col0) tile, with optional pivot j.
+template <class C, bool PIVOT, bool PACKED, int KU>
+__device__ __forceinline__ void tile_minsum(Smem<C>& sm, const VF32& V, int row0, int col0,
+                                            int jpiv, int am, int bn, Acc<PACKED>& acc) {
+  acc.zero();
+  const int nst = (V.nf + BK - 1) / BK;
+#pragma unroll
+  for (int s = 0; s < STAGES - 1; ++s) {
+    if (s < nst) issue_slice<C, PIVOT>(sm, s, V, row0, col0, s * BK, jpiv);
+    cp_async_commit();
+  }
+  for (int s = 0; s < nst; ++s) {
+    const int buf = s % STAGES;
+    cp_async_wait<STAGES - 2>();
+    if (PIVOT) pivot_min_slice<C>(sm, buf);
+    __syncthreads();
+    const int sn = s + STAGES - 1;
+    if (sn < nst) issue_slice<C, PIVOT>(sm, sn % STAGES, V, row0, col0, sn * BK, jpiv);
+    cp_async_commit();
+    compute_slice<C, PACKED, KU>(sm, buf, am, bn, acc);
+    if ((s + 1) % FOLD == 0) acc.fold();
+  }
+  acc.fold();
+  cp_async_wait<0>();
+  __syncthreads();  // the ring is reused by the next tile
+}
+
+// Thread -> output coordinates inside the tile.
+template <class C>
+struct Lanes {
+  int am, bn;  // smem column offsets of the A / B fragments
+  __device__ __forceinline__ Lanes() {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int wm = warp / C::WN, wn = warp % C::WN, lm = lane >> 2, ln = lane & 3;
+    am = wm * 64 + lm * 4;
+    bn = wn * 32 + ln * 4;
+  }
+  __device__ __forceinline__ int row(int r) const { return am + (r < 4 ? r : 28 + r); }
+  __device__ __forceinline__ int col(int c) const { return bn + (c < 4 ? c : 12 + c); }
+};
+
+__host__ __device__ __forceinline__ int64_t pair_index(int64_t nv, int64_t i, int64_t j) {
+  return i * (2 * nv - i - 1) / 2 + (j - i - 1);
+}
+
+// Upper-triangle tile index t -> (I, J), I <= J < T, row-major.
+__device__ __forceinline__ void tri_tile(int64_t t, int T, int& I, int& J) {
+  double disc = (2.0 * T + 1) * (2.0 * T + 1) - 8.0 * (double)t;
+  int i = (int)floor(((2.0 * T + 1) - sqrt(disc)) * 0.5);
+  i = max(0, min(i, T - 1));
+  while (i > 0 && (int64_t)i * T - (int64_t)i * (i - 1) / 2 > t) --i;
+  while (i + 1 < T && (int64_t)(i + 1) * T - (int64_t)(i + 1) * i / 2 <= t) ++i;
+  I = i;
+  J = i + (int)(t - ((int64_t)i * T - (int64_t)i * (i - 1) / 2));
+}
+
+// Section 2.2 eq. (1): n3 = n2(ij) + n2(ik) + n2(jk) - n3' in FP64, then
+// c3 = (3/2) n3 / d3 rounded to FP32 (d3 = S_i + S_j + S_k from FP64 sums).
+__device__ __forceinline__ float c3_value(float2 n3p_hl, double n2ij, double n2ik, double n2jk,
+                                          double d3) {
+  const double n3p = (double)n3p_hl.x + (double)n3p_hl.y;
+  const double n3 = ((n2ij + n2ik) + n2jk) - n3p;
+  const float d = (float)d3;
+  return (d == 0.0f) ? 0.0f : __fdiv_rn(1.5f * (float)n3, d);
+}
+
+// Pivot-slab offset: sum_{j'=jb}^{j-1} j'(n-1-j') = F(j) - F(jb),
+// F(x) = (n-1) x(x-1)/2 - (x-1) x (2x-1)/6.
+__host__ __device__ __forceinline__ int64_t slab_offset(int64_t n, int64_t jb, int64_t j) {
+  auto F = [n](int64_t x) { return (n - 1) * (x * (x - 1) / 2) - (x - 1) * x * (2 * x - 1) / 6; };
+  return F(j) - F(jb);
+}
+
+// Tiles (tile width B) of pivot j: I tiles covering rows [0, j) times K tiles
+// covering columns (j, nv).
+__host__ __device__ __forceinline__ int64_t pivot_tiles(int nv, int64_t j, int B) {
+  const int64_t Tk = (nv + B - 1) / B;
+  const int64_t nI = (j + B - 1) / B;
+  const int64_t nK = (j + 1 < nv) ? (Tk - (j + 1) / B) : 0;
+  return nI * nK;
+}
+
+// ---------------------------------------------------------------------------
+// 2-way: all c2 (or the n2 table) over the upper triangle of tiles.
+template <class C, bool PACKED, int KU>
+__global__ void __launch_bounds__(C::NT, C::MINB)
+    mgemm2_kernel(VF32 V, const double* __restrict__ S, void* __restrict__ out, int mode, int T,
+                  int64_t ntiles) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Smem<C>& sm = *reinterpret_cast<Smem<C>*>(smem_raw);
+  const Lanes<C> L;
+  Acc<PACKED> acc;
+  const int64_t nv = V.nv;
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    int I, J;
+    tri_tile(t, T, I, J);
+    const int row0 = I * C::BM, col0 = J * C::BN;
+    tile_minsum<C, false, PACKED, KU>(sm, V, row0, col0, 0, L.am, L.bn, acc);
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      const int i = row0 + L.row(r);
+      if (i >= nv) continue;
+      const double Si = S ? S[i] : 0.0;
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        const int j = col0 + L.col(c);
+        if (j <= i || j >= nv) continue;
+        const float2 hl = acc.hl(r, c);
+        if (mode == OUT2_C2_F32) {
+          const float n2 = __fadd_rn(hl.x, hl.y);
+          const float d = (float)(Si + S[j]);
+          static_cast<float*>(out)[pair_index(nv, i, j)] = (d == 0.0f) ? 0.0f : __fdiv_rn(2.0f * n2, d);
+        } else if (mode == OUT2_C2_F64) {
+          const double n2 = (double)hl.x + (double)hl.y;
+          const double d = Si + S[j];
+          static_cast<double*>(out)[pair_index(nv, i, j)] = (d == 0.0) ? 0.0 : (2.0 * n2) / d;
+        } else {
+          const float n2 = __fadd_rn(hl.x, hl.y);
+          float* tab = static_cast<float*>(out);
+          tab[(int64_t)i * nv + j] = n2;
+          tab[(int64_t)j * nv + i] = n2;
+        }
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// 3-way: c3 for pivots [jb, jb+npiv) over (j, I, K) tiles with I*B < j and
+// K*B+B-1 > j.  pref[x] = number of tiles of pivots jb .. jb+x-1.
+template <class C, bool PACKED, int KU>
+__global__ void __launch_bounds__(C::NT, C::MINB)
+    mgemm3_kernel(VF32 V, const double* __restrict__ S, const float* __restrict__ n2sq,
+                  const int64_t* __restrict__ pref, int npiv, int jb, float* __restrict__ out,
+                  int64_t ntiles) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Smem<C>& sm = *reinterpret_cast<Smem<C>*>(smem_raw);
+  const Lanes<C> L;
+  Acc<PACKED> acc;
+  const int nv = V.nv;
+  const int Tk = (nv + C::BN - 1) / C::BN;
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    int lo = 0, hi = npiv;  // largest x with pref[x] <= t
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (pref[mid] <= t) lo = mid; else hi = mid;
+    }
+    const int j = jb + lo;
+    const int64_t local = t - pref[lo];
+    const int k0t = (j + 1) / C::BN;
+    const int nK = Tk - k0t;
+    const int row0 = (int)(local / nK) * C::BM, col0 = (k0t + (int)(local % nK)) * C::BN;
+    tile_minsum<C, true, PACKED, KU>(sm, V, row0, col0, j, L.am, L.bn, acc);
+    const int64_t w = nv - 1 - j;
+    const int64_t base = slab_offset(nv, jb, j);
+    const double Sj = S[j];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      const int i = row0 + L.row(r);
+      if (i >= j) continue;
+      const double Sij = S[i] + Sj;
+      const double n2ij = (double)n2sq[(int64_t)i * nv + j];
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        const int k = col0 + L.col(c);
+        if (k <= j || k >= nv) continue;
+        out[base + (int64_t)i * w + (k - j - 1)] =
+            c3_value(acc.hl(r, c), n2ij, (double)n2sq[(int64_t)i * nv + k],
+                     (double)n2sq[(int64_t)j * nv + k], Sij + S[k]);
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Thresholded 3-way over an explicit list of 128-tile blocks (I, Jt, K),
+// I <= Jt <= K: work item = (block, pivot j in tile Jt).  Every triple
+// i<j<k with c3 >= tau is appended as a lexicographic key
+// (i << 2b | j << b | k) and its value; the counter receives the total even
+// beyond `cap`.
+template <class C, bool PACKED, int KU>
+__global__ void __launch_bounds__(C::NT, C::MINB)
+    mgemm3_thresh_kernel(VF32 V, const double* __restrict__ S, const float* __restrict__ n2sq,
+                         const int* __restrict__ blocks, int64_t nitems, ThreshArgs ta) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Smem<C>& sm = *reinterpret_cast<Smem<C>*>(smem_raw);
+  const Lanes<C> L;
+  Acc<PACKED> acc;
+  const int nv = V.nv;
+  constexpr int B = C::BM;
+  for (int64_t t = blockIdx.x; t < nitems; t += gridDim.x) {
+    const int64_t b = t / B;
+    const int I = blocks[3 * b], Jt = blocks[3 * b + 1], K = blocks[3 * b + 2];
+    const int j = Jt * B + (int)(t % B);
+    const int row0 = I * B, col0 = K * B;
+    // CTA-uniform skip: no row i < j or no column k > j in this item
+    if (j >= nv || row0 >= j || col0 + B - 1 <= j || col0 >= nv) continue;
+    tile_minsum<C, true, PACKED, KU>(sm, V, row0, col0, j, L.am, L.bn, acc);
+    const double Sj = S[j];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      const int i = row0 + L.row(r);
+      if (i >= j) continue;
+      const double Sij = S[i] + Sj;
+      const double n2ij = (double)n2sq[(int64_t)i * nv + j];
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        const int k = col0 + L.col(c);
+        if (k <= j || k >= nv) continue;
+        const float v = c3_value(acc.hl(r, c), n2ij, (double)n2sq[(int64_t)i * nv + k],
+                                 (double)n2sq[(int64_t)j * nv + k], Sij + S[k]);
+        if (v >= ta.tau) {
+          const unsigned long long pos = atomicAdd(ta.counter, 1ull);
+          if (pos < (unsigned long long)ta.cap) {
+            ta.keys[pos] = ((unsigned long long)i << (2 * ta.bits)) |
+                           ((unsigned long long)j << ta.bits) | (unsigned long long)k;
+            ta.vals[pos] = v;
+          }
+        }
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Batched persistent kernel: many independent problems of uneven size in one
+// launch.  CTAs take items from an atomic work queue over a list ordered
+//   [sums blocks] [2-way tiles + n2-table tiles] [3-way pivot tiles],
+// each group longest-first.  A tile's epilogue waits (bounded) for its
+// problem's sums, a 3-way tile's epilogue for its problem's n2 table; every
+// item it waits on sits earlier in the queue and has therefore been taken by
+// a running CTA that waits on nothing later, so the waits always end.
+__device__ __forceinline__ int ld_acquire(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Thread 0 waits until *ctr >= target (2 s limit); the CTA follows its verdict.
+__device__ __forceinline__ bool cta_wait_count(const int* ctr, int target, int* err, int* s_flag) {
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    if (ld_acquire(ctr) < target) {
+      unsigned long long t0;
+      asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t0));
+      while (ld_acquire(ctr) < target) {
+        unsigned long long t1;
+        asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t1));
+        if (t1 - t0 > 2000000000ull || *(volatile int*)err) {
+          atomicExch(err, 1);
+          ok = 0;
+          break;
+        }
+        __nanosleep(256);
+      }
+    }
+    *s_flag = ok;
+  }
+  __syncthreads();
+  const bool ok = *s_flag != 0;
+  __syncthreads();
+  return ok;
+}
+
+__device__ __forceinline__ void cta_signal(int* ctr) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(ctr, 1);
+  }
+}
+
+template <class C, bool PACKED, int KU>
+__global__ void __launch_bounds__(C::NT, C::MINB)
+    batched_kernel(const BatchProb* __restrict__ probs, int nprob, const BatchItem* __restrict__ items,
+                   int nitems, int* __restrict__ counters) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Smem<C>& sm = *reinterpret_cast<Smem<C>*>(smem_raw);
+  __shared__ int s_item, s_flag;
+  __shared__ double s_part[8][33];
+  const Lanes<C> L;
+  Acc<PACKED> acc;
+  int* err = counters + 1;
+  int* sums_done = counters + 2;
+  int* n2_done = counters + 2 + nprob;
+  for (;;) {
+    if (threadIdx.x == 0) s_item = atomicAdd(&counters[0], 1);
+    __syncthreads();
+    const int it = s_item;
+    __syncthreads();
+    if (it >= nitems) break;
+    const BatchItem w = items[it];
+    const BatchProb p = probs[w.prob];
+    const VF32 V = p.v;
+    const int nv = V.nv;
+    if (w.kind == BK_SUMS) {
+      // per-vector FP64 sums of 32 vectors in the same fixed order as
+      // vector_sums_fm: partial u sums fields u, u+8, ...; partials added
+      // in order 0..7 (so results match the single-problem path bit for bit)
+      constexpr int NW = C::NT / 32;
+      const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+      const int i = w.a * 32 + lane;
+      for (int u = warp; u < 8; u += NW) {
+        double sacc = 0.0;
+        if (i < nv)
+          for (int q = u; q < V.nf; q += 8) sacc += (double)__ldcg(V.p + (int64_t)q * V.ld + i);
+        s_part[u][lane] = sacc;
+      }
+      __syncthreads();
+      if (warp == 0 && i < nv) {
+        double tsum = s_part[0][lane];
+#pragma unroll
+        for (int u = 1; u < 8; ++u) tsum += s_part[u][lane];
+        p.S[i] = tsum;
+      }
+      cta_signal(&sums_done[w.prob]);
+      continue;
+    }
+    if (w.kind == BK_TILE2 || w.kind == BK_N2) {
+      const int row0 = w.a * C::BM, col0 = w.b * C::BN;
+      tile_minsum<C, false, PACKED, KU>(sm, V, row0, col0, 0, L.am, L.bn, acc);
+      if (!cta_wait_count(&sums_done[w.prob], p.nsum_blocks, err, &s_flag)) continue;
+#pragma unroll
+      for (int r = 0; r < 8; ++r) {
+        const int i = row0 + L.row(r);
+        if (i >= nv) continue;
+        const double Si = __ldcg(p.S + i);
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          const int j = col0 + L.col(c);
+          if (j <= i || j >= nv) continue;
+          const float2 hl = acc.hl(r, c);
+          if (w.kind == BK_N2) {
+            const float n2 = __fadd_rn(hl.x, hl.y);
+            p.n2[(int64_t)i * nv + j] = n2;
+            p.n2[(int64_t)j * nv + i] = n2;
+          } else if (p.out_f64) {
+            const double n2 = (double)hl.x + (double)hl.y;
+            const double d = Si + __ldcg(p.S + j);
+            static_cast<double*>(p.out)[pair_index(nv, i, j)] = (d == 0.0) ? 0.0 : (2.0 * n2) / d;
+          } else {
+            const float n2 = __fadd_rn(hl.x, hl.y);
+            const float d = (float)(Si + __ldcg(p.S + j));
+            static_cast<float*>(p.out)[pair_index(nv, i, j)] =
+                (d == 0.0f) ? 0.0f : __fdiv_rn(2.0f * n2, d);
+          }
+        }
+      }
+      if (w.kind == BK_N2) cta_signal(&n2_done[w.prob]);
+      continue;
+    }
+    // BK_TILE3: pivot j, tile index b inside the pivot
+    const int j = w.a;
+    const int Tk = (nv + C::BN - 1) / C::BN;
+    const int k0t = (j + 1) / C::BN;
+    const int nK = Tk - k0t;
+    const int row0 = (w.b / nK) * C::BM, col0 = (k0t + w.b % nK) * C::BN;
+    tile_minsum<C, true, PACKED, KU>(sm, V, row0, col0, j, L.am, L.bn, acc);
+    if (!cta_wait_count(&n2_done[w.prob], p.n2_tiles, err, &s_flag)) continue;
+    const int64_t wdt = nv - 1 - j;
+    const int64_t base = slab_offset(nv, 0, j);
+    const double Sj = __ldcg(p.S + j);
+    float* out = static_cast<float*>(p.out);
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      const int i = row0 + L.row(r);
+      if (i >= j) continue;
+      const double Sij = __ldcg(p.S + i) + Sj;
+      const double n2ij = (double)__ldcg(p.n2 + (int64_t)i * nv + j);
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        const int k = col0 + L.col(c);
+        if (k <= j || k >= nv) continue;
+        out[base + (int64_t)i * wdt + (k - j - 1)] =
+            c3_value(acc.hl(r, c), n2ij, (double)__ldcg(p.n2 + (int64_t)i * nv + k),
+                     (double)__ldcg(p.n2 + (int64_t)j * nv + k), Sij + __ldcg(p.S + k));
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Host-side launchers of one configuration (instantiated per .cu file).
+template <class C, bool PACKED, int KU>
+struct Launch {
+  static constexpr size_t smem = sizeof(Smem<C>);
+  static cudaError_t attrs() {
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(mgemm2_kernel<C, PACKED, KU>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
+      return e;
+    if ((e = cudaFuncSetAttribute(mgemm3_kernel<C, PACKED, KU>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
+      return e;
+    return cudaFuncSetAttribute(batched_kernel<C, PACKED, KU>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  }
+  static void mgemm2(unsigned grid, cudaStream_t st, const VF32& V, const double* S, void* out,
+                     int mode, int T, int64_t ntiles) {
+    mgemm2_kernel<C, PACKED, KU><<<grid, C::NT, smem, st>>>(V, S, out, mode, T, ntiles);
+  }
+  static void mgemm3(unsigned grid, cudaStream_t st, const VF32& V, const double* S,
+                     const float* n2sq, const int64_t* pref, int npiv, int jb, float* out,
+                     int64_t ntiles) {
+    mgemm3_kernel<C, PACKED, KU><<<grid, C::NT, smem, st>>>(V, S, n2sq, pref, npiv, jb, out,
+                                                            ntiles);
+  }
+  static void batched(unsigned grid, cudaStream_t st, const BatchProb* probs, int nprob,
+                      const BatchItem* items, int nitems, int* counters) {
+    batched_kernel<C, PACKED, KU><<<grid, C::NT, smem, st>>>(probs, nprob, items, nitems, counters);
+  }
+};
+
+}  // namespace mg
+}  // namespace ps

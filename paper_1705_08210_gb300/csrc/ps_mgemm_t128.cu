@@ -1,0 +1,42 @@
+// ps_mgemm_t128.cu -- 128 x 128-tile instantiations of the FP32 min-product
+// kernels (8 warps, one CTA per SM), plus the thresholded 3-way kernel.
+#include "ps_mgemm_impl.cuh"
+
+namespace ps {
+
+template <bool P, int KU>
+static MgemmVariant make_t128() {
+  using L = mg::Launch<mg::T128, P, KU>;
+  return MgemmVariant{&L::attrs, &L::mgemm2, &L::mgemm3, &L::batched, mg::T128::BM, mg::T128::MINB};
+}
+
+const MgemmVariant* mgemm_variant_t128(int packed, int ku) {
+  static const MgemmVariant v[6] = {make_t128<true, 16>(),  make_t128<true, 8>(),
+                                    make_t128<true, 4>(),   make_t128<false, 16>(),
+                                    make_t128<false, 8>(),  make_t128<false, 4>()};
+  const int k = ku == 16 ? 0 : (ku == 4 ? 2 : 1);
+  return &v[(packed ? 0 : 3) + k];
+}
+
+cudaError_t launch_thresh_t128(int num_sms, const VF32& V, const double* S, const float* n2sq,
+                               const int* blocks, int64_t nblocks, const ThreshArgs& ta,
+                               cudaStream_t st) {
+  using C = mg::T128;
+  static bool attrs_done[64] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const size_t smem = sizeof(mg::Smem<C>);
+  if (!attrs_done[dev & 63]) {
+    cudaError_t e = cudaFuncSetAttribute(mg::mgemm3_thresh_kernel<C, true, 8>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attrs_done[dev & 63] = true;
+  }
+  const int64_t nitems = nblocks * C::BM;
+  if (nitems == 0) return cudaSuccess;
+  const unsigned grid = (unsigned)std::min<int64_t>(nitems, (int64_t)num_sms * C::MINB);
+  mg::mgemm3_thresh_kernel<C, true, 8><<<grid, C::NT, smem, st>>>(V, S, n2sq, blocks, nitems, ta);
+  return cudaGetLastError();
+}
+
+}  // namespace ps

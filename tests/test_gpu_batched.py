@@ -20,7 +20,10 @@ def _make_batch(ps, shapes, seed):
     keep, probs = [], (ps.ps_problem * len(shapes))()
     for t, (way, nv, nf) in enumerate(shapes):
         V = synth.zero_inflated(nv, nf, seed + t)
-        X = torch.from_numpy(V).cuda()
+        ld = (nv + 3) // 4 * 4  # batched inputs need ld % 4 == 0
+        Xp = torch.full((nf, ld), float("nan"), device="cuda")
+        Xp[:, :nv] = torch.from_numpy(V).cuda()
+        X = Xp[:, :nv]
         n = nv * (nv - 1) // 2 if way == 2 else ps.ps_slab_size(nv, 0, nv)
         out = torch.full((n,), float("nan"), dtype=torch.float32, device="cuda")
         probs[t].V = ps.matrix(X)
@@ -68,7 +71,7 @@ def test_batched_new_data_same_buffers(ps, handle):
     # new values in the same device buffers: the replayed graph must see them
     for t, (V, X, o) in enumerate(keep):
         V2 = synth.zero_inflated(V.shape[1], V.shape[0], 6000 + t)
-        X.copy_(torch.from_numpy(V2))
+        X.copy_(torch.from_numpy(V2).cuda())
         keep[t] = (V2, X, o)
     ps.check(ps.ps_metrics_batched(handle.h, probs, 4, ps.PS_BATCH_PERSISTENT, st), handle.h)
     torch.cuda.synchronize()
