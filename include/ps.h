@@ -178,17 +178,27 @@ ps_status ps_metrics_3way(ps_handle h, const ps_matrix* V, int64_t j_begin,
 /* ---------------------------------------------------------------------------
  * Thresholded 3-way search: every triple i<j<k with c3 >= tau, sorted
  * lexicographically by (i,j,k).
- *   use_proposal : 0 = exhaustive; 1 = only blocks proposed by the learned
- *                  encoder loaded with ps_proposal_load (see below);
- *                  2 = only blocks that the exact 2-way bound cannot rule
- *                  out (lossless).
+ *   use_proposal : 0 = exhaustive over all 128-tile blocks (I<=J<=K);
+ *                  1 = only the blocks the trained encoder proposes
+ *                      (ps_proposal_train; vectors reordered by its
+ *                      clusters; falls back to exhaustive when more than 60%
+ *                      of the blocks are proposed); recall < 1 is possible;
+ *                  2 = only blocks that the bound
+ *                      c3 <= 1.5 min(n2ij+n2ik+n2jk, n2jk+S_i, n2ik+S_j,
+ *                      n2ij+S_k) / d3 (from min(a,b,c) >= min(a,b) +
+ *                      min(a,c) - a) cannot rule out: lossless; reordered by
+ *                      the encoder when one is trained for this nf.
+ *                  Every reported value equals the exhaustive one bit for
+ *                  bit (eq. (1) is summed in original index order).
  *   out          : `capacity` ps_triple slots (device or host).
  *   count        : one int64 (device or host) receiving the total number of
  *                  triples found, also when it exceeds `capacity`.
  * Returns PS_ERR_CAPACITY when the total exceeds `capacity`; the first
  * `capacity` triples in sorted order are then written.
- * Errors: PS_ERR_INVALID_ARG for nv < 3, capacity < 0, null pointers;
- *   PS_ERR_INVALID_ARG for use_proposal 1 without a loaded encoder. */
+ * Synchronous: returns once the result and count are written.
+ * Errors: PS_ERR_INVALID_ARG for nv < 3 or nv > 2^21, capacity < 0, null
+ *   pointers, use_proposal outside 0..2, or use_proposal 1 without a trained
+ *   encoder for this nf. */
 ps_status ps_threshold_3way(ps_handle h, const ps_matrix* V, float tau,
                             int32_t use_proposal, ps_triple* out,
                             int64_t capacity, int64_t* count,
@@ -240,6 +250,50 @@ ps_status ps_autotune_batched(ps_handle h, const ps_problem* probs, int32_t n,
                               int32_t choice_len, ps_stream stream);
 
 /* ---------------------------------------------------------------------------
+ * Learned block proposal for ps_threshold_3way (not in the paper).
+ * Encoder: e_i = W2 relu(W1 x_i + b1) + b2, x_i = log1p(v_i) (d_in = n_f
+ * inputs, 256 hidden, 64 outputs), BF16 weights in the products, FP32
+ * accumulation, FP32 master weights; pair score z_ij = e_i . e_j + beta.
+ * Parameters (FP32, this order): W1[256][d_in], b1[256], W2[64][256], b2[64],
+ * beta.  The encoder lives in the handle.
+ *
+ * ps_proposal_init: allocates and initialises (Glorot-uniform weights from a
+ *   seeded host generator, zero biases, beta = 0).
+ * ps_proposal_param_count: number of parameters (-1 without an encoder).
+ * ps_proposal_params: set != 0 copies `params` into the encoder (and, with a
+ *   non-NULL theta, marks it trained with that proposal threshold);
+ *   set == 0 copies the parameters (and theta) out.  Host or device memory.
+ * ps_proposal_pair_grad: embeddings E (nv x 64, row-major) of an FP32
+ *   field-major DEVICE matrix with nf = d_in, and, when grad is not NULL, the
+ *   gradient of the mean logistic loss over `npairs` pairs (pairs[2p],
+ *   pairs[2p+1] vector indices, labels 0/1; device memory) in parameter
+ *   order, and the loss.  Synchronises `stream`.
+ * ps_proposal_train: for every training matrix (FP32 field-major DEVICE,
+ *   one common nf, ld % 4 == 0) runs the exact thresholded search at `tau`,
+ *   labels a pair positive when it belongs to a triple with c3 >= tau, adds
+ *   4 random negatives per positive, then takes `steps` Adam steps (rate lr)
+ *   on the logistic pair loss, cycling through the matrices, and sets the
+ *   proposal threshold theta to the (1 - target_recall) quantile of the
+ *   positive pair scores.  final_loss (may be NULL) receives the last loss.
+ * ps_proposal_last_stats: fraction of the 128-tile blocks (I<=J<=K) that
+ *   the last ps_threshold_3way call searched, and their number.
+ * Errors: PS_ERR_INVALID_ARG for bad sizes or a missing encoder. */
+ps_status ps_proposal_init(ps_handle h, int32_t d_in, uint64_t seed);
+int64_t ps_proposal_param_count(ps_handle h);
+ps_status ps_proposal_params(ps_handle h, int32_t set, float* params,
+                             int64_t n, float* theta);
+ps_status ps_proposal_pair_grad(ps_handle h, const ps_matrix* V,
+                                const int32_t* pairs, const float* labels,
+                                int64_t npairs, float* E_out, float* grad,
+                                double* loss, ps_stream stream);
+ps_status ps_proposal_train(ps_handle h, const ps_matrix* train,
+                            int32_t ntrain, float tau, int32_t steps, float lr,
+                            float target_recall, uint64_t seed,
+                            double* final_loss, ps_stream stream);
+ps_status ps_proposal_last_stats(ps_handle h, double* kept_fraction,
+                                 int64_t* blocks);
+
+/* ---------------------------------------------------------------------------
  * Quantizer of the thermometer path (not in the paper).
  *   P      : the nearest-rank 99.9th percentile of the nonzero entries
  *            (rank ceil(0.999*m) of m nonzeros, ascending, 1-based);
@@ -263,7 +317,8 @@ ps_status ps_quantize(ps_handle h, const ps_matrix* V, int32_t levels,
  * ps_timing_read synchronises on the recorded events of `kernel` and returns
  * their number and summed duration.  Kernel names: "vector_sums", "pack",
  * "mgemm2", "mgemm2_f64", "mgemm2_n2", "mgemm3", "quantize", "thermo_encode",
- * "thermo_gemm", "threshold3", "sort", "batched".
+ * "thermo_gemm", "threshold3", "sort", "batched", "proposal_encode",
+ * "proposal_score", "proposal_bound".
  * Errors: PS_ERR_INVALID_ARG for null arguments. */
 ps_status ps_timing_enable(ps_handle h, int32_t enable);
 ps_status ps_timing_read(ps_handle h, const char* kernel, int64_t* launches,

@@ -281,9 +281,10 @@ int key_bits_for(int nv) {
 
 // Run the thresholded kernel over `blk` (3 ints per block), sort the hits,
 // write the first `capacity` and the total count.  Synchronous.
-ps_status threshold_blocks(ps_ctx* h, const Prepared& P, const std::vector<int>& blk, float tau,
-                           ps_triple* out, int64_t capacity, int64_t* count, cudaStream_t st) {
-  const int nv = P.f32.nv;
+ps_status threshold_blocks(ps_ctx* h, const VF32& v, const double* S, const int* perm,
+                           const std::vector<int>& blk, float tau, ps_triple* out, int64_t capacity,
+                           int64_t* count, cudaStream_t st) {
+  const int nv = v.nv;
   const float* n2 = static_cast<const float*>(h->ws.ptr[WS_N2]);
   const int64_t nblocks = (int64_t)blk.size() / 3;
   int* dblk = static_cast<int*>(ws_get(h, WS_BLOCKS, std::max<size_t>(blk.size(), 1) * sizeof(int)));
@@ -306,10 +307,11 @@ ps_status threshold_blocks(ps_ctx* h, const Prepared& P, const std::vector<int>&
     ta.vals = reinterpret_cast<float*>(hits + (size_t)cap * 16);
     ta.counter = counter;
     ta.cap = cap;
+    ta.perm = perm;
     PS_CUDA_TRY(h, cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st));
     {
       ScopedTimer tm(h, "threshold3", st);
-      PS_CUDA_TRY(h, launch_mgemm3_thresh(h, P.f32, P.S, n2, dblk, nblocks, ta, st));
+      PS_CUDA_TRY(h, launch_mgemm3_thresh(h, v, S, n2, dblk, nblocks, ta, st));
     }
     unsigned long long c = 0;
     PS_CUDA_TRY(h, cudaMemcpyAsync(&c, counter, sizeof(c), cudaMemcpyDeviceToHost, st));
@@ -427,6 +429,7 @@ ps_status ps_destroy(ps_handle h) {
     cudaDeviceSynchronize();
     timing_clear(h);
     batch_state_free(h);
+    mlp_free(h);
     for (int s = 0; s < WS_NUM_SLOTS; ++s)
       if (h->ws.ptr[s]) cudaFree(h->ws.ptr[s]);
   }
@@ -553,31 +556,66 @@ ps_status ps_threshold_3way(ps_handle h, const ps_matrix* V, float tau, int32_t 
   if (capacity < 0) return fail(h, PS_ERR_INVALID_ARG, "capacity < 0");
   if (!count) return fail(h, PS_ERR_INVALID_ARG, "null count");
   if (capacity > 0 && !out) return fail(h, PS_ERR_INVALID_ARG, "null out");
-  if (use_proposal != 0) return fail(h, PS_ERR_INVALID_ARG, "use_proposal %d not available", use_proposal);
+  if (use_proposal < 0 || use_proposal > 2)
+    return fail(h, PS_ERR_INVALID_ARG, "use_proposal %d is not 0, 1 or 2", use_proposal);
+  if (use_proposal == 1 && !h->mlp.trained)
+    return fail(h, PS_ERR_INVALID_ARG, "use_proposal 1 needs a trained encoder (ps_proposal_train)");
+  if (use_proposal == 1 && V->nf != h->mlp.d_in)
+    return fail(h, PS_ERR_INVALID_ARG, "encoder expects nf=%d", h->mlp.d_in);
   Guard g(h->device);
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   Prepared P;
   s = prepare(h, *V, st, true, &P);
   if (s != PS_OK) return s;
   const int nv = (int)V->nv;
+  // reorder by the encoder's clusters when a proposal is asked for and an
+  // encoder is trained for this n_f
+  VF32 v = P.f32;
+  double* S = P.S;
+  int* perm = nullptr;
+  if (use_proposal != 0 && h->mlp.trained && V->nf == h->mlp.d_in) {
+    s = proposal_reorder(h, P.f32, P.S, st, &v, &S, &perm);
+    if (s != PS_OK) return s;
+  }
   float* n2 = static_cast<float*>(ws_get(h, WS_N2, (size_t)nv * nv * 4));
   if (!n2) return PS_ERR_OOM;
   {
     ScopedTimer tm(h, "mgemm2_n2", st);
-    PS_CUDA_TRY(h, launch_mgemm2(h, P.f32, P.S, n2, OUT2_N2_SQUARE_F32, st));
+    PS_CUDA_TRY(h, launch_mgemm2(h, v, S, n2, OUT2_N2_SQUARE_F32, st));
   }
-  // every block (I <= Jt <= K) of 128-wide tiles
-  const int T = (int)ceil_div(nv, 128);
   std::vector<int> blk;
-  blk.reserve((size_t)T * (T + 1) * (T + 2) / 2);
-  for (int I = 0; I < T; ++I)
-    for (int K = I; K < T; ++K)
-      for (int Jt = I; Jt <= K; ++Jt) {
-        blk.push_back(I);
-        blk.push_back(Jt);
-        blk.push_back(K);
-      }
-  return threshold_blocks(h, P, blk, tau, out, capacity, count, st);
+  double kept = 1.0;
+  if (use_proposal == 1) {
+    s = proposal_blocks_learned(h, v, st, &blk, &kept);
+    if (s != PS_OK) return s;
+  } else if (use_proposal == 2) {
+    s = proposal_blocks_bound(h, v, S, n2, tau, st, &blk, &kept);
+    if (s != PS_OK) return s;
+  }
+  if (use_proposal == 0 || (use_proposal == 1 && kept > 0.6)) {
+    // exhaustive: every block (I <= Jt <= K) of 128-wide tiles (also the
+    // fallback when the learned proposal would keep most blocks anyway)
+    const int T = (int)ceil_div(nv, 128);
+    blk.clear();
+    for (int I = 0; I < T; ++I)
+      for (int K = I; K < T; ++K)
+        for (int Jt = I; Jt <= K; ++Jt) {
+          blk.push_back(I);
+          blk.push_back(Jt);
+          blk.push_back(K);
+        }
+    kept = 1.0;
+  }
+  h->last_kept = kept;
+  h->last_blocks = (int64_t)blk.size() / 3;
+  return threshold_blocks(h, v, S, perm, blk, tau, out, capacity, count, st);
+}
+
+ps_status ps_proposal_last_stats(ps_handle h, double* kept_fraction, int64_t* blocks) {
+  if (!h || !kept_fraction || !blocks) return fail(h, PS_ERR_INVALID_ARG, "null argument");
+  *kept_fraction = h->last_kept;
+  *blocks = h->last_blocks;
+  return PS_OK;
 }
 
 ps_status ps_quantize(ps_handle h, const ps_matrix* V, int32_t levels, float* P_out, uint8_t* q_out,

@@ -437,6 +437,7 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
   const Lanes<C> L;
   Acc<PACKED> acc;
   const int nv = V.nv;
+  const int* __restrict__ perm = ta.perm;
   constexpr int B = C::BM;
   for (int64_t t = blockIdx.x; t < nitems; t += gridDim.x) {
     const int64_t b = t / B;
@@ -446,24 +447,33 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
     // CTA-uniform skip: no row i < j or no column k > j in this item
     if (j >= nv || row0 >= j || col0 + B - 1 <= j || col0 >= nv) continue;
     tile_minsum<C, true, PACKED, KU>(sm, V, row0, col0, j, L.am, L.bn, acc);
-    const double Sj = S[j];
+    const int oj = perm ? perm[j] : j;
 #pragma unroll
     for (int r = 0; r < 8; ++r) {
       const int i = row0 + L.row(r);
       if (i >= j) continue;
-      const double Sij = S[i] + Sj;
-      const double n2ij = (double)n2sq[(int64_t)i * nv + j];
+      const int oi = perm ? perm[i] : i;
 #pragma unroll
       for (int c = 0; c < 8; ++c) {
         const int k = col0 + L.col(c);
         if (k <= j || k >= nv) continue;
-        const float v = c3_value(acc.hl(r, c), n2ij, (double)n2sq[(int64_t)i * nv + k],
-                                 (double)n2sq[(int64_t)j * nv + k], Sij + S[k]);
+        // the three vectors in increasing ORIGINAL index (a, b, c): the sums of
+        // eq. (1) are then formed in the same order as without a reordering,
+        // so every value is bit-identical to the exhaustive search
+        int pa = i, pb = j, pc = k, a = oi, bb = oj, cc = perm ? perm[k] : k;
+        if (perm) {
+          if (a > bb) { int x = a; a = bb; bb = x; x = pa; pa = pb; pb = x; }
+          if (bb > cc) { int x = bb; bb = cc; cc = x; x = pb; pb = pc; pc = x; }
+          if (a > bb) { int x = a; a = bb; bb = x; x = pa; pa = pb; pb = x; }
+        }
+        const float v = c3_value(acc.hl(r, c), (double)n2sq[(int64_t)pa * nv + pb],
+                                 (double)n2sq[(int64_t)pa * nv + pc], (double)n2sq[(int64_t)pb * nv + pc],
+                                 (S[pa] + S[pb]) + S[pc]);
         if (v >= ta.tau) {
           const unsigned long long pos = atomicAdd(ta.counter, 1ull);
           if (pos < (unsigned long long)ta.cap) {
-            ta.keys[pos] = ((unsigned long long)i << (2 * ta.bits)) |
-                           ((unsigned long long)j << ta.bits) | (unsigned long long)k;
+            ta.keys[pos] = ((unsigned long long)a << (2 * ta.bits)) |
+                           ((unsigned long long)bb << ta.bits) | (unsigned long long)cc;
             ta.vals[pos] = v;
           }
         }

@@ -78,6 +78,15 @@ ps_metrics_batched = _sig("ps_metrics_batched", ctypes.c_int,
                           [_h, ctypes.POINTER(ps_problem), _i32, _i32, _p])
 ps_autotune_batched = _sig("ps_autotune_batched", ctypes.c_int,
                            [_h, ctypes.POINTER(ps_problem), _i32, ctypes.c_char_p, ctypes.c_char_p, _i32, _p])
+ps_proposal_init = _sig("ps_proposal_init", ctypes.c_int, [_h, _i32, ctypes.c_uint64])
+ps_proposal_param_count = _sig("ps_proposal_param_count", _i64, [_h])
+ps_proposal_params = _sig("ps_proposal_params", ctypes.c_int, [_h, _i32, _p, _i64, _p])
+ps_proposal_pair_grad = _sig("ps_proposal_pair_grad", ctypes.c_int, [_h, _M, _p, _p, _i64, _p, _p, _p, _p])
+ps_proposal_train = _sig("ps_proposal_train", ctypes.c_int,
+                         [_h, _M, _i32, ctypes.c_float, _i32, ctypes.c_float, ctypes.c_float, ctypes.c_uint64,
+                          _p, _p])
+ps_proposal_last_stats = _sig("ps_proposal_last_stats", ctypes.c_int,
+                              [_h, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_i64)])
 ps_metrics_2way_static = _sig("ps_metrics_2way_static", ctypes.c_int, [_M, _p, _i32, _p])
 ps_probe_minadd_peak = _sig("ps_probe_minadd_peak", ctypes.c_int,
                             [_h, _i32, ctypes.POINTER(ctypes.c_double)])

@@ -1,0 +1,111 @@
+"""Learned block proposal and lossless bound filter for the thresholded 3-way
+search.  The encoder's forward and gradient are checked against the FP64 CPU
+re-statement; the proposal's recall is judged by the exhaustive search; the
+bound filter must reproduce the exhaustive result exactly."""
+import ctypes
+
+import numpy as np
+import pytest
+
+from oracle import mlp_oracle as mo
+from paper_1705_08210_gb300 import synth
+from gpu_run import threshold_3way
+
+pytestmark = pytest.mark.gpu
+
+
+def _dev(V):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(V)).cuda()
+
+
+def test_encoder_gradient_matches_fp64_oracle(ps, handle):
+    import torch
+    d_in, nv = 32, 40
+    ps.check(ps.ps_proposal_init(handle.h, d_in, 1234), handle.h)
+    n = ps.ps_proposal_param_count(handle.h)
+    rng = np.random.default_rng(3)
+    theta = (rng.normal(0, 0.15, size=n)).astype(np.float32)
+    ps.check(ps.ps_proposal_params(handle.h, 1, theta.ctypes.data, n, None), handle.h)
+    V = synth.zero_inflated(nv, d_in, synth.seed_for(5, 77), p_zero=0.5)
+    X = _dev(V)
+    m = ps.matrix(X)
+    pairs = np.stack([rng.integers(0, nv, 80), rng.integers(0, nv, 80)], axis=1).astype(np.int32)
+    pairs = pairs[pairs[:, 0] != pairs[:, 1]]
+    y = (rng.random(len(pairs)) < 0.4).astype(np.float32)
+    dp, dy = _dev(pairs), _dev(y)
+    E = torch.empty(nv * 64, device="cuda")
+    g = torch.empty(n, device="cuda")
+    loss = ctypes.c_double()
+    ps.check(ps.ps_proposal_pair_grad(handle.h, ctypes.byref(m), dp.data_ptr(), dy.data_ptr(), len(y),
+                                      E.data_ptr(), g.data_ptr(), ctypes.addressof(loss),
+                                      torch.cuda.current_stream().cuda_stream), handle.h)
+    # the products use BF16 copies of W1 and W2
+    th = theta.astype(np.float64)
+    n1 = 256 * d_in
+    th[:n1] = mo.bf16_round(theta[:n1])
+    o = n1 + 256
+    th[o:o + 64 * 256] = mo.bf16_round(theta[o:o + 64 * 256])
+    ref_loss, ref_g, ref_E = mo.pair_loss_and_grad(th, V, pairs, y)
+    gE = E.cpu().numpy().reshape(nv, 64)
+    assert np.max(np.abs(gE - ref_E)) <= 1e-4 * np.max(np.abs(ref_E))
+    assert abs(loss.value - ref_loss) <= 1e-5 * max(1.0, abs(ref_loss))
+    gg = g.cpu().numpy()
+    for lo, hi, name in [(0, n1, "W1"), (n1, n1 + 256, "b1"), (o, o + 64 * 256, "W2"),
+                         (o + 64 * 256, n - 1, "b2"), (n - 1, n, "beta")]:
+        err = np.max(np.abs(gg[lo:hi] - ref_g[lo:hi]))
+        scale = np.max(np.abs(ref_g[lo:hi])) + 1e-12
+        assert err <= 2e-3 * scale, (name, err, scale)
+
+
+def _trained(ps, handle, nf, n_profiles, seeds, steps=300):
+    import torch
+    mats, keep = (ps.ps_matrix * len(seeds))(), []
+    for t, sd in enumerate(seeds):
+        V, _ = synth.latent_profiles(1024, nf, sd, n_profiles=n_profiles, sigma=0.4)
+        X = _dev(V)
+        keep.append(X)
+        mats[t] = ps.matrix(X)
+    loss = ctypes.c_double()
+    ps.check(ps.ps_proposal_train(handle.h, mats, len(seeds), 0.7, steps, 1e-3, 0.999, 99,
+                                  ctypes.addressof(loss), torch.cuda.current_stream().cuda_stream), handle.h)
+    return loss.value
+
+
+def test_learned_proposal_recall_and_gain(ps, handle):
+    nf = 256
+    loss = _trained(ps, handle, nf, 16, [synth.seed_for(5, 100 + s) for s in range(3)])
+    assert np.isfinite(loss)
+    V, _ = synth.latent_profiles(2048, nf, synth.seed_for(5, 200), n_profiles=16, sigma=0.4)
+    st0, c0, t0, v0 = threshold_3way(ps, handle, V, 0.7, capacity=4_000_000, use_proposal=0)
+    assert st0 == ps.PS_OK and c0 > 1000
+    st1, c1, t1, v1 = threshold_3way(ps, handle, V, 0.7, capacity=4_000_000, use_proposal=1)
+    kept = ctypes.c_double()
+    nb = ctypes.c_int64()
+    ps.check(ps.ps_proposal_last_stats(handle.h, ctypes.byref(kept), ctypes.byref(nb)), handle.h)
+    assert st1 == ps.PS_OK
+    ref = {tuple(x): v for x, v in zip(t0.tolist(), v0)}
+    got = {tuple(x): v for x, v in zip(t1.tolist(), v1)}
+    assert set(got) <= set(ref)                        # no false triples
+    assert all(got[k] == ref[k] for k in got)          # bit-identical values
+    recall = len(got) / len(ref)
+    print(f"learned proposal: recall {recall:.5f}, blocks searched {kept.value:.4f} ({nb.value})")
+    assert recall >= 0.99
+    assert kept.value < 0.5                            # the encoder prunes most blocks
+
+
+def test_bound_filter_is_lossless(ps, handle):
+    V, _ = synth.latent_profiles(700, 128, synth.seed_for(5, 300), n_profiles=8, sigma=0.3)
+    st0, c0, t0, v0 = threshold_3way(ps, handle, V, 0.7, capacity=2_000_000, use_proposal=0)
+    st2, c2, t2, v2 = threshold_3way(ps, handle, V, 0.7, capacity=2_000_000, use_proposal=2)
+    assert st0 == st2 == ps.PS_OK and c0 == c2 > 0
+    np.testing.assert_array_equal(t0, t2)
+    np.testing.assert_array_equal(v0, v2)
+
+
+def test_proposal_requires_trained_encoder(ps):
+    h2 = ps.Handle(0)
+    V = synth.zero_inflated(50, 16, 1)
+    st, _, _, _ = threshold_3way(ps, h2, V, 0.7, capacity=10, use_proposal=1)
+    assert st == ps.PS_ERR_INVALID_ARG
+    h2.close()
