@@ -161,6 +161,58 @@ def run_reference(args, w, ws, rank):
     print(json.dumps(line), flush=True)
 
 
+def threshold_section(ps, synth, h, torch, sptr):
+    """Exhaustive vs learned vs bound-filtered thresholded 3-way search on
+    8192 x 2048 vectors from 64 latent profiles (sigma 0.4), tau = 0.7."""
+    nv, nf, tau = 8192, 2048, 0.7
+    V, _ = synth.latent_profiles(nv, nf, synth.seed_for(5), n_profiles=64, sigma=0.4)
+    X = torch.from_numpy(V).cuda()
+    m = ps.matrix(X)
+    cap = 20_000_000
+    out = torch.empty((cap, 4), dtype=torch.int32, device="cuda")
+    cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+
+    def run(mode):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ps.check(ps.ps_threshold_3way(h.h, ctypes.byref(m), tau, mode, out.data_ptr(), cap, cnt.data_ptr(),
+                                      sptr), h.h)
+        dt = time.perf_counter() - t0
+        kept = ctypes.c_double()
+        nb = ctypes.c_int64()
+        ps.check(ps.ps_proposal_last_stats(h.h, ctypes.byref(kept), ctypes.byref(nb)), h.h)
+        n = int(cnt.item())
+        keys = out[:n, :3].to(torch.int64)
+        return dt, n, (keys[:, 0] << 42) | (keys[:, 1] << 21) | keys[:, 2], out[:n, 3].clone(), kept.value
+
+    t_ex, n_ex, k_ex, v_ex, _ = run(0)
+    # encoder trained on the exact results of 4 random 1024-vector subsets
+    rng = np.random.default_rng(170508210)
+    subs = [torch.from_numpy(np.ascontiguousarray(V[:, np.sort(rng.choice(nv, 1024, replace=False))])).cuda()
+            for _ in range(4)]
+    mats = (ps.ps_matrix * 4)(*[ps.matrix(x) for x in subs])
+    loss = ctypes.c_double()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ps.check(ps.ps_proposal_train(h.h, mats, 4, tau, 600, 1e-3, 0.999, 99, ctypes.addressof(loss), sptr), h.h)
+    t_train = time.perf_counter() - t0
+    t_l, n_l, k_l, v_l, kept_l = run(1)
+    found = torch.isin(k_l, k_ex)
+    recall = float(found.sum().item()) / max(n_ex, 1)
+    t_b, n_b, k_b, v_b, kept_b = run(2)
+    exact_b = n_b == n_ex and bool(torch.equal(k_b, k_ex)) and bool(torch.equal(v_b, v_ex))
+    del out, X, subs
+    torch.cuda.empty_cache()
+    return {"workload": "3way threshold 8192x2048 f32, 64 latent profiles, sigma 0.4, tau 0.7",
+            "comparisons_exhaustive": nf * nv * (nv - 1) * (nv - 2) // 6,
+            "exhaustive": {"seconds": t_ex, "triples": n_ex},
+            "learned": {"train_seconds": t_train, "train_loss": loss.value, "search_seconds": t_l,
+                        "triples": n_l, "recall": recall, "blocks_searched": kept_l,
+                        "speedup_search": t_ex / t_l, "speedup_incl_training": t_ex / (t_l + t_train)},
+            "bound_lossless": {"search_seconds": t_b, "triples": n_b, "identical_to_exhaustive": exact_b,
+                               "blocks_searched": kept_b, "speedup": t_ex / t_b}}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -172,6 +224,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-secondary", action="store_true")
     ap.add_argument("--no-thermo", action="store_true")
+    ap.add_argument("--no-threshold", action="store_true")
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
     ws, rank, local = dist_env()
@@ -387,6 +440,11 @@ def main():
                                             "mgemm3_ms": k3, "frac_of_peak": c3 / (k3 / 1e3) / peak_cmp}}
         del o3, X3
 
+    # ---- thresholded 3-way search with proposals (8192 x 2048 latent profiles) ----
+    thresh = None
+    if not args.no_threshold and w["way"] == 2 and ws == 1:
+        thresh = threshold_section(ps, synth, h, torch, sptr)
+
     cb = None
     if rank == 0 and not args.no_cpu_baseline and ws == 1:
         cb = cpu_baseline(V, w, 8192 if w["way"] == 2 else 256)
@@ -402,7 +460,8 @@ def main():
                            "parallelism": f"independent instance per rank x{ws}"},
                 "roofline": roofline, "cpu_baseline": cb, "e2e": e2e, "clocks": clk,
                 "gpu_launches": launches_per_step * args.steps,
-                "sampled_max_rel_err": max_rel, "thermo_tensor_core": thermo, "secondary": secondary}
+                "sampled_max_rel_err": max_rel, "thermo_tensor_core": thermo, "secondary": secondary,
+                "threshold_3way": thresh}
         print(json.dumps(line), flush=True)
     h.close()
     if ws > 1:

@@ -251,28 +251,33 @@ ps_status ps_autotune_batched(ps_handle h, const ps_problem* probs, int32_t n,
 
 /* ---------------------------------------------------------------------------
  * Learned block proposal for ps_threshold_3way (not in the paper).
- * Encoder: e_i = W2 relu(W1 x_i + b1) + b2, x_i = log1p(v_i) (d_in = n_f
+ * Encoder: e_i = W2 relu(W1 x_i + b1) + b2, x_iq = log1p(v_iq n_f / S_i) (d_in = n_f
  * inputs, 256 hidden, 64 outputs), BF16 weights in the products, FP32
- * accumulation, FP32 master weights; pair score z_ij = e_i . e_j + beta.
- * Parameters (FP32, this order): W1[256][d_in], b1[256], W2[64][256], b2[64],
- * beta.  The encoder lives in the handle.
+ * accumulation, FP32 master weights; p_i = softmax(e_i) is a soft
+ * assignment to 64 learned clusters and a pair is scored
+ * P_ij = p_i . p_j (probability of sharing a cluster).
+ * Parameters (FP32, this order): W1[256][d_in], b1[256], W2[64][256], b2[64].
+ * The encoder lives in the handle.
  *
  * ps_proposal_init: allocates and initialises (Glorot-uniform weights from a
- *   seeded host generator, zero biases, beta = 0).
+ *   seeded host generator, zero biases).
  * ps_proposal_param_count: number of parameters (-1 without an encoder).
  * ps_proposal_params: set != 0 copies `params` into the encoder (and, with a
  *   non-NULL theta, marks it trained with that proposal threshold);
  *   set == 0 copies the parameters (and theta) out.  Host or device memory.
  * ps_proposal_pair_grad: embeddings E (nv x 64, row-major) of an FP32
  *   field-major DEVICE matrix with nf = d_in, and, when grad is not NULL, the
- *   gradient of the mean logistic loss over `npairs` pairs (pairs[2p],
+ *   gradient of the mean binary cross-entropy of P (clamped to
+ *   [1e-6, 1-1e-6]) over `npairs` pairs (pairs[2p],
  *   pairs[2p+1] vector indices, labels 0/1; device memory) in parameter
  *   order, and the loss.  Synchronises `stream`.
  * ps_proposal_train: for every training matrix (FP32 field-major DEVICE,
- *   one common nf, ld % 4 == 0) runs the exact thresholded search at `tau`,
+ *   one common nf, ld % 4 == 0; typically small random subsets of the
+ *   vectors to be searched, which share their population's structure) runs
+ *   the exact thresholded search at `tau`,
  *   labels a pair positive when it belongs to a triple with c3 >= tau, adds
  *   4 random negatives per positive, then takes `steps` Adam steps (rate lr)
- *   on the logistic pair loss, cycling through the matrices, and sets the
+ *   on the pair loss, cycling through the matrices, and sets the
  *   proposal threshold theta to the (1 - target_recall) quantile of the
  *   positive pair scores.  final_loss (may be NULL) receives the last loss.
  * ps_proposal_last_stats: fraction of the 128-tile blocks (I<=J<=K) that

@@ -586,7 +586,7 @@ ps_status ps_threshold_3way(ps_handle h, const ps_matrix* V, float tau, int32_t 
   std::vector<int> blk;
   double kept = 1.0;
   if (use_proposal == 1) {
-    s = proposal_blocks_learned(h, v, st, &blk, &kept);
+    s = proposal_blocks_learned(h, v, S, st, &blk, &kept);
     if (s != PS_OK) return s;
   } else if (use_proposal == 2) {
     s = proposal_blocks_bound(h, v, S, n2, tau, st, &blk, &kept);

@@ -1,12 +1,14 @@
 // ps_mlp.cu -- the encoder of the learned block proposal: forward, pair-loss
 // backward and Adam kernels.
 //
-// Not in the paper.  e_i = W2 relu(W1 x_i + b1) + b2 with x_i = log1p(v_i)
+// Not in the paper.  e_i = W2 relu(W1 x_i + b1) + b2 with x_iq =
+// log1p(v_iq n_f / S_i) (scale-free input)
 // (d_in = n_f inputs, 256 hidden, 64 outputs), BF16 weights in the forward
 // and backward products, FP32 accumulation, FP32 master weights for Adam.
-// A pair (i, j) is scored z_ij = e_i . e_j + beta; training minimises the
-// logistic loss of z against the label "the pair belongs to a triple with
-// c3 >= tau" (labels come from the exact thresholded search).
+// p_i = softmax(e_i) is a soft assignment to 64 learned clusters; a pair is
+// scored P_ij = p_i . p_j (probability of sharing a cluster), and training
+// minimises the binary cross-entropy of P against the label "the pair
+// belongs to a triple with c3 >= tau" (labels from the exact search).
 //
 // The products are small (n x d_in x 256 with n <= 8192): a shared-memory
 // tiled CUDA-core GEMM with FP32 accumulation is used for all of them; the
@@ -66,16 +68,25 @@ cudaError_t gemm(int M, int N, int K, AccA A, AccB B, Epi epi, cudaStream_t st) 
 }
 
 // ---- operand accessors ----
-struct XLog {  // x(i, q) = log1p(V[q*ld + i])
+struct XLog {  // x(i, q) = log1p(V[q*ld + i] * r[i]),  r[i] = n_f / S_i
   const float* p;
   int64_t ld;
-  __device__ float operator()(int i, int q) const { return log1pf(__ldg(p + (int64_t)q * ld + i)); }
+  const float* r;
+  __device__ float operator()(int i, int q) const { return log1pf(__ldg(p + (int64_t)q * ld + i) * r[i]); }
 };
 struct XLogT {  // x(q, i) (k = vector index)
   const float* p;
   int64_t ld;
-  __device__ float operator()(int q, int i) const { return log1pf(__ldg(p + (int64_t)q * ld + i)); }
+  const float* r;
+  __device__ float operator()(int q, int i) const { return log1pf(__ldg(p + (int64_t)q * ld + i) * r[i]); }
 };
+
+// r[i] = n_f / S_i (0 for an all-zero vector): the encoder input
+// log1p(v_iq * r_i) does not change when a vector is scaled.
+__global__ void input_scale_kernel(const double* __restrict__ S, int n, int nf, float* __restrict__ r) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) r[i] = S[i] > 0.0 ? (float)((double)nf / S[i]) : 0.f;
+}
 struct RowBF {  // w(r, c) = W[r*ld + c] in BF16
   const __nv_bfloat16* p;
   int ld;
@@ -136,51 +147,68 @@ __global__ void colsum_kernel(const float* __restrict__ G, int rows, int cols, f
   out[c] = s;
 }
 
-// Pair logistic loss: z = e_i . e_j + beta; dz = (sigmoid(z) - y) / npairs.
-// dE rows accumulate dz * e_other; the loss and d beta are reduced per block.
-__global__ void pair_loss_kernel(const float* __restrict__ E, const int* __restrict__ pairs,
-                                 const float* __restrict__ y, int64_t npairs,
-                                 const float* __restrict__ beta_p,
-                                 float* __restrict__ dE, double* __restrict__ loss,
-                                 float* __restrict__ dbeta) {
+// Row softmax P = softmax(E) (n x 64), one warp per row.
+__global__ void softmax_kernel(const float* __restrict__ E, int n, float* __restrict__ Pm) {
+  const int row = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (row >= n) return;
+  const float a = E[(int64_t)row * MLP_OUT + lane], b = E[(int64_t)row * MLP_OUT + 32 + lane];
+  float mx = fmaxf(a, b);
+  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  const float ea = expf(a - mx), eb = expf(b - mx);
+  float s = ea + eb;
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  Pm[(int64_t)row * MLP_OUT + lane] = ea / s;
+  Pm[(int64_t)row * MLP_OUT + 32 + lane] = eb / s;
+}
+
+// Pair loss: P = p_i . p_j clamped to [1e-6, 1 - 1e-6],
+// loss = -(y log P + (1-y) log(1-P)), mean over pairs; dPm accumulates
+// dloss/dP * p_other into both rows.
+__global__ void pair_loss_kernel(const float* __restrict__ Pm, const int* __restrict__ pairs,
+                                 const float* __restrict__ y, int64_t npairs, float* __restrict__ dPm,
+                                 double* __restrict__ loss) {
   __shared__ double sl[256];
-  __shared__ float sb[256];
   double l = 0.0;
-  float gb = 0.f;
   const float inv = 1.0f / (float)npairs;
-  const float beta = *beta_p;
   for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < npairs;
        p += (int64_t)gridDim.x * blockDim.x) {
     const int i = pairs[2 * p], j = pairs[2 * p + 1];
-    const float* ei = E + (int64_t)i * MLP_OUT;
-    const float* ej = E + (int64_t)j * MLP_OUT;
-    float z = beta;
-    for (int d = 0; d < MLP_OUT; ++d) z = fmaf(ei[d], ej[d], z);
+    const float* pi = Pm + (int64_t)i * MLP_OUT;
+    const float* pj = Pm + (int64_t)j * MLP_OUT;
+    float P = 0.f;
+    for (int d = 0; d < MLP_OUT; ++d) P = fmaf(pi[d], pj[d], P);
+    const float Pc = fminf(fmaxf(P, 1e-6f), 1.f - 1e-6f);
     const float t = y[p];
-    // log(1 + exp(-|z|)) + max(z, 0) - t z
-    l += (double)(log1pf(expf(-fabsf(z))) + fmaxf(z, 0.f) - t * z);
-    const float s = 1.f / (1.f + expf(-z));
-    const float g = (s - t) * inv;
-    gb += g;
+    l += (double)(-(t * logf(Pc) + (1.f - t) * log1pf(-Pc)));
+    // d/dP of the clamped loss (zero outside the clamp)
+    float g = (P > 1e-6f && P < 1.f - 1e-6f) ? (-t / Pc + (1.f - t) / (1.f - Pc)) : 0.f;
+    g *= inv;
     for (int d = 0; d < MLP_OUT; ++d) {
-      atomicAdd(&dE[(int64_t)i * MLP_OUT + d], g * ej[d]);
-      atomicAdd(&dE[(int64_t)j * MLP_OUT + d], g * ei[d]);
+      atomicAdd(&dPm[(int64_t)i * MLP_OUT + d], g * pj[d]);
+      atomicAdd(&dPm[(int64_t)j * MLP_OUT + d], g * pi[d]);
     }
   }
   sl[threadIdx.x] = l;
-  sb[threadIdx.x] = gb;
   __syncthreads();
   for (int o = 128; o > 0; o >>= 1) {
-    if (threadIdx.x < o) {
-      sl[threadIdx.x] += sl[threadIdx.x + o];
-      sb[threadIdx.x] += sb[threadIdx.x + o];
-    }
+    if (threadIdx.x < o) sl[threadIdx.x] += sl[threadIdx.x + o];
     __syncthreads();
   }
-  if (threadIdx.x == 0) {
-    atomicAdd(loss, sl[0] / (double)npairs);
-    atomicAdd(dbeta, sb[0]);
-  }
+  if (threadIdx.x == 0) atomicAdd(loss, sl[0] / (double)npairs);
+}
+
+// dE = p * (dP - (p . dP)) per row (softmax Jacobian), one warp per row.
+__global__ void softmax_backward_kernel(const float* __restrict__ Pm, const float* dPm, int n,
+                                        float* dE) {
+  const int row = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (row >= n) return;
+  const int64_t o = (int64_t)row * MLP_OUT;
+  const float pa = Pm[o + lane], pb = Pm[o + 32 + lane];
+  const float ga = dPm[o + lane], gb = dPm[o + 32 + lane];
+  float dot = pa * ga + pb * gb;
+  for (int s = 16; s > 0; s >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, s);
+  dE[o + lane] = pa * (ga - dot);
+  dE[o + 32 + lane] = pb * (gb - dot);
 }
 
 // Adam on the FP32 master weights; BF16 copies for the products.
@@ -209,9 +237,15 @@ __global__ void to_bf16_kernel(const float* __restrict__ w, __nv_bfloat16* __res
 }  // namespace
 
 // Parameter layout (FP32, contiguous): W1 [256][d_in], b1 [256], W2 [64][256],
-// b2 [64], beta [1].
+// b2 [64].
 int64_t mlp_param_count(int d_in) {
-  return (int64_t)MLP_HIDDEN * d_in + MLP_HIDDEN + (int64_t)MLP_OUT * MLP_HIDDEN + MLP_OUT + 1;
+  return (int64_t)MLP_HIDDEN * d_in + MLP_HIDDEN + (int64_t)MLP_OUT * MLP_HIDDEN + MLP_OUT;
+}
+
+cudaError_t mlp_softmax(const float* E, int n, float* Pm, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  softmax_kernel<<<(unsigned)ceil_div(n, 8), 256, 0, st>>>(E, n, Pm);
+  return cudaGetLastError();
 }
 
 cudaError_t mlp_sync_bf16(MlpState& M, cudaStream_t st) {
@@ -221,11 +255,19 @@ cudaError_t mlp_sync_bf16(MlpState& M, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-// E (n x 64) for the n vectors of the FP32 field-major view V (n = V.nv).
-cudaError_t mlp_forward(MlpState& M, const VF32& V, float* Hpre, float* H, float* E, cudaStream_t st) {
+cudaError_t mlp_input_scale(const double* S, int n, int nf, float* r, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  input_scale_kernel<<<(unsigned)ceil_div(n, 256), 256, 0, st>>>(S, n, nf, r);
+  return cudaGetLastError();
+}
+
+// E (n x 64) for the n vectors of the FP32 field-major view V (n = V.nv);
+// r: per-vector input scales (mlp_input_scale).
+cudaError_t mlp_forward(MlpState& M, const VF32& V, const float* r, float* Hpre, float* H, float* E,
+                        cudaStream_t st) {
   const float* b1 = M.w + (int64_t)MLP_HIDDEN * M.d_in;
   const float* b2 = b1 + MLP_HIDDEN + (int64_t)MLP_OUT * MLP_HIDDEN;
-  cudaError_t e = gemm(V.nv, MLP_HIDDEN, M.d_in, XLog{V.p, V.ld}, RowBF{M.w1b, M.d_in},
+  cudaError_t e = gemm(V.nv, MLP_HIDDEN, M.d_in, XLog{V.p, V.ld, r}, RowBF{M.w1b, M.d_in},
                        EpiHidden{b1, Hpre, H}, st);
   if (e != cudaSuccess) return e;
   return gemm(V.nv, MLP_OUT, MLP_HIDDEN, RowF{H, MLP_HIDDEN}, RowBF{M.w2b, MLP_HIDDEN}, EpiOut{b2, E},
@@ -233,12 +275,12 @@ cudaError_t mlp_forward(MlpState& M, const VF32& V, float* Hpre, float* H, float
 }
 
 // Gradient of the mean pair loss w.r.t. all parameters (layout as above);
-// loss receives the mean loss.  Buffers: Hpre, H (n x 256), E, dE (n x 64),
-// dH (n x 256).
-cudaError_t mlp_pair_grad(MlpState& M, const VF32& V, const int* pairs, const float* y, int64_t npairs,
-                          float* Hpre, float* H, float* E, float* dE, float* dH, float* grad,
-                          double* loss, cudaStream_t st) {
-  cudaError_t e = mlp_forward(M, V, Hpre, H, E, st);
+// loss receives the mean loss.  Buffers: Hpre, H, dH (n x 256), E, Pm, dE
+// (n x 64); dE is also used for dP.
+cudaError_t mlp_pair_grad(MlpState& M, const VF32& V, const float* r, const int* pairs, const float* y,
+                          int64_t npairs, float* Hpre, float* H, float* E, float* Pm, float* dE, float* dH,
+                          float* grad, double* loss, cudaStream_t st) {
+  cudaError_t e = mlp_forward(M, V, r, Hpre, H, E, st);
   if (e != cudaSuccess) return e;
   const int n = V.nv;
   const int64_t n1 = (int64_t)MLP_HIDDEN * M.d_in, n2 = (int64_t)MLP_OUT * MLP_HIDDEN;
@@ -246,13 +288,14 @@ cudaError_t mlp_pair_grad(MlpState& M, const VF32& V, const int* pairs, const fl
   float* gb1 = grad + n1;
   float* gW2 = gb1 + MLP_HIDDEN;
   float* gb2 = gW2 + n2;
-  float* gbeta = gb2 + MLP_OUT;
+  if ((e = mlp_softmax(E, n, Pm, st))) return e;
   if ((e = cudaMemsetAsync(dE, 0, (size_t)n * MLP_OUT * sizeof(float), st))) return e;
-  if ((e = cudaMemsetAsync(gbeta, 0, sizeof(float), st))) return e;
   if ((e = cudaMemsetAsync(loss, 0, sizeof(double), st))) return e;
   const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(npairs, 256), 1024));
-  const float* beta = M.w + mlp_param_count(M.d_in) - 1;
-  pair_loss_kernel<<<g, 256, 0, st>>>(E, pairs, y, npairs, beta, dE, loss, gbeta);
+  pair_loss_kernel<<<g, 256, 0, st>>>(Pm, pairs, y, npairs, dE, loss);
+  if ((e = cudaGetLastError())) return e;
+  // dP -> dE in place (each row reads its own dP before writing)
+  softmax_backward_kernel<<<(unsigned)ceil_div(n, 8), 256, 0, st>>>(Pm, dE, n, dE);
   if ((e = cudaGetLastError())) return e;
   // dW2[o][h] = sum_i dE[i][o] H[i][h];  db2 = colsum(dE)
   if ((e = gemm(MLP_OUT, MLP_HIDDEN, n, ColF{dE, MLP_OUT}, ColF{H, MLP_HIDDEN}, EpiStore{gW2, MLP_HIDDEN}, st)))
@@ -263,7 +306,7 @@ cudaError_t mlp_pair_grad(MlpState& M, const VF32& V, const int* pairs, const fl
                 EpiReluGrad{Hpre, dH}, st)))
     return e;
   // dW1[h][q] = sum_i dH[i][h] x[i][q];  db1 = colsum(dH)
-  if ((e = gemm(MLP_HIDDEN, M.d_in, n, ColF{dH, MLP_HIDDEN}, XLogT{V.p, V.ld}, EpiStore{gW1, M.d_in}, st)))
+  if ((e = gemm(MLP_HIDDEN, M.d_in, n, ColF{dH, MLP_HIDDEN}, XLogT{V.p, V.ld, r}, EpiStore{gW1, M.d_in}, st)))
     return e;
   colsum_kernel<<<1, 256, 0, st>>>(dH, n, MLP_HIDDEN, gb1);
   return cudaGetLastError();

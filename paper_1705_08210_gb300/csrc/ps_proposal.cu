@@ -3,13 +3,13 @@
 // Not in the paper.  The exact thresholded search visits every 128-tile
 // block (I <= J <= K) of the tetrahedron.  Two ways to visit fewer:
 //
-//  * learned (use_proposal = 1): the encoder of ps_mlp.cu embeds every
-//    vector; vectors are reordered by their embedding's arg-max coordinate
-//    (a learned cluster), so vectors that form high-c3 triples land in the
-//    same tiles; for every tile pair the maximum pair score
-//    z = e_a . e_b + beta is taken, and a block is proposed when its three
-//    tile pairs all reach the threshold theta calibrated on the training
-//    data.  Recall is measured against the exhaustive search.
+//  * learned (use_proposal = 1): the encoder of ps_mlp.cu assigns every
+//    vector a soft cluster p = softmax(e) over 64 learned clusters; vectors
+//    are reordered by their most likely cluster, so vectors that form
+//    high-c3 triples land in the same tiles; for every tile pair the maximum
+//    pair score P = p_a . p_b is taken, and a block is proposed when its
+//    three tile pairs all reach the threshold theta calibrated on the
+//    training data.  Recall is measured against the exhaustive search.
 //  * bound (use_proposal = 2, lossless): from min(a,b,c) >= min(a,b) +
 //    min(a,c) - a, n3' >= n2(ij) + n2(ik) - S_i (and its two rotations), so
 //    c3 <= 1.5 min(n2ij+n2ik+n2jk, n2jk+S_i, n2ik+S_j, n2ij+S_k) / d3.
@@ -68,9 +68,8 @@ __global__ void gather_kernel(VF32 V, const double* __restrict__ S, const int* _
 }
 
 // Tmax[A][B] = Tmax[B][A] = max over a in tile A, b in tile B (a < b) of
-// e_a . e_b + beta; one block per tile pair A <= B.
+// P = p_a . p_b (p: cluster probabilities); one block per tile pair A <= B.
 __global__ void __launch_bounds__(256) tile_pair_max_kernel(const float* __restrict__ E, int n, int T,
-                                                            const float* __restrict__ beta_p,
                                                             float* __restrict__ Tmax) {
   __shared__ float ea[PT][MLP_OUT + 1];
   __shared__ float eb[PT][MLP_OUT + 1];
@@ -87,13 +86,12 @@ __global__ void __launch_bounds__(256) tile_pair_max_kernel(const float* __restr
     eb[r][d] = ib < n ? E[(int64_t)ib * MLP_OUT + d] : 0.f;
   }
   __syncthreads();
-  const float beta = *beta_p;
   float best = -INFINITY;
   for (int e = threadIdx.x; e < PT * PT; e += 256) {
     const int r = e / PT, c = e % PT;
     const int ia = A * PT + r, ib = B * PT + c;
     if (ia >= n || ib >= n || ia >= ib) continue;
-    float z = beta;
+    float z = 0.f;
 #pragma unroll 16
     for (int d = 0; d < MLP_OUT; ++d) z = fmaf(ea[r][d], eb[c][d], z);
     best = fmaxf(best, z);
@@ -110,14 +108,14 @@ __global__ void __launch_bounds__(256) tile_pair_max_kernel(const float* __restr
   }
 }
 
-// Pair scores z for a list of pairs.
+// Pair scores P = p_i . p_j for a list of pairs.
 __global__ void pair_score_kernel(const float* __restrict__ E, const int* __restrict__ pairs, int64_t np,
-                                  const float* __restrict__ beta_p, float* __restrict__ z) {
+                                  float* __restrict__ z) {
   for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < np;
        p += (int64_t)gridDim.x * blockDim.x) {
     const float* ei = E + (int64_t)pairs[2 * p] * MLP_OUT;
     const float* ej = E + (int64_t)pairs[2 * p + 1] * MLP_OUT;
-    float s = *beta_p;
+    float s = 0.f;
     for (int d = 0; d < MLP_OUT; ++d) s = fmaf(ei[d], ej[d], s);
     z[p] = s;
   }
@@ -217,7 +215,7 @@ ps_status mlp_alloc(ps_ctx* h, int d_in, uint64_t seed) {
   M.v = M.m + n;
   M.w1b = reinterpret_cast<__nv_bfloat16*>(reinterpret_cast<uintptr_t>(M.v + n + 64) & ~(uintptr_t)255);
   M.w2b = M.w1b + n1;
-  // Glorot-uniform weights, zero biases, beta = 0 (host generator)
+  // Glorot-uniform weights, zero biases (host generator)
   std::vector<float> w((size_t)n, 0.f);
   uint64_t s = seed;
   const float a1 = std::sqrt(6.f / (float)(d_in + MLP_HIDDEN)), a2 = std::sqrt(6.f / (float)(MLP_HIDDEN + MLP_OUT));
@@ -246,7 +244,7 @@ ps_status proposal_reorder(ps_ctx* h, const VF32& v, const double* S, cudaStream
   if (v.nf != M.d_in)
     return fail(h, PS_ERR_INVALID_ARG, "encoder expects nf=%d, matrix has nf=%d", M.d_in, v.nf);
   const int64_t ldp = round_up(n, 4);
-  float* buf = static_cast<float*>(ws_get(h, WS_MLP, (size_t)n * (2 * MLP_HIDDEN + MLP_OUT) * 4));
+  float* buf = static_cast<float*>(ws_get(h, WS_MLP, (size_t)n * (2 * MLP_HIDDEN + 2 * MLP_OUT + 1) * 4));
   float* vperm = static_cast<float*>(ws_get(h, WS_PERMV, (size_t)v.nf * ldp * 4 + (size_t)n * 8 + 256));
   unsigned char* sortb = static_cast<unsigned char*>(ws_get(h, WS_HITS, (size_t)n * 24 + 256));
   int* dperm = static_cast<int*>(ws_get(h, WS_PERM, (size_t)n * 4 + 256));
@@ -256,9 +254,11 @@ ps_status proposal_reorder(ps_ctx* h, const VF32& v, const double* S, cudaStream
   float* Hpre = buf;
   float* H = Hpre + (size_t)n * MLP_HIDDEN;
   float* E = H + (size_t)n * MLP_HIDDEN;
+  float* r = E + (size_t)n * 2 * MLP_OUT;
   {
     ScopedTimer tm(h, "proposal_encode", st);
-    PS_CUDA_TRY(h, mlp_forward(M, v, Hpre, H, E, st));
+    PS_CUDA_TRY(h, mlp_input_scale(S, n, v.nf, r, st));
+    PS_CUDA_TRY(h, mlp_forward(M, v, r, Hpre, H, E, st));
   }
   unsigned long long* keys = reinterpret_cast<unsigned long long*>(sortb);
   unsigned long long* ktmp = keys + n;
@@ -282,22 +282,25 @@ ps_status proposal_reorder(ps_ctx* h, const VF32& v, const double* S, cudaStream
 
 // Learned proposal on the reordered view: blocks whose three tile pairs
 // reach theta.  Returns the fraction of blocks kept in *kept.
-ps_status proposal_blocks_learned(ps_ctx* h, const VF32& vp, cudaStream_t st, std::vector<int>* blk,
-                                  double* kept) {
+ps_status proposal_blocks_learned(ps_ctx* h, const VF32& vp, const double* Sp, cudaStream_t st,
+                                  std::vector<int>* blk, double* kept) {
   MlpState& M = h->mlp;
   const int n = vp.nv;
   const int T = (int)ceil_div(n, PT);
-  float* buf = static_cast<float*>(ws_get(h, WS_MLP, (size_t)n * (2 * MLP_HIDDEN + MLP_OUT) * 4));
+  float* buf = static_cast<float*>(ws_get(h, WS_MLP, (size_t)n * (2 * MLP_HIDDEN + 2 * MLP_OUT + 1) * 4));
   float* tmax = static_cast<float*>(ws_get(h, WS_AUX2, (size_t)T * T * 4 + 256));
   if (!buf || !tmax) return PS_ERR_OOM;
   float* Hpre = buf;
   float* H = Hpre + (size_t)n * MLP_HIDDEN;
   float* E = H + (size_t)n * MLP_HIDDEN;
+  float* Pm = E + (size_t)n * MLP_OUT;
+  float* r = Pm + (size_t)n * MLP_OUT;
   {
     ScopedTimer tm(h, "proposal_score", st);
-    PS_CUDA_TRY(h, mlp_forward(M, vp, Hpre, H, E, st));
-    const float* beta = M.w + mlp_param_count(M.d_in) - 1;
-    tile_pair_max_kernel<<<(unsigned)((int64_t)T * (T + 1) / 2), 256, 0, st>>>(E, n, T, beta, tmax);
+    PS_CUDA_TRY(h, mlp_input_scale(Sp, n, vp.nf, r, st));
+    PS_CUDA_TRY(h, mlp_forward(M, vp, r, Hpre, H, E, st));
+    PS_CUDA_TRY(h, mlp_softmax(E, n, Pm, st));
+    tile_pair_max_kernel<<<(unsigned)((int64_t)T * (T + 1) / 2), 256, 0, st>>>(Pm, n, T, tmax);
     PS_CUDA_TRY(h, cudaGetLastError());
   }
   std::vector<float> tm_h((size_t)T * T);
@@ -425,20 +428,25 @@ extern "C" ps_status ps_proposal_pair_grad(ps_handle h, const ps_matrix* V, cons
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   const int n = (int)V->nv;
   const VF32 v{static_cast<const float*>(V->data), V->ld, n, (int)V->nf};
-  float* buf = static_cast<float*>(ws_get(h, WS_MLP, (size_t)n * (3 * MLP_HIDDEN + 2 * MLP_OUT) * 4 + 1024));
+  float* buf = static_cast<float*>(ws_get(h, WS_MLP, (size_t)n * (3 * MLP_HIDDEN + 3 * MLP_OUT + 1) * 4 + 1024));
   double* dloss = static_cast<double*>(ws_get(h, WS_AUX3, 256));
-  if (!buf || !dloss) return PS_ERR_OOM;
+  double* dS = static_cast<double*>(ws_get(h, WS_SUMS, (size_t)std::max(n, 1) * 8));
+  if (!buf || !dloss || !dS) return PS_ERR_OOM;
   float* Hpre = buf;
   float* H = Hpre + (size_t)n * MLP_HIDDEN;
   float* E = H + (size_t)n * MLP_HIDDEN;
-  float* dE = E + (size_t)n * MLP_OUT;
+  float* Pm = E + (size_t)n * MLP_OUT;
+  float* dE = Pm + (size_t)n * MLP_OUT;
   float* dH = dE + (size_t)n * MLP_OUT;
-  cudaError_t e;
-  if (grad && npairs > 0) {
-    e = mlp_pair_grad(h->mlp, v, pairs, labels, npairs, Hpre, H, E, dE, dH, grad, dloss, st);
+  float* r = dH + (size_t)n * MLP_HIDDEN;
+  cudaError_t e = launch_vector_sums(*V, dS, st);
+  if (e == cudaSuccess) e = mlp_input_scale(dS, n, (int)V->nf, r, st);
+  if (e != cudaSuccess) {
+  } else if (grad && npairs > 0) {
+    e = mlp_pair_grad(h->mlp, v, r, pairs, labels, npairs, Hpre, H, E, Pm, dE, dH, grad, dloss, st);
     if (e == cudaSuccess && loss) e = cudaMemcpyAsync(loss, dloss, 8, cudaMemcpyDefault, st);
   } else {
-    e = mlp_forward(h->mlp, v, Hpre, H, E, st);
+    e = mlp_forward(h->mlp, v, r, Hpre, H, E, st);
   }
   if (e == cudaSuccess && E_out) e = cudaMemcpyAsync(E_out, E, (size_t)n * MLP_OUT * 4, cudaMemcpyDefault, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -467,6 +475,7 @@ extern "C" ps_status ps_proposal_train(ps_handle h, const ps_matrix* train, int3
   DevBuf mem;
   struct Set {
     VF32 v;
+    float* r;
     int* pairs;
     float* y;
     int64_t np;
@@ -523,6 +532,16 @@ extern "C" ps_status ps_proposal_train(ps_handle h, const ps_matrix* train, int3
     }
     Set S;
     S.v = VF32{static_cast<const float*>(V.data), V.ld, n, (int)V.nf};
+    double* sums = static_cast<double*>(mem.get((size_t)n * 8));
+    S.r = static_cast<float*>(mem.get((size_t)n * 4));
+    if (!sums || !S.r) {
+      s = fail(h, PS_ERR_OOM, "training scales");
+      break;
+    }
+    if (launch_vector_sums(V, sums, st) != cudaSuccess || mlp_input_scale(sums, n, (int)V.nf, S.r, st) != cudaSuccess) {
+      s = fail(h, PS_ERR_CUDA, "training scales");
+      break;
+    }
     S.np = (int64_t)yy.size();
     S.npos = (int64_t)posset.size();
     S.pairs = static_cast<int*>(mem.get(pr.size() * 4));
@@ -540,7 +559,7 @@ extern "C" ps_status ps_proposal_train(ps_handle h, const ps_matrix* train, int3
     int nmax = 0;
     for (const Set& S : sets) nmax = std::max(nmax, S.v.nv);
     const int64_t np_all = mlp_param_count(h->mlp.d_in);
-    float* buf = static_cast<float*>(mem.get((size_t)nmax * (3 * MLP_HIDDEN + 2 * MLP_OUT) * 4));
+    float* buf = static_cast<float*>(mem.get((size_t)nmax * (3 * MLP_HIDDEN + 3 * MLP_OUT) * 4));
     float* grad = static_cast<float*>(mem.get((size_t)np_all * 4));
     double* dloss = static_cast<double*>(mem.get(8));
     if (!buf || !grad || !dloss) s = fail(h, PS_ERR_OOM, "training state");
@@ -551,9 +570,10 @@ extern "C" ps_status ps_proposal_train(ps_handle h, const ps_matrix* train, int3
       float* Hpre = buf;
       float* H = Hpre + (size_t)n * MLP_HIDDEN;
       float* E = H + (size_t)n * MLP_HIDDEN;
-      float* dE = E + (size_t)n * MLP_OUT;
+      float* Pm = E + (size_t)n * MLP_OUT;
+      float* dE = Pm + (size_t)n * MLP_OUT;
       float* dH = dE + (size_t)n * MLP_OUT;
-      cudaError_t e = mlp_pair_grad(h->mlp, S.v, S.pairs, S.y, S.np, Hpre, H, E, dE, dH, grad, dloss, st);
+      cudaError_t e = mlp_pair_grad(h->mlp, S.v, S.r, S.pairs, S.y, S.np, Hpre, H, E, Pm, dE, dH, grad, dloss, st);
       if (e == cudaSuccess) e = mlp_adam(h->mlp, grad, lr, st);
       if (e != cudaSuccess) s = cuda_fail(h, e, "training step");
       if (it == steps - 1 && s == PS_OK) {
@@ -570,10 +590,11 @@ extern "C" ps_status ps_proposal_train(ps_handle h, const ps_matrix* train, int3
       float* H = Hpre + (size_t)n * MLP_HIDDEN;
       float* E = H + (size_t)n * MLP_HIDDEN;
       float* zz = static_cast<float*>(mem.get((size_t)std::max<int64_t>(S.npos, 1) * 4));
-      cudaError_t e = mlp_forward(h->mlp, S.v, Hpre, H, E, st);
-      const float* beta = h->mlp.w + np_all - 1;
+      float* Pm = E + (size_t)n * MLP_OUT;
+      cudaError_t e = mlp_forward(h->mlp, S.v, S.r, Hpre, H, E, st);
+      if (e == cudaSuccess) e = mlp_softmax(E, n, Pm, st);
       if (e == cudaSuccess && S.npos > 0) {
-        pair_score_kernel<<<256, 256, 0, st>>>(E, S.pos, S.npos, beta, zz);
+        pair_score_kernel<<<256, 256, 0, st>>>(Pm, S.pos, S.npos, zz);
         e = cudaGetLastError();
       }
       std::vector<float> hz((size_t)S.npos);
@@ -588,7 +609,7 @@ extern "C" ps_status ps_proposal_train(ps_handle h, const ps_matrix* train, int3
       if (!zs.empty()) {
         const size_t q = (size_t)std::floor((1.0 - (double)target_recall) * (double)zs.size());
         theta = zs[std::min(q, zs.size() - 1)];
-        theta -= 1e-3f * (1.f + std::fabs(theta));
+        theta *= 0.999f;
       }
       h->mlp.theta = theta;
       h->mlp.trained = true;

@@ -11,7 +11,7 @@ def test_pair_gradient_matches_finite_differences():
     d_in, nv = 6, 9
     V = rng.exponential(1.0, size=(d_in, nv))
     V[rng.random((d_in, nv)) < 0.5] = 0.0
-    n = mo.HIDDEN * d_in + mo.HIDDEN + mo.OUT * mo.HIDDEN + mo.OUT + 1
+    n = mo.n_params(d_in)
     theta = rng.normal(0, 0.2, size=n)
     pairs = np.array([[0, 1], [2, 5], [3, 4], [1, 8], [0, 7], [6, 8]])
     y = np.array([1, 0, 1, 0, 1, 0], dtype=np.float64)
@@ -26,6 +26,15 @@ def test_pair_gradient_matches_finite_differences():
         tm = theta.copy(); tm[k] -= eps
         num = (mo.pair_loss_and_grad(tp, V, pairs, y)[0] - mo.pair_loss_and_grad(tm, V, pairs, y)[0]) / (2 * eps)
         assert abs(num - grad[k]) <= 1e-6 * max(1.0, abs(num)), (k, num, grad[k])
+
+
+def test_softmax_pair_score_is_a_probability():
+    rng = np.random.default_rng(1)
+    E = rng.normal(0, 3, size=(10, mo.OUT))
+    P = mo.softmax(E)
+    np.testing.assert_allclose(P.sum(axis=1), 1.0, rtol=1e-14)
+    S = P @ P.T
+    assert np.all(S >= 0) and np.all(S <= 1 + 1e-12)
 
 
 def test_bf16_rounding():
