@@ -205,6 +205,29 @@ ps_status ps_threshold_3way(ps_handle h, const ps_matrix* V, float tau,
                             ps_stream stream);
 
 /* ---------------------------------------------------------------------------
+ * Sharding over several GPUs (one process per GPU; V replicated, no
+ * collective on the data path).  The paper splits the vector axis over nodes
+ * with circulant exchanges (Section 4.1); with V resident on every GPU the
+ * unique outputs are simply split into equal-work contiguous ranges.
+ *
+ * ps_partition: host-only (no GPU needed).  way 2: rows [begin, end) of the
+ *   packed triangle (128-row bands, ~1/nparts of the pairs each); their
+ *   outputs are packed entries [out_begin, out_end).  way 3: pivots
+ *   [begin, end) (pass them to ps_metrics_3way), slab entries
+ *   [out_begin, out_end) of the full pivot range.  out_begin / out_end may
+ *   be NULL.  Parts are disjoint and cover everything.
+ * ps_metrics_2way_part: the pairs of rows [begin, end) of part `part`,
+ *   written at their packed positions of the full nv*(nv-1)/2 DEVICE array
+ *   `out` (other entries untouched); FP32 path.
+ * Errors: PS_ERR_INVALID_ARG for bad sizes or part indices. */
+ps_status ps_partition(int64_t nv, int32_t way, int32_t nparts, int32_t part,
+                       int64_t* begin, int64_t* end, int64_t* out_begin,
+                       int64_t* out_end);
+ps_status ps_metrics_2way_part(ps_handle h, const ps_matrix* V, int32_t nparts,
+                               int32_t part, void* out, int32_t out_dtype,
+                               ps_stream stream);
+
+/* ---------------------------------------------------------------------------
  * Batched uneven instances (not in the paper, whose unit of work is one
  * large decomposed problem, Section 4).  Each problem: */
 typedef struct {

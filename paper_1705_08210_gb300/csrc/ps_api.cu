@@ -515,6 +515,57 @@ ps_status ps_metrics_2way(ps_handle h, const ps_matrix* V, int32_t path, int32_t
   return finish(h, o, P.host_input || o.host, st);
 }
 
+ps_status ps_partition(int64_t nv, int32_t way, int32_t nparts, int32_t part, int64_t* begin,
+                       int64_t* end, int64_t* out_begin, int64_t* out_end) {
+  if (nv < way || (way != 2 && way != 3) || nparts < 1 || part < 0 || part >= nparts || !begin || !end)
+    return fail(nullptr, PS_ERR_INVALID_ARG, "ps_partition: bad arguments");
+  if (way == 2) {
+    partition_2way(nv, nparts, part, begin, end);
+    auto idx = [nv](int64_t i) { return i * (2 * nv - i - 1) / 2; };  // first pair of row i
+    if (out_begin) *out_begin = idx(*begin);
+    if (out_end) *out_end = idx(*end);
+  } else {
+    partition_3way(nv, nparts, part, begin, end);
+    if (out_begin) *out_begin = ps_slab_size(nv, 0, *begin);
+    if (out_end) *out_end = ps_slab_size(nv, 0, *end);
+  }
+  return PS_OK;
+}
+
+ps_status ps_metrics_2way_part(ps_handle h, const ps_matrix* V, int32_t nparts, int32_t part,
+                               void* out, int32_t out_dtype, ps_stream stream) {
+  if (!h) return fail(nullptr, PS_ERR_INVALID_ARG, "null handle");
+  ps_status s = check_matrix(h, V, 2);
+  if (s != PS_OK) return s;
+  if (nparts < 1 || part < 0 || part >= nparts) return fail(h, PS_ERR_INVALID_ARG, "part %d of %d", part, nparts);
+  if (!out) return fail(h, PS_ERR_INVALID_ARG, "null out");
+  if (out_dtype != PS_F32 && out_dtype != PS_F64)
+    return fail(h, PS_ERR_INVALID_ARG, "out_dtype %d is not PS_F32/PS_F64", out_dtype);
+  Guard g(h->device);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  int64_t rb = 0, re = 0;
+  partition_2way(V->nv, nparts, part, &rb, &re);
+  const int64_t npairs = V->nv * (V->nv - 1) / 2;
+  OutBuf o;
+  s = resolve_out(h, out, (size_t)npairs * dtype_size(out_dtype), WS_OUTPUT, &o);
+  if (s != PS_OK) return s;
+  if (o.host) return fail(h, PS_ERR_INVALID_ARG, "ps_metrics_2way_part needs a device output");
+  Prepared P;
+  s = prepare(h, *V, st, true, &P);
+  if (s != PS_OK) return s;
+  {
+    ScopedTimer tm(h, "mgemm2", st);
+    // row bands are whole 128-row tiles; the kernels use 128-wide tiles here
+    const int keep_tile = h->mgemm_tile;
+    h->mgemm_tile = 128;
+    const cudaError_t e = launch_mgemm2(h, P.f32, P.S, o.dev, out_dtype == PS_F64 ? OUT2_C2_F64 : OUT2_C2_F32,
+                                        st, (int)(rb / 128), (int)ceil_div(re, 128));
+    h->mgemm_tile = keep_tile;
+    PS_CUDA_TRY(h, e);
+  }
+  return finish(h, o, P.host_input, st);
+}
+
 ps_status ps_metrics_3way(ps_handle h, const ps_matrix* V, int64_t j_begin, int64_t j_end,
                           float* out_slab, ps_stream stream) {
   if (!h) return fail(nullptr, PS_ERR_INVALID_ARG, "null handle");

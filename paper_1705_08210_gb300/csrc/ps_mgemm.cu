@@ -145,17 +145,62 @@ int mgemm_variant_code(const ps_ctx* h) {
 }
 
 cudaError_t launch_mgemm2(ps_ctx* h, const VF32& V, const double* S, void* out, int mode,
-                          cudaStream_t st) {
+                          cudaStream_t st, int tile_begin, int tile_end) {
   const int code = mgemm_variant_code(h);
   const MgemmVariant* v = mgemm_variant_of(code);
   cudaError_t e = ensure_attrs(h, code, v);
   if (e != cudaSuccess) return e;
   const int T = (int)ceil_div(V.nv, v->tile);
-  const int64_t ntiles = (int64_t)T * (T + 1) / 2;
-  if (ntiles == 0) return cudaSuccess;
+  const int64_t I0 = std::max(0, tile_begin), I1 = tile_end < 0 ? T : std::min(tile_end, T);
+  if (I1 <= I0) return cudaSuccess;
+  // tiles in rows [0, I) of the triangle: I*T - I(I-1)/2
+  const int64_t tbase = I0 * T - I0 * (I0 - 1) / 2;
+  const int64_t ntiles = (I1 * T - I1 * (I1 - 1) / 2) - tbase;
   const unsigned grid = (unsigned)std::min<int64_t>(ntiles, (int64_t)h->num_sms * v->minb);
-  v->mgemm2(grid, st, V, S, out, mode, T, ntiles);
+  v->mgemm2(grid, st, V, S, out, mode, T, tbase, ntiles);
   return cudaGetLastError();
+}
+
+void partition_2way(int64_t nv, int nparts, int part, int64_t* row_begin, int64_t* row_end) {
+  // pairs in 128-row band b: rows i in [128b, 128b+128), each with nv-1-i
+  // partners; bands are assigned so that every part gets ~1/nparts of them
+  const int64_t T = ceil_div(nv, 128);
+  const double total = (double)nv * (double)(nv - 1) / 2.0;
+  auto rows_pairs = [nv](int64_t r) {  // pairs in rows [0, r)
+    return (double)r * (double)(nv - 1) - (double)r * (double)(r - 1) / 2.0;
+  };
+  auto cut = [&](int p) -> int64_t {
+    if (p <= 0) return 0;
+    if (p >= nparts) return T;
+    const double target = total * (double)p / (double)nparts;
+    int64_t b = 0;
+    while (b < T && rows_pairs(std::min(nv, (b + 1) * 128)) <= target) ++b;
+    // nearer of the two band edges around the target
+    if (b < T && target - rows_pairs(std::min(nv, b * 128)) > rows_pairs(std::min(nv, (b + 1) * 128)) - target)
+      ++b;
+    return b;
+  };
+  *row_begin = std::min(nv, cut(part) * 128);
+  *row_end = std::min(nv, cut(part + 1) * 128);
+}
+
+void partition_3way(int64_t nv, int nparts, int part, int64_t* j_begin, int64_t* j_end) {
+  // pivot j owns j (nv-1-j) triples; equal prefix shares
+  const double total = (double)nv * (double)(nv - 1) * (double)(nv - 2) / 6.0;
+  auto cut = [&](int p) -> int64_t {
+    if (p <= 0) return 0;
+    if (p >= nparts) return nv;
+    const double target = total * (double)p / (double)nparts;
+    double acc = 0.0;
+    for (int64_t j = 0; j < nv; ++j) {
+      const double w = (double)j * (double)(nv - 1 - j);
+      if (acc + w / 2.0 > target) return j;
+      acc += w;
+    }
+    return nv;
+  };
+  *j_begin = cut(part);
+  *j_end = cut(part + 1);
 }
 
 int64_t pivot_tile_count(int nv, int64_t jb, int64_t je, int B) {

@@ -335,7 +335,7 @@ __host__ __device__ __forceinline__ int64_t pivot_tiles(int nv, int64_t j, int B
 template <class C, bool PACKED, int KU>
 __global__ void __launch_bounds__(C::NT, C::MINB)
     mgemm2_kernel(VF32 V, const double* __restrict__ S, void* __restrict__ out, int mode, int T,
-                  int64_t ntiles) {
+                  int64_t tbase, int64_t ntiles) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Smem<C>& sm = *reinterpret_cast<Smem<C>*>(smem_raw);
   const Lanes<C> L;
@@ -343,7 +343,7 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
   const int64_t nv = V.nv;
   for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
     int I, J;
-    tri_tile(t, T, I, J);
+    tri_tile(tbase + t, T, I, J);
     const int row0 = I * C::BM, col0 = J * C::BN;
     tile_minsum<C, false, PACKED, KU>(sm, V, row0, col0, 0, L.am, L.bn, acc);
 #pragma unroll
@@ -656,8 +656,8 @@ struct Launch {
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   }
   static void mgemm2(unsigned grid, cudaStream_t st, const VF32& V, const double* S, void* out,
-                     int mode, int T, int64_t ntiles) {
-    mgemm2_kernel<C, PACKED, KU><<<grid, C::NT, smem, st>>>(V, S, out, mode, T, ntiles);
+                     int mode, int T, int64_t tbase, int64_t ntiles) {
+    mgemm2_kernel<C, PACKED, KU><<<grid, C::NT, smem, st>>>(V, S, out, mode, T, tbase, ntiles);
   }
   static void mgemm3(unsigned grid, cudaStream_t st, const VF32& V, const double* S,
                      const float* n2sq, const int64_t* pref, int npiv, int jb, float* out,

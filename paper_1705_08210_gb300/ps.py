@@ -87,6 +87,10 @@ ps_proposal_train = _sig("ps_proposal_train", ctypes.c_int,
                           _p, _p])
 ps_proposal_last_stats = _sig("ps_proposal_last_stats", ctypes.c_int,
                               [_h, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_i64)])
+ps_partition = _sig("ps_partition", ctypes.c_int,
+                    [_i64, _i32, _i32, _i32, ctypes.POINTER(_i64), ctypes.POINTER(_i64), ctypes.POINTER(_i64),
+                     ctypes.POINTER(_i64)])
+ps_metrics_2way_part = _sig("ps_metrics_2way_part", ctypes.c_int, [_h, _M, _i32, _i32, _p, _i32, _p])
 ps_metrics_2way_static = _sig("ps_metrics_2way_static", ctypes.c_int, [_M, _p, _i32, _p])
 ps_probe_minadd_peak = _sig("ps_probe_minadd_peak", ctypes.c_int,
                             [_h, _i32, ctypes.POINTER(ctypes.c_double)])

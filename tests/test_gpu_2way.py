@@ -126,3 +126,18 @@ def test_config2_full_size_sampled(ps, handle):
     ref = oracle.c2_pairs(Vv, rp)
     err = assert_rel(got, ref, RTOL32, "config2 sampled")
     print(f"config2 sampled max rel err {err:.3e}")
+
+
+def test_parts_assemble_full_result(ps, handle):
+    import torch
+    nv, nf = 1000, 300
+    V = synth.zero_inflated(nv, nf, synth.seed_for(1, 31))
+    full = metrics_2way(ps, handle, V)
+    X = torch.from_numpy(V).cuda()
+    m = ps.matrix(X)
+    out = torch.full((nv * (nv - 1) // 2,), float("nan"), device="cuda")
+    for p in range(3):
+        ps.check(ps.ps_metrics_2way_part(handle.h, ctypes.byref(m), 3, p, out.data_ptr(), 0,
+                                         torch.cuda.current_stream().cuda_stream), handle.h)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(out.cpu().numpy(), full)
