@@ -413,6 +413,7 @@ ps_status ps_create(ps_handle* out, int device) {
     if (ku == 4 || ku == 8 || ku == 16) h->mgemm_ku = ku;
   }
   if (const char* v = getenv("PS_MGEMM_TILE")) h->mgemm_tile = atoi(v) == 64 ? 64 : 128;
+  if (const char* v = getenv("PS_MGEMM_WARPS")) h->mgemm_warps = atoi(v) == 16 ? 16 : 8;
   if (prop.major < 10) {
     delete h;
     return fail(nullptr, PS_ERR_UNSUPPORTED, "device %d is sm_%d%d; this library is built for sm_103a",
@@ -557,7 +558,7 @@ ps_status ps_metrics_2way_part(ps_handle h, const ps_matrix* V, int32_t nparts, 
     ScopedTimer tm(h, "mgemm2", st);
     // row bands are whole 128-row tiles; the kernels use 128-wide tiles here
     const int keep_tile = h->mgemm_tile;
-    h->mgemm_tile = 128;
+    h->mgemm_tile = 128;  // (8 or 16 warps per 128 x 128 tile as configured)
     const cudaError_t e = launch_mgemm2(h, P.f32, P.S, o.dev, out_dtype == PS_F64 ? OUT2_C2_F64 : OUT2_C2_F32,
                                         st, (int)(rb / 128), (int)ceil_div(re, 128));
     h->mgemm_tile = keep_tile;

@@ -61,8 +61,8 @@ uint64_t full_signature(const ps_problem* probs, int n, int variant) {
 }
 
 // candidate configurations of the autotuner (see mgemm_variant_code):
-// tile 128 or 64 x unroll depth 16, 8, 4, all with packed adds
-const int kVariants[6] = {108, 116, 104, 1108, 1116, 1104};
+// tile 128 (8 or 16 warps) or 64 x unroll depth 16, 8, 4, all packed adds
+const int kVariants[9] = {108, 116, 104, 1108, 1116, 1104, 2108, 2116, 2104};
 
 bool is_device(const void* p) {
   cudaPointerAttributes a;
@@ -344,9 +344,10 @@ extern "C" ps_status ps_autotune_batched(ps_handle h, const ps_problem* probs, i
   }
   h->batch->tuned[sig] = best;
   if (choice && choice_len > 0) {
-    snprintf(choice, (size_t)choice_len, "tile %d x %d, %s add, %d-step unroll%s",
-             best / 1000 ? 64 : 128, best / 1000 ? 64 : 128, (best / 100) % 10 ? "packed f32x2" : "scalar",
-             best % 100, detail.empty() ? " (cached)" : "");
+    const int shape = best / 1000;
+    snprintf(choice, (size_t)choice_len, "tile %d x %d (%d warps), %s add, %d-step unroll%s",
+             shape == 1 ? 64 : 128, shape == 1 ? 64 : 128, shape == 1 ? 2 : (shape == 2 ? 16 : 8),
+             (best / 100) % 10 ? "packed f32x2" : "scalar", best % 100, detail.empty() ? " (cached)" : "");
   }
   return PS_OK;
 }

@@ -119,7 +119,7 @@ __global__ void __launch_bounds__(1024) pivot_prefix_kernel(int nv, int jb, int 
 }
 
 std::mutex g_attr_mu;
-uint64_t g_attr_done[2048] = {};  // per variant code: bit d = attributes set on device d
+uint64_t g_attr_done[4096] = {};  // per variant code: bit d = attributes set on device d
 
 cudaError_t ensure_attrs(ps_ctx* h, int code, const MgemmVariant* v) {
   std::lock_guard<std::mutex> lk(g_attr_mu);
@@ -133,15 +133,16 @@ cudaError_t ensure_attrs(ps_ctx* h, int code, const MgemmVariant* v) {
 }  // namespace
 
 const MgemmVariant* mgemm_variant_of(int code) {
-  const int tile64 = code / 1000, packed = (code / 100) % 10, ku = code % 100;
-  if (tile64) return mgemm_variant_t64(ku);
+  const int shape = code / 1000, packed = (code / 100) % 10, ku = code % 100;
+  if (shape == 1) return mgemm_variant_t64(ku);
+  if (shape == 2) return mgemm_variant_t128w16(ku);
   return mgemm_variant_t128(packed, ku);
 }
 
 int mgemm_variant_code(const ps_ctx* h) {
-  const int tile64 = h->mgemm_tile == 64 ? 1 : 0;
-  const int packed = tile64 ? 1 : (h->mgemm_packed_add ? 1 : 0);
-  return tile64 * 1000 + packed * 100 + h->mgemm_ku;
+  const int shape = h->mgemm_tile == 64 ? 1 : (h->mgemm_warps == 16 ? 2 : 0);
+  const int packed = shape ? 1 : (h->mgemm_packed_add ? 1 : 0);
+  return shape * 1000 + packed * 100 + h->mgemm_ku;
 }
 
 cudaError_t launch_mgemm2(ps_ctx* h, const VF32& V, const double* S, void* out, int mode,

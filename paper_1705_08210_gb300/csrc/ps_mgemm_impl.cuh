@@ -32,10 +32,12 @@ namespace mg {
 constexpr int BK = 16, STAGES = 4;
 constexpr int FOLD = 4;  // stages (of BK fields) per compensated fold: 64 fields
 
-template <int WM_, int WN_, int MINB_>
+// WM x WN warps; a warp owns 64 rows x 4*NJ columns, a lane 8 x NJ outputs
+// (NJ = 8: two 4-column groups 16 apart; NJ = 4: one group).
+template <int WM_, int WN_, int MINB_, int NJ_ = 8>
 struct TileCfg {
-  static constexpr int WM = WM_, WN = WN_;
-  static constexpr int BM = 64 * WM, BN = 32 * WN;
+  static constexpr int WM = WM_, WN = WN_, NJ = NJ_;
+  static constexpr int BM = 64 * WM, BN = 4 * NJ * WN;
   static constexpr int NT = 32 * WM * WN;
   static constexpr int MINB = MINB_;               // resident CTAs per SM
   static constexpr int CHA = BK * BM / 4 / NT;    // 16-byte A chunks per thread
@@ -45,6 +47,7 @@ struct TileCfg {
 };
 using T128 = TileCfg<2, 4, 1>;
 using T64 = TileCfg<1, 2, 4>;
+using T128W16 = TileCfg<2, 8, 1, 4>;  // 128 x 128, 16 warps of 8 x 4 outputs per lane
 
 template <class C>
 struct __align__(16) Smem {
@@ -154,34 +157,35 @@ __device__ __forceinline__ float2 f2_unpack(unsigned long long v) {
   return r;
 }
 
-// Per-thread accumulators for 8 x 8 outputs: "lo" accumulates up to 64
+// Per-thread accumulators for 8 x NJ outputs: "lo" accumulates up to 64
 // fields; fold() moves it into "hi" with an exact TwoSum and leaves the
 // rounding residual in "lo".  PACKED adds pairs with one add.rn.f32x2.
-template <bool PACKED>
+template <bool PACKED, int NJ>
 struct Acc;
 
-template <>
-struct Acc<true> {
-  unsigned long long hi[8][4];
-  unsigned long long lo[8][4];
+template <int NJ>
+struct Acc<true, NJ> {
+  static constexpr int NP = NJ / 2;
+  unsigned long long hi[8][NP];
+  unsigned long long lo[8][NP];
   __device__ __forceinline__ void zero() {
 #pragma unroll
     for (int r = 0; r < 8; ++r)
 #pragma unroll
-      for (int c = 0; c < 4; ++c) hi[r][c] = lo[r][c] = 0ull;
+      for (int c = 0; c < NP; ++c) hi[r][c] = lo[r][c] = 0ull;
   }
-  __device__ __forceinline__ void step(const float (&a)[8], const float (&b)[8]) {
+  __device__ __forceinline__ void step(const float (&a)[8], const float (&b)[NJ]) {
 #pragma unroll
     for (int r = 0; r < 8; ++r)
 #pragma unroll
-      for (int c = 0; c < 4; ++c)
+      for (int c = 0; c < NP; ++c)
         lo[r][c] = f2_add(lo[r][c], fminf(a[r], b[2 * c]), fminf(a[r], b[2 * c + 1]));
   }
   __device__ __forceinline__ void fold() {
 #pragma unroll
     for (int r = 0; r < 8; ++r)
 #pragma unroll
-      for (int c = 0; c < 4; ++c) {
+      for (int c = 0; c < NP; ++c) {
         const unsigned long long s = f2_add2(hi[r][c], lo[r][c]);
         const unsigned long long bp = f2_sub2(s, hi[r][c]);
         const unsigned long long ap = f2_sub2(s, bp);
@@ -197,27 +201,27 @@ struct Acc<true> {
   }
 };
 
-template <>
-struct Acc<false> {
-  float hi[8][8];
-  float lo[8][8];
+template <int NJ>
+struct Acc<false, NJ> {
+  float hi[8][NJ];
+  float lo[8][NJ];
   __device__ __forceinline__ void zero() {
 #pragma unroll
     for (int r = 0; r < 8; ++r)
 #pragma unroll
-      for (int c = 0; c < 8; ++c) hi[r][c] = lo[r][c] = 0.0f;
+      for (int c = 0; c < NJ; ++c) hi[r][c] = lo[r][c] = 0.0f;
   }
-  __device__ __forceinline__ void step(const float (&a)[8], const float (&b)[8]) {
+  __device__ __forceinline__ void step(const float (&a)[8], const float (&b)[NJ]) {
 #pragma unroll
     for (int r = 0; r < 8; ++r)
 #pragma unroll
-      for (int c = 0; c < 8; ++c) lo[r][c] = __fadd_rn(lo[r][c], fminf(a[r], b[c]));
+      for (int c = 0; c < NJ; ++c) lo[r][c] = __fadd_rn(lo[r][c], fminf(a[r], b[c]));
   }
   __device__ __forceinline__ void fold() {
 #pragma unroll
     for (int r = 0; r < 8; ++r)
 #pragma unroll
-      for (int c = 0; c < 8; ++c) {
+      for (int c = 0; c < NJ; ++c) {
         const float s = __fadd_rn(hi[r][c], lo[r][c]);
         const float bp = __fsub_rn(s, hi[r][c]);
         const float ap = __fsub_rn(s, bp);
@@ -233,25 +237,30 @@ struct Acc<false> {
 // iteration (smaller KU keeps the hot loop in the instruction cache).
 template <class C, bool PACKED, int KU>
 __device__ __forceinline__ void compute_slice(const Smem<C>& sm, int buf, int am, int bn,
-                                              Acc<PACKED>& acc) {
+                                              Acc<PACKED, C::NJ>& acc) {
   const float* As = &sm.A[buf][0][am];
   const float* Bs = &sm.B[buf][0][bn];
 #pragma unroll KU
   for (int kk = 0; kk < BK; ++kk) {
     const float4 a0 = *reinterpret_cast<const float4*>(As + kk * C::BM);
     const float4 a1 = *reinterpret_cast<const float4*>(As + kk * C::BM + 32);
-    const float4 b0 = *reinterpret_cast<const float4*>(Bs + kk * C::BN);
-    const float4 b1 = *reinterpret_cast<const float4*>(Bs + kk * C::BN + 16);
     const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-    const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
-    acc.step(a, b);
+    const float4 b0 = *reinterpret_cast<const float4*>(Bs + kk * C::BN);
+    if constexpr (C::NJ == 8) {
+      const float4 b1 = *reinterpret_cast<const float4*>(Bs + kk * C::BN + 16);
+      const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+      acc.step(a, b);
+    } else {
+      const float b[4] = {b0.x, b0.y, b0.z, b0.w};
+      acc.step(a, b);
+    }
   }
 }
 
 // Full k loop over n_f for one (row0, col0) tile, with optional pivot j.
 template <class C, bool PIVOT, bool PACKED, int KU>
 __device__ __forceinline__ void tile_minsum(Smem<C>& sm, const VF32& V, int row0, int col0,
-                                            int jpiv, int am, int bn, Acc<PACKED>& acc) {
+                                            int jpiv, int am, int bn, Acc<PACKED, C::NJ>& acc) {
   acc.zero();
   const int nst = (V.nf + BK - 1) / BK;
 #pragma unroll
@@ -283,7 +292,7 @@ struct Lanes {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int wm = warp / C::WN, wn = warp % C::WN, lm = lane >> 2, ln = lane & 3;
     am = wm * 64 + lm * 4;
-    bn = wn * 32 + ln * 4;
+    bn = wn * (4 * C::NJ) + ln * 4;
   }
   __device__ __forceinline__ int row(int r) const { return am + (r < 4 ? r : 28 + r); }
   __device__ __forceinline__ int col(int c) const { return bn + (c < 4 ? c : 12 + c); }
@@ -339,7 +348,7 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Smem<C>& sm = *reinterpret_cast<Smem<C>*>(smem_raw);
   const Lanes<C> L;
-  Acc<PACKED> acc;
+  Acc<PACKED, C::NJ> acc;
   const int64_t nv = V.nv;
   for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
     int I, J;
@@ -352,7 +361,7 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
       if (i >= nv) continue;
       const double Si = S ? S[i] : 0.0;
 #pragma unroll
-      for (int c = 0; c < 8; ++c) {
+      for (int c = 0; c < C::NJ; ++c) {
         const int j = col0 + L.col(c);
         if (j <= i || j >= nv) continue;
         const float2 hl = acc.hl(r, c);
@@ -386,7 +395,7 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Smem<C>& sm = *reinterpret_cast<Smem<C>*>(smem_raw);
   const Lanes<C> L;
-  Acc<PACKED> acc;
+  Acc<PACKED, C::NJ> acc;
   const int nv = V.nv;
   const int Tk = (nv + C::BN - 1) / C::BN;
   for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
@@ -411,7 +420,7 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
       const double Sij = S[i] + Sj;
       const double n2ij = (double)n2sq[(int64_t)i * nv + j];
 #pragma unroll
-      for (int c = 0; c < 8; ++c) {
+      for (int c = 0; c < C::NJ; ++c) {
         const int k = col0 + L.col(c);
         if (k <= j || k >= nv) continue;
         out[base + (int64_t)i * w + (k - j - 1)] =
@@ -435,7 +444,7 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Smem<C>& sm = *reinterpret_cast<Smem<C>*>(smem_raw);
   const Lanes<C> L;
-  Acc<PACKED> acc;
+  Acc<PACKED, C::NJ> acc;
   const int nv = V.nv;
   const int* __restrict__ perm = ta.perm;
   constexpr int B = C::BM;
@@ -454,7 +463,7 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
       if (i >= j) continue;
       const int oi = perm ? perm[i] : i;
 #pragma unroll
-      for (int c = 0; c < 8; ++c) {
+      for (int c = 0; c < C::NJ; ++c) {
         const int k = col0 + L.col(c);
         if (k <= j || k >= nv) continue;
         // the three vectors in increasing ORIGINAL index (a, b, c): the sums of
@@ -539,7 +548,7 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
   __shared__ int s_item, s_flag;
   __shared__ double s_part[8][33];
   const Lanes<C> L;
-  Acc<PACKED> acc;
+  Acc<PACKED, C::NJ> acc;
   int* err = counters + 1;
   int* sums_done = counters + 2;
   int* n2_done = counters + 2 + nprob;
@@ -586,7 +595,7 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
         if (i >= nv) continue;
         const double Si = __ldcg(p.S + i);
 #pragma unroll
-        for (int c = 0; c < 8; ++c) {
+        for (int c = 0; c < C::NJ; ++c) {
           const int j = col0 + L.col(c);
           if (j <= i || j >= nv) continue;
           const float2 hl = acc.hl(r, c);
@@ -628,7 +637,7 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
       const double Sij = __ldcg(p.S + i) + Sj;
       const double n2ij = (double)__ldcg(p.n2 + (int64_t)i * nv + j);
 #pragma unroll
-      for (int c = 0; c < 8; ++c) {
+      for (int c = 0; c < C::NJ; ++c) {
         const int k = col0 + L.col(c);
         if (k <= j || k >= nv) continue;
         out[base + (int64_t)i * wdt + (k - j - 1)] =

@@ -25,6 +25,9 @@ namespace {
 __host__ __device__ constexpr int sel_shift(int pass) { return pass == 0 ? 21 : (pass == 1 ? 10 : 0); }
 __host__ __device__ constexpr int sel_bits(int pass) { return pass == 2 ? 10 : 11; }
 
+// Histogram of one radix digit over the nonzero entries that match the
+// prefix selected so far.  Rows (fields) are distributed over blocks, each
+// thread walks its columns (vectors) of a row: no index division per entry.
 __global__ void __launch_bounds__(256) radix_hist_kernel(VF32 V, int pass,
                                                          const SelectState* __restrict__ st,
                                                          unsigned long long* __restrict__ hist) {
@@ -36,15 +39,15 @@ __global__ void __launch_bounds__(256) radix_hist_kernel(VF32 V, int pass,
   const unsigned prefix = pass == 0 ? 0u : st->prefix;
   const bool done = pass > 0 && st->done;
   if (!done) {
-    const int64_t total = (int64_t)V.nf * V.nv;
-    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
-         t += (int64_t)gridDim.x * blockDim.x) {
-      const int64_t q = t / V.nv, i = t - q * V.nv;
-      const float x = V.p[q * V.ld + i];
-      if (x == 0.0f) continue;
-      const unsigned b = __float_as_uint(x);
-      if (pass > 0 && (hi_shift >= 32 ? 0u : (b >> hi_shift)) != prefix) continue;
-      atomicAdd(&sh[(b >> shift) & mask], 1u);
+    for (int q = blockIdx.x; q < V.nf; q += gridDim.x) {
+      const float* row = V.p + (int64_t)q * V.ld;
+      for (int i = threadIdx.x; i < V.nv; i += blockDim.x) {
+        const float x = row[i];
+        if (x == 0.0f) continue;
+        const unsigned b = __float_as_uint(x);
+        if (pass > 0 && (hi_shift >= 32 ? 0u : (b >> hi_shift)) != prefix) continue;
+        atomicAdd(&sh[(b >> shift) & mask], 1u);
+      }
     }
   }
   __syncthreads();
@@ -176,18 +179,25 @@ __global__ void __launch_bounds__(256) thermo_encode_kernel(VF32 V, int L,
   const int row_bytes = ENC_F * Lm;  // multiple of 16
   const int pieces = row_bytes / 16;
   for (int e = threadIdx.x; e < ENC_V * pieces; e += blockDim.x) {
-    const int r = e / pieces, pc = e % pieces;
+    const int pc = e % pieces, r = e / pieces;  // consecutive threads: consecutive pieces of a row
     const int i = i0 + r;
     if (i >= nv_pad) continue;
+    // first byte of the piece: field qf, threshold tt (1-based); then step
+    int qf = (pc * 16) / Lm;
+    int tt = pc * 16 - qf * Lm + 1;
+    int lev = lv[qf][r];
     uint32_t w[4];
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       uint32_t word = 0;
 #pragma unroll
       for (int b = 0; b < 4; ++b) {
-        const int k = pc * 16 + u * 4 + b;
-        const int qf = k / Lm, tt = k - qf * Lm + 1;
-        word |= (lv[qf][r] >= tt ? 0x38u : 0u) << (8 * b);
+        word |= (lev >= tt ? 0x38u : 0u) << (8 * b);
+        if (++tt > Lm) {
+          tt = 1;
+          ++qf;
+          lev = qf < ENC_F ? lv[qf][r] : 0;
+        }
       }
       w[u] = word;
     }
@@ -200,9 +210,7 @@ __global__ void __launch_bounds__(256) thermo_encode_kernel(VF32 V, int L,
 
 cudaError_t launch_percentile_nonzero(ps_ctx* h, const VF32& V, double p, SelectState* st,
                                       unsigned long long* hist, cudaStream_t s) {
-  const int64_t total = (int64_t)V.nf * V.nv;
-  const unsigned grid = (unsigned)std::max<int64_t>(
-      1, std::min<int64_t>(ceil_div(total, 256), (int64_t)h->num_sms * 8));
+  const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(V.nf, (int64_t)h->num_sms * 8));
   for (int pass = 0; pass < 3; ++pass) {
     cudaError_t e = cudaMemsetAsync(hist, 0, 2048 * sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;

@@ -89,7 +89,7 @@ def test_autotuner_writes_cache_and_reuses_it(ps, handle, tmp_path):
     buf = ctypes.create_string_buffer(128)
     ps.check(ps.ps_autotune_batched(handle.h, probs, 5, path.encode(), buf, 128, st), handle.h)
     lines = [json.loads(x) for x in open(path)]
-    assert len(lines) == 1 and len(lines[0]["ms"]) == 6
+    assert len(lines) == 1 and len(lines[0]["ms"]) == 9
     assert str(lines[0]["variant"]) in lines[0]["ms"]
     buf2 = ctypes.create_string_buffer(128)
     ps.check(ps.ps_autotune_batched(handle.h, probs, 5, path.encode(), buf2, 128, st), handle.h)
