@@ -34,7 +34,9 @@
  *   tensors, managed memory) or HOST memory (pinned or pageable).  The kind
  *   is detected with cudaPointerGetAttributes.  Host buffers are staged
  *   through library-owned device memory inside the call, and a call that
- *   touches any host buffer synchronises `stream` before returning.  A call
+ *   touches any host buffer synchronises `stream` before returning (the FP32
+ *   2-way path with a host output computes in row bands and copies each
+ *   finished band while the next one computes).  A call
  *   on device buffers only is asynchronous on `stream`.  The caller owns all
  *   buffers it passes; the library owns only its workspace (grown on demand,
  *   freed by ps_destroy).

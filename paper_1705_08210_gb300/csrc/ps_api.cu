@@ -259,8 +259,7 @@ ps_status thermo_2way(ps_ctx* h, const VF32& v, int levels, void* out, int out_f
   PS_CUDA_TRY(h, cudaMemsetAsync(err, 0, sizeof(int), st));
   {
     ScopedTimer tm(h, "thermo_encode", st);
-    PS_CUDA_TRY(h, launch_level_sums(v, levels, sel, SQ, st));
-    PS_CUDA_TRY(h, launch_thermo_encode(v, levels, sel, T, Kpad, nv_pad, st));
+    PS_CUDA_TRY(h, launch_thermo_encode(v, levels, sel, T, Kpad, nv_pad, SQ, st));
   }
   {
     ScopedTimer tm(h, "thermo_gemm", st);
@@ -430,6 +429,7 @@ ps_status ps_destroy(ps_handle h) {
     Guard g(h->device);
     cudaDeviceSynchronize();
     timing_clear(h);
+    if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
     batch_state_free(h);
     mlp_free(h);
     for (int s = 0; s < WS_NUM_SLOTS; ++s)
@@ -488,6 +488,40 @@ ps_status ps_metrics_2way(ps_handle h, const ps_matrix* V, int32_t path, int32_t
     if (s != PS_OK) return s;
     s = thermo_2way(h, P.f32, levels, o.dev, out_dtype == PS_F64, st);
     if (s != PS_OK) return s;
+  } else if (path == PS_PATH_FP32 && o.host && V->nv >= 8 * 128) {
+    // host output: compute in equal-work row bands and copy each finished
+    // band (a contiguous packed range) to the host on the handle's copy
+    // stream while the next band computes
+    s = prepare(h, *V, st, true, &P);
+    if (s != PS_OK) return s;
+    if (!h->copy_stream) PS_CUDA_TRY(h, cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking));
+    constexpr int NB = 8;
+    cudaEvent_t ev[NB];
+    for (int b = 0; b < NB; ++b) PS_CUDA_TRY(h, cudaEventCreateWithFlags(&ev[b], cudaEventDisableTiming));
+    const int keep_tile = h->mgemm_tile;
+    h->mgemm_tile = 128;  // bands are whole 128-row tiles
+    const size_t esz = dtype_size(out_dtype);
+    cudaError_t e = cudaSuccess;
+    for (int b = 0; b < NB && e == cudaSuccess; ++b) {
+      int64_t rb = 0, re = 0;
+      partition_2way(V->nv, NB, b, &rb, &re);
+      {
+        ScopedTimer tm(h, "mgemm2", st);
+        e = launch_mgemm2(h, P.f32, P.S, o.dev, out_dtype == PS_F64 ? OUT2_C2_F64 : OUT2_C2_F32, st,
+                          (int)(rb / 128), (int)ceil_div(re, 128));
+      }
+      if (e == cudaSuccess) e = cudaEventRecord(ev[b], st);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(h->copy_stream, ev[b], 0);
+      const int64_t ob = rb * (2 * V->nv - rb - 1) / 2, oe = re * (2 * V->nv - re - 1) / 2;
+      if (e == cudaSuccess && oe > ob)
+        e = cudaMemcpyAsync(static_cast<char*>(o.user) + ob * esz, static_cast<char*>(o.dev) + ob * esz,
+                            (size_t)(oe - ob) * esz, cudaMemcpyDeviceToHost, h->copy_stream);
+    }
+    h->mgemm_tile = keep_tile;
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->copy_stream);
+    for (int b = 0; b < NB; ++b) cudaEventDestroy(ev[b]);
+    PS_CUDA_TRY(h, e);
+    o.bytes = 0;  // already copied
   } else if (path == PS_PATH_FP32) {
     s = prepare(h, *V, st, true, &P);
     if (s != PS_OK) return s;

@@ -164,7 +164,7 @@ constexpr int ENC_V = 32, ENC_F = 128;
 __global__ void __launch_bounds__(256) thermo_encode_kernel(VF32 V, int L,
                                                             const SelectState* __restrict__ st,
                                                             uint8_t* __restrict__ T, int64_t Kpad,
-                                                            int nv_pad) {
+                                                            int nv_pad, int* __restrict__ SQ) {
   __shared__ uint8_t lv[ENC_F][ENC_V];
   const float r32 = recip_scale(st, L);
   const int i0 = blockIdx.x * ENC_V;
@@ -175,6 +175,12 @@ __global__ void __launch_bounds__(256) thermo_encode_kernel(VF32 V, int L,
     lv[r][c] = (q < V.nf && i < V.nv) ? (uint8_t)level_of(V.p[(int64_t)q * V.ld + i], r32, L) : 0;
   }
   __syncthreads();
+  // the quantized denominators: integer level sums (exact in any order)
+  if (SQ && threadIdx.x < ENC_V && i0 + (int)threadIdx.x < V.nv) {
+    int sacc = 0;
+    for (int r = 0; r < ENC_F; ++r) sacc += lv[r][threadIdx.x];
+    atomicAdd(&SQ[i0 + threadIdx.x], sacc);
+  }
   const int Lm = L - 1;
   const int row_bytes = ENC_F * Lm;  // multiple of 16
   const int pieces = row_bytes / 16;
@@ -239,10 +245,14 @@ cudaError_t launch_level_sums(const VF32& V, int levels, const SelectState* st, 
 int64_t thermo_kpad(int64_t nf, int levels) { return ceil_div(std::max<int64_t>(nf, 1), ENC_F) * ENC_F * (levels - 1); }
 
 cudaError_t launch_thermo_encode(const VF32& V, int levels, const SelectState* st, uint8_t* T,
-                                 int64_t Kpad, int nv_pad, cudaStream_t s) {
+                                 int64_t Kpad, int nv_pad, int* SQ, cudaStream_t s) {
   dim3 grid((unsigned)ceil_div(nv_pad, ENC_V), (unsigned)(Kpad / ((int64_t)ENC_F * (levels - 1))));
   if (grid.y > 65535) return cudaErrorInvalidConfiguration;
-  thermo_encode_kernel<<<grid, 256, 0, s>>>(V, levels, st, T, Kpad, nv_pad);
+  if (SQ) {
+    const cudaError_t e = cudaMemsetAsync(SQ, 0, (size_t)nv_pad * sizeof(int), s);
+    if (e != cudaSuccess) return e;
+  }
+  thermo_encode_kernel<<<grid, 256, 0, s>>>(V, levels, st, T, Kpad, nv_pad, SQ);
   return cudaGetLastError();
 }
 

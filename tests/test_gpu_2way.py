@@ -141,3 +141,15 @@ def test_parts_assemble_full_result(ps, handle):
                                          torch.cuda.current_stream().cuda_stream), handle.h)
     torch.cuda.synchronize()
     np.testing.assert_array_equal(out.cpu().numpy(), full)
+
+
+def test_host_output_banded_path_matches_device(ps, handle):
+    # nv >= 1024: the host-output call computes in row bands and overlaps
+    # the device-to-host copies; results must equal the device-output call
+    nv, nf = 1500, 120
+    V = synth.zero_inflated(nv, nf, synth.seed_for(1, 41))
+    dev = metrics_2way(ps, handle, V)
+    host = metrics_2way(ps, handle, V, on_host=True)
+    np.testing.assert_array_equal(host, dev)
+    host64 = metrics_2way(ps, handle, V, on_host=True, out_dtype=np.float64)
+    np.testing.assert_array_equal(host64, metrics_2way(ps, handle, V, out_dtype=np.float64))
