@@ -92,7 +92,12 @@ typedef enum {
   PS_PATH_FP64 = 1,
   /* Quantize to `levels` levels, thermometer-encode, and run the numerator
    * product on the tensor cores (exact on the quantized data). */
-  PS_PATH_THERMO = 2
+  PS_PATH_THERMO = 2,
+  /* Values scaled by a power of two and rounded to FP16, pairs of fields
+   * packed as half2: one packed min (min.f16x2) for two comparisons, both
+   * halves added to FP32 accumulators (relative error <= ~5e-4 from the FP16
+   * rounding of the inputs; exact on integers below 2048). */
+  PS_PATH_HALF2 = 3
 } ps_path;
 
 typedef enum { PS_LAYOUT_FIELD_MAJOR = 0, PS_LAYOUT_VECTOR_MAJOR = 1 } ps_layout;
@@ -346,7 +351,7 @@ ps_status ps_quantize(ps_handle h, const ps_matrix* V, int32_t levels,
  * (it waits for recorded events first).
  * ps_timing_read synchronises on the recorded events of `kernel` and returns
  * their number and summed duration.  Kernel names: "vector_sums", "pack",
- * "mgemm2", "mgemm2_f64", "mgemm2_n2", "mgemm3", "quantize", "thermo_encode",
+ * "mgemm2", "mgemm2_f64", "mgemm2_half", "mgemm2_n2", "mgemm3", "quantize", "thermo_encode",
  * "thermo_gemm", "threshold3", "sort", "batched", "proposal_encode",
  * "proposal_score", "proposal_bound".
  * Errors: PS_ERR_INVALID_ARG for null arguments. */

@@ -471,7 +471,7 @@ ps_status ps_metrics_2way(ps_handle h, const ps_matrix* V, int32_t path, int32_t
   if (!out) return fail(h, PS_ERR_INVALID_ARG, "null out");
   if (out_dtype != PS_F32 && out_dtype != PS_F64)
     return fail(h, PS_ERR_INVALID_ARG, "out_dtype %d is not PS_F32/PS_F64", out_dtype);
-  if (path != PS_PATH_FP32 && path != PS_PATH_FP64 && path != PS_PATH_THERMO)
+  if (path != PS_PATH_FP32 && path != PS_PATH_FP64 && path != PS_PATH_THERMO && path != PS_PATH_HALF2)
     return fail(h, PS_ERR_INVALID_ARG, "path %d is not a ps_path", path);
   if (path == PS_PATH_THERMO && (levels < 2 || levels > 16))
     return fail(h, PS_ERR_INVALID_ARG, "levels=%d outside [2,16]", levels);
@@ -488,6 +488,22 @@ ps_status ps_metrics_2way(ps_handle h, const ps_matrix* V, int32_t path, int32_t
     if (s != PS_OK) return s;
     s = thermo_2way(h, P.f32, levels, o.dev, out_dtype == PS_F64, st);
     if (s != PS_OK) return s;
+  } else if (path == PS_PATH_HALF2) {
+    s = prepare(h, *V, st, true, &P);
+    if (s != PS_OK) return s;
+    const int64_t ldh = round_up(V->nv, 4);
+    const int64_t np = (V->nf + 1) / 2;
+    uint32_t* vh = static_cast<uint32_t*>(ws_get(h, WS_QUANT, (size_t)std::max<int64_t>(np * ldh, 1) * 4));
+    unsigned* aux = static_cast<unsigned*>(ws_get(h, WS_AUX3, 256));
+    if (!vh || !aux) return PS_ERR_OOM;
+    float* inv_scale = reinterpret_cast<float*>(aux + 16);
+    {
+      ScopedTimer tm(h, "pack", st);
+      PS_CUDA_TRY(h, launch_pack_half2(P.f32, vh, ldh, aux, inv_scale, st));
+    }
+    const VF32 hv{reinterpret_cast<const float*>(vh), ldh, (int)V->nv, (int)np};
+    ScopedTimer tm(h, "mgemm2_half", st);
+    PS_CUDA_TRY(h, launch_mgemm2_half(h->num_sms, hv, P.S, o.dev, out_dtype == PS_F64, inv_scale, st));
   } else if (path == PS_PATH_FP32 && o.host && V->nv >= 8 * 128) {
     // host output: compute in equal-work row bands and copy each finished
     // band (a contiguous packed range) to the host on the handle's copy

@@ -217,6 +217,24 @@ struct Acc<false, NJ> {
 #pragma unroll
       for (int c = 0; c < NJ; ++c) lo[r][c] = __fadd_rn(lo[r][c], fminf(a[r], b[c]));
   }
+  // Two consecutive fields at once: a[r], b[c] hold (field k, field k+1) as
+  // half2; one packed min, then both halves added to the FP32 accumulator in
+  // field order (mixed-precision FP16 + FP32 -> FP32 adds).
+  __device__ __forceinline__ void step_h(const uint32_t (&a)[8], const uint32_t (&b)[NJ]) {
+#pragma unroll
+    for (int r = 0; r < 8; ++r)
+#pragma unroll
+      for (int c = 0; c < NJ; ++c) {
+        uint32_t m;
+        asm("min.f16x2 %0, %1, %2;" : "=r"(m) : "r"(a[r]), "r"(b[c]));
+        float x = lo[r][c];
+        asm("{\n\t.reg .b16 l, h;\n\tmov.b32 {l, h}, %1;\n\tadd.rn.f32.f16 %0, l, %0;\n\t"
+            "add.rn.f32.f16 %0, h, %0;\n\t}"
+            : "+f"(x)
+            : "r"(m));
+        lo[r][c] = x;
+      }
+  }
   __device__ __forceinline__ void fold() {
 #pragma unroll
     for (int r = 0; r < 8; ++r)
@@ -235,11 +253,24 @@ struct Acc<false, NJ> {
 
 // BK k-steps of the micro-kernel on ring buffer `buf`, KU steps per loop
 // iteration (smaller KU keeps the hot loop in the instruction cache).
-template <class C, bool PACKED, int KU>
+template <class C, bool PACKED, int KU, bool HALF = false>
 __device__ __forceinline__ void compute_slice(const Smem<C>& sm, int buf, int am, int bn,
                                               Acc<PACKED, C::NJ>& acc) {
   const float* As = &sm.A[buf][0][am];
   const float* Bs = &sm.B[buf][0][bn];
+  if constexpr (HALF) {  // 4-byte elements hold half2 field pairs
+#pragma unroll KU
+    for (int kk = 0; kk < BK; ++kk) {
+      const uint4 a0 = *reinterpret_cast<const uint4*>(As + kk * C::BM);
+      const uint4 a1 = *reinterpret_cast<const uint4*>(As + kk * C::BM + 32);
+      const uint4 b0 = *reinterpret_cast<const uint4*>(Bs + kk * C::BN);
+      const uint4 b1 = *reinterpret_cast<const uint4*>(Bs + kk * C::BN + 16);
+      const uint32_t a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+      const uint32_t b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+      acc.step_h(a, b);
+    }
+    return;
+  } else {
 #pragma unroll KU
   for (int kk = 0; kk < BK; ++kk) {
     const float4 a0 = *reinterpret_cast<const float4*>(As + kk * C::BM);
@@ -255,10 +286,11 @@ __device__ __forceinline__ void compute_slice(const Smem<C>& sm, int buf, int am
       acc.step(a, b);
     }
   }
+  }
 }
 
 // Full k loop over n_f for one (row0, col0) tile, with optional pivot j.
-template <class C, bool PIVOT, bool PACKED, int KU>
+template <class C, bool PIVOT, bool PACKED, int KU, bool HALF = false>
 __device__ __forceinline__ void tile_minsum(Smem<C>& sm, const VF32& V, int row0, int col0,
                                             int jpiv, int am, int bn, Acc<PACKED, C::NJ>& acc) {
   acc.zero();
@@ -276,7 +308,7 @@ __device__ __forceinline__ void tile_minsum(Smem<C>& sm, const VF32& V, int row0
     const int sn = s + STAGES - 1;
     if (sn < nst) issue_slice<C, PIVOT>(sm, sn % STAGES, V, row0, col0, sn * BK, jpiv);
     cp_async_commit();
-    compute_slice<C, PACKED, KU>(sm, buf, am, bn, acc);
+    compute_slice<C, PACKED, KU, HALF>(sm, buf, am, bn, acc);
     if ((s + 1) % FOLD == 0) acc.fold();
   }
   acc.fold();
@@ -378,6 +410,50 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
           float* tab = static_cast<float*>(out);
           tab[(int64_t)i * nv + j] = n2;
           tab[(int64_t)j * nv + i] = n2;
+        }
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// 2-way on half2 field pairs (PS_PATH_HALF2): V holds (field 2p, field 2p+1)
+// of every vector, scaled by a power of two `scale` before rounding to FP16;
+// n2 = (hi + lo) / scale is exact rescaling.  Denominators S come from the
+// caller's values.
+template <class C, int KU>
+__global__ void __launch_bounds__(C::NT, C::MINB)
+    mgemm2_half_kernel(VF32 V, const double* __restrict__ S, void* __restrict__ out, int out_f64,
+                       const float* __restrict__ inv_scale_p, int T, int64_t ntiles) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Smem<C>& sm = *reinterpret_cast<Smem<C>*>(smem_raw);
+  const Lanes<C> L;
+  Acc<false, C::NJ> acc;
+  const int64_t nv = V.nv;
+  const float inv_scale = *inv_scale_p;
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    int I, J;
+    tri_tile(t, T, I, J);
+    const int row0 = I * C::BM, col0 = J * C::BN;
+    tile_minsum<C, false, false, KU, true>(sm, V, row0, col0, 0, L.am, L.bn, acc);
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      const int i = row0 + L.row(r);
+      if (i >= nv) continue;
+      const double Si = S[i];
+#pragma unroll
+      for (int c = 0; c < C::NJ; ++c) {
+        const int j = col0 + L.col(c);
+        if (j <= i || j >= nv) continue;
+        const float2 hl = acc.hl(r, c);
+        if (out_f64) {
+          const double n2 = ((double)hl.x + (double)hl.y) * (double)inv_scale;
+          const double d = Si + S[j];
+          static_cast<double*>(out)[pair_index(nv, i, j)] = (d == 0.0) ? 0.0 : (2.0 * n2) / d;
+        } else {
+          const float n2 = __fmul_rn(__fadd_rn(hl.x, hl.y), inv_scale);
+          const float d = (float)(Si + S[j]);
+          static_cast<float*>(out)[pair_index(nv, i, j)] = (d == 0.0f) ? 0.0f : __fdiv_rn(2.0f * n2, d);
         }
       }
     }

@@ -18,6 +18,27 @@ const MgemmVariant* mgemm_variant_t128(int packed, int ku) {
   return &v[(packed ? 0 : 3) + k];
 }
 
+cudaError_t launch_mgemm2_half(int num_sms, const VF32& Vh, const double* S, void* out, int out_f64,
+                               const float* inv_scale, cudaStream_t st) {
+  using C = mg::T128;
+  static bool attrs_done[64] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const size_t smem = sizeof(mg::Smem<C>);
+  if (!attrs_done[dev & 63]) {
+    cudaError_t e = cudaFuncSetAttribute(mg::mgemm2_half_kernel<C, 8>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attrs_done[dev & 63] = true;
+  }
+  const int T = (int)ceil_div(Vh.nv, C::BM);
+  const int64_t ntiles = (int64_t)T * (T + 1) / 2;
+  if (ntiles == 0) return cudaSuccess;
+  const unsigned grid = (unsigned)std::min<int64_t>(ntiles, (int64_t)num_sms * C::MINB);
+  mg::mgemm2_half_kernel<C, 8><<<grid, C::NT, smem, st>>>(Vh, S, out, out_f64, inv_scale, T, ntiles);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_thresh_t128(int num_sms, const VF32& V, const double* S, const float* n2sq,
                                const int* blocks, int64_t nblocks, const ThreshArgs& ta,
                                cudaStream_t st) {

@@ -7,6 +7,8 @@
 
 #include <algorithm>
 
+#include <cuda_fp16.h>
+
 namespace ps {
 namespace {
 
@@ -86,7 +88,57 @@ __global__ void __launch_bounds__(256) pack_vm(const T* __restrict__ X, int64_t 
   }
 }
 
+// Largest value of the matrix (non-negative data: unsigned order of the bit
+// patterns is the numeric order).
+__global__ void max_bits_kernel(VF32 V, unsigned* __restrict__ mx) {
+  unsigned m = 0;
+  for (int q = blockIdx.x; q < V.nf; q += gridDim.x) {
+    const float* row = V.p + (int64_t)q * V.ld;
+    for (int i = threadIdx.x; i < V.nv; i += blockDim.x) m = max(m, __float_as_uint(fmaxf(row[i], 0.f)));
+  }
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(mx, m);
+}
+
+// out[p*ldo + i] = half2(scale * V[2p][i], scale * V[2p+1][i]) (0 beyond nv / nf);
+// scale = 2^e chosen on the device so the largest value lands in [2^13, 2^14).
+__global__ void pack_half2_kernel(VF32 V, const unsigned* __restrict__ mx, uint32_t* __restrict__ out,
+                                  int64_t ldo, int np, float* __restrict__ inv_scale_out) {
+  const float vmax = __uint_as_float(*mx);
+  int e = 0;
+  if (vmax > 0.f) {
+    frexpf(vmax, &e);                     // vmax in [2^(e-1), 2^e)
+    e = max(-24, min(24, 14 - e));        // scale 2^e
+  }
+  const float scale = ldexpf(1.0f, e);
+  if (blockIdx.x == 0 && threadIdx.x == 0) *inv_scale_out = ldexpf(1.0f, -e);
+  const int64_t total = (int64_t)np * ldo;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t p = t / ldo, i = t - p * ldo;
+    float x0 = 0.f, x1 = 0.f;
+    if (i < V.nv) {
+      x0 = V.p[(2 * p) * V.ld + i] * scale;
+      if (2 * p + 1 < V.nf) x1 = V.p[(2 * p + 1) * V.ld + i] * scale;
+    }
+    const __half2 hv = __floats2half2_rn(x0, x1);
+    out[t] = *reinterpret_cast<const uint32_t*>(&hv);
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_pack_half2(const VF32& V, uint32_t* out, int64_t ldo, unsigned* mx, float* inv_scale,
+                              cudaStream_t st) {
+  const int np = (V.nf + 1) / 2;
+  cudaError_t e = cudaMemsetAsync(mx, 0, sizeof(unsigned), st);
+  if (e != cudaSuccess) return e;
+  max_bits_kernel<<<(unsigned)std::max(1, std::min(V.nf, 152 * 8)), 256, 0, st>>>(V, mx);
+  const int64_t total = (int64_t)np * ldo;
+  pack_half2_kernel<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(total, 256), 152 * 32)), 256,
+                      0, st>>>(V, mx, out, ldo, np, inv_scale);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_vector_sums(const ps_matrix& V, double* S, cudaStream_t st) {
   if (V.nv <= 0) return cudaSuccess;
