@@ -115,6 +115,45 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+# DRAM traffic per launch from a committed ncu summary, valid while the
+# kernel's sources hash to the value recorded with the capture.
+TRAFFIC = {
+    "mgemm2": ("profiles/mgemm2_2way_32768x8192_dram.md",
+               ["paper_1705_08210_gb300/csrc/ps_mgemm_impl.cuh", "paper_1705_08210_gb300/csrc/ps_mgemm_t128.cu",
+                "paper_1705_08210_gb300/csrc/ps_mgemm.cu"]),
+    "thermo_gemm": ("profiles/thermo_gemm_2way_32768x8192_dram.md", ["paper_1705_08210_gb300/csrc/ps_thermo.cu"]),
+}
+
+
+def sources_sha256(paths):
+    import hashlib
+    hsh = hashlib.sha256()
+    for p in paths:
+        with open(os.path.join(ROOT, p), "rb") as f:
+            hsh.update(f.read())
+    return hsh.hexdigest()
+
+
+def profiled_traffic(kernel, workload):
+    """Bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of
+    `kernel` on `workload`, or None when no capture matches the current
+    sources."""
+    if kernel not in TRAFFIC:
+        return None
+    summary, srcs = TRAFFIC[kernel]
+    path = os.path.join(ROOT, summary)
+    if not os.path.exists(path):
+        return None
+    rec = {}
+    for line in open(path):
+        if ":" in line and line.strip().startswith(("traffic_bytes_per_launch", "source_sha256", "workload")):
+            k, v = line.strip().split(":", 1)
+            rec[k.strip()] = v.strip()
+    if rec.get("workload") != workload or rec.get("source_sha256") != sources_sha256(srcs):
+        return None
+    return float(rec["traffic_bytes_per_launch"]) / 1e9
+
+
 def cpu_baseline(V_fm: np.ndarray, w, n_sample: int):
     """The plain FP64 oracle on the first n_sample vectors, all host cores."""
     import oracle
@@ -347,7 +386,9 @@ def main():
     probe0 = ctypes.c_double()
     ps.check(ps.ps_probe_minadd_peak(h.h, 0, ctypes.byref(probe0)), h.h)
     roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_cmp / 1e12, "unit": "Tcmp/s",
-                "frac": achieved / peak_cmp, "traffic": None,
+                "frac": achieved / peak_cmp, "traffic": profiled_traffic(main_kernel, args.workload),
+                "traffic_unit": "GB per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
+                "algorithmic_bytes": (V.nbytes + out_bytes) / 1e9,
                 "kernel": main_kernel, "kernel_ms": k_avg_ms,
                 "peak_basis": f"{n_sm} SMs x 64 FP32 min lanes/clock (ALU pipe) x {sm_max:.0f} MHz max clock",
                 "probe_minadd_f32x2": probe.value / 1e12, "probe_minadd_scalar": probe0.value / 1e12}
@@ -455,7 +496,8 @@ def main():
         thermo = {"value": cmp_per_step / (tms / 1e3), "unit": UNIT, "ms_per_step": tms, "levels": L,
                   "speedup_vs_fp32": ms_step / tms, "kernel_ms": kt,
                   "roofline": {"bound": "tensor", "achieved": tach / 1e12, "peak": fp8_peak / 1e12,
-                               "unit": "TFLOP/s", "frac": tach / fp8_peak, "traffic": None,
+                               "unit": "TFLOP/s", "frac": tach / fp8_peak,
+                               "traffic": profiled_traffic("thermo_gemm", args.workload),
                                "kernel": "thermo_gemm", "dtype": "fp8 e4m3 0/1, fp32 accumulate",
                                "peak_basis": "measured bf16 dense burst x 2 (nominal fp8/bf16 ratio), of measured"},
                   "quantization_error_vs_fp64_oracle": None}

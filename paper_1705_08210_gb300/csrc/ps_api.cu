@@ -257,13 +257,14 @@ ps_status thermo_2way(ps_ctx* h, const VF32& v, int levels, void* out, int out_f
   int* err = static_cast<int*>(ws_get(h, WS_AUX3, 256));
   if (!T || !SQ || !err) return PS_ERR_OOM;
   PS_CUDA_TRY(h, cudaMemsetAsync(err, 0, sizeof(int), st));
+  unsigned* sync = reinterpret_cast<unsigned*>(err + 32);
   {
     ScopedTimer tm(h, "thermo_encode", st);
     PS_CUDA_TRY(h, launch_thermo_encode(v, levels, sel, T, Kpad, nv_pad, SQ, st));
   }
   {
     ScopedTimer tm(h, "thermo_gemm", st);
-    PS_CUDA_TRY(h, launch_thermo_gemm(h, T, Kpad, v.nv, nv_pad, SQ, out, out_f64, err, st));
+    PS_CUDA_TRY(h, launch_thermo_gemm(h, T, Kpad, v.nv, nv_pad, SQ, out, out_f64, err, sync, st));
   }
   int herr = 0;
   PS_CUDA_TRY(h, cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -413,7 +414,9 @@ ps_status ps_create(ps_handle* out, int device) {
   }
   if (const char* v = getenv("PS_MGEMM_TILE")) h->mgemm_tile = atoi(v) == 64 ? 64 : 128;
   if (const char* v = getenv("PS_MGEMM_WARPS")) h->mgemm_warps = atoi(v) == 16 ? 16 : 8;
+  if (const char* v = getenv("PS_MGEMM_BAND")) h->mgemm_band = std::max(1, std::min(atoi(v), 64));
   if (const char* v = getenv("PS_THERMO_TILE_M")) h->thermo_tile_m = atoi(v) == 128 ? 128 : 256;
+  if (const char* v = getenv("PS_THERMO_SYNC_KB")) h->thermo_sync_kb = std::max(0, atoi(v));
   if (prop.major < 10) {
     delete h;
     return fail(nullptr, PS_ERR_UNSUPPORTED, "device %d is sm_%d%d; this library is built for sm_103a",
@@ -503,7 +506,7 @@ ps_status ps_metrics_2way(ps_handle h, const ps_matrix* V, int32_t path, int32_t
     }
     const VF32 hv{reinterpret_cast<const float*>(vh), ldh, (int)V->nv, (int)np};
     ScopedTimer tm(h, "mgemm2_half", st);
-    PS_CUDA_TRY(h, launch_mgemm2_half(h->num_sms, hv, P.S, o.dev, out_dtype == PS_F64, inv_scale, st));
+    PS_CUDA_TRY(h, launch_mgemm2_half(h->num_sms, h->mgemm_band, hv, P.S, o.dev, out_dtype == PS_F64, inv_scale, st));
   } else if (path == PS_PATH_FP32 && o.host && V->nv >= 8 * 128) {
     // host output: compute in equal-work row bands and copy each finished
     // band (a contiguous packed range) to the host on the handle's copy

@@ -158,7 +158,7 @@ cudaError_t launch_mgemm2(ps_ctx* h, const VF32& V, const double* S, void* out, 
   const int64_t tbase = I0 * T - I0 * (I0 - 1) / 2;
   const int64_t ntiles = (I1 * T - I1 * (I1 - 1) / 2) - tbase;
   const unsigned grid = (unsigned)std::min<int64_t>(ntiles, (int64_t)h->num_sms * v->minb);
-  v->mgemm2(grid, st, V, S, out, mode, T, tbase, ntiles);
+  v->mgemm2(grid, st, V, S, out, mode, T, (int)I0, (int)I1, std::max(1, h->mgemm_band), ntiles);
   return cudaGetLastError();
 }
 

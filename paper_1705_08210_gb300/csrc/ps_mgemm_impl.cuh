@@ -335,7 +335,7 @@ __host__ __device__ __forceinline__ int64_t pair_index(int64_t nv, int64_t i, in
 }
 
 // Upper-triangle tile index t -> (I, J), I <= J < T, row-major.
-__device__ __forceinline__ void tri_tile(int64_t t, int T, int& I, int& J) {
+__host__ __device__ __forceinline__ void tri_tile(int64_t t, int T, int& I, int& J) {
   double disc = (2.0 * T + 1) * (2.0 * T + 1) - 8.0 * (double)t;
   int i = (int)floor(((2.0 * T + 1) - sqrt(disc)) * 0.5);
   i = max(0, min(i, T - 1));
@@ -343,6 +343,35 @@ __device__ __forceinline__ void tri_tile(int64_t t, int T, int& I, int& J) {
   while (i + 1 < T && (int64_t)(i + 1) * T - (int64_t)(i + 1) * i / 2 <= t) ++i;
   I = i;
   J = i + (int)(t - ((int64_t)i * T - (int64_t)i * (i - 1) / 2));
+}
+
+// Tiles of tile rows [R0, R1) of the upper triangle (every J >= I < T), in
+// bands of G tile rows: the band's diagonal triangle first, then G-wide
+// column chunks from left to right, each chunk column by column.  Consecutive
+// indices (the tiles the persistent CTAs hold at one time) then share a band's
+// G row panels and a few column panels, which stay in L2; the row-major walk
+// re-reads each column panel from DRAM once per tile row instead of once per
+// band.  Index t counts from the first tile of row R0.
+__host__ __device__ __forceinline__ void band_tile(int64_t t, int T, int R0, int R1, int G, int& I, int& J) {
+  auto P = [T](int64_t r) { return r * T - r * (r - 1) / 2; };  // tiles in rows [0, r)
+  int gi, gj;
+  tri_tile(P(R0) + t, T, gi, gj);
+  const int b0 = R0 + ((gi - R0) / G) * G;
+  const int g = min(G, R1 - b0);
+  int64_t u = P(R0) + t - P(b0);
+  const int64_t diag = (int64_t)g * (g + 1) / 2;
+  if (u < diag) {
+    int li, lj;
+    tri_tile(u, g, li, lj);
+    I = b0 + li;
+    J = b0 + lj;
+  } else {
+    u -= diag;
+    const int64_t c = u / ((int64_t)g * G);
+    const int64_t v = u - c * g * G;
+    I = b0 + (int)(v % g);
+    J = b0 + g + (int)(c * G + v / g);
+  }
 }
 
 // Section 2.2 eq. (1): n3 = n2(ij) + n2(ik) + n2(jk) - n3' in FP64, then
@@ -376,7 +405,7 @@ __host__ __device__ __forceinline__ int64_t pivot_tiles(int nv, int64_t j, int B
 template <class C, bool PACKED, int KU>
 __global__ void __launch_bounds__(C::NT, C::MINB)
     mgemm2_kernel(VF32 V, const double* __restrict__ S, void* __restrict__ out, int mode, int T,
-                  int64_t tbase, int64_t ntiles) {
+                  int R0, int R1, int G, int64_t ntiles) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Smem<C>& sm = *reinterpret_cast<Smem<C>*>(smem_raw);
   const Lanes<C> L;
@@ -384,7 +413,7 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
   const int64_t nv = V.nv;
   for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
     int I, J;
-    tri_tile(tbase + t, T, I, J);
+    band_tile(t, T, R0, R1, G, I, J);
     const int row0 = I * C::BM, col0 = J * C::BN;
     tile_minsum<C, false, PACKED, KU>(sm, V, row0, col0, 0, L.am, L.bn, acc);
 #pragma unroll
@@ -424,7 +453,7 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
 template <class C, int KU>
 __global__ void __launch_bounds__(C::NT, C::MINB)
     mgemm2_half_kernel(VF32 V, const double* __restrict__ S, void* __restrict__ out, int out_f64,
-                       const float* __restrict__ inv_scale_p, int T, int64_t ntiles) {
+                       const float* __restrict__ inv_scale_p, int T, int G, int64_t ntiles) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Smem<C>& sm = *reinterpret_cast<Smem<C>*>(smem_raw);
   const Lanes<C> L;
@@ -433,7 +462,7 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
   const float inv_scale = *inv_scale_p;
   for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
     int I, J;
-    tri_tile(t, T, I, J);
+    band_tile(t, T, 0, T, G, I, J);
     const int row0 = I * C::BM, col0 = J * C::BN;
     tile_minsum<C, false, false, KU, true>(sm, V, row0, col0, 0, L.am, L.bn, acc);
 #pragma unroll
@@ -741,8 +770,8 @@ struct Launch {
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   }
   static void mgemm2(unsigned grid, cudaStream_t st, const VF32& V, const double* S, void* out,
-                     int mode, int T, int64_t tbase, int64_t ntiles) {
-    mgemm2_kernel<C, PACKED, KU><<<grid, C::NT, smem, st>>>(V, S, out, mode, T, tbase, ntiles);
+                     int mode, int T, int R0, int R1, int G, int64_t ntiles) {
+    mgemm2_kernel<C, PACKED, KU><<<grid, C::NT, smem, st>>>(V, S, out, mode, T, R0, R1, G, ntiles);
   }
   static void mgemm3(unsigned grid, cudaStream_t st, const VF32& V, const double* S,
                      const float* n2sq, const int64_t* pref, int npiv, int jb, float* out,

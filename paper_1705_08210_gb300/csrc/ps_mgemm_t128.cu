@@ -18,7 +18,7 @@ const MgemmVariant* mgemm_variant_t128(int packed, int ku) {
   return &v[(packed ? 0 : 3) + k];
 }
 
-cudaError_t launch_mgemm2_half(int num_sms, const VF32& Vh, const double* S, void* out, int out_f64,
+cudaError_t launch_mgemm2_half(int num_sms, int band, const VF32& Vh, const double* S, void* out, int out_f64,
                                const float* inv_scale, cudaStream_t st) {
   using C = mg::T128;
   static bool attrs_done[64] = {};
@@ -35,7 +35,7 @@ cudaError_t launch_mgemm2_half(int num_sms, const VF32& Vh, const double* S, voi
   const int64_t ntiles = (int64_t)T * (T + 1) / 2;
   if (ntiles == 0) return cudaSuccess;
   const unsigned grid = (unsigned)std::min<int64_t>(ntiles, (int64_t)num_sms * C::MINB);
-  mg::mgemm2_half_kernel<C, 8><<<grid, C::NT, smem, st>>>(Vh, S, out, out_f64, inv_scale, T, ntiles);
+  mg::mgemm2_half_kernel<C, 8><<<grid, C::NT, smem, st>>>(Vh, S, out, out_f64, inv_scale, T, std::max(1, band), ntiles);
   return cudaGetLastError();
 }
 

@@ -26,8 +26,16 @@
 // (Section 3.1's triangle), walked in 12 x 12 super-blocks so that the CTAs
 // running together share operand panels in L2; measured 2.4% faster from the
 // larger tile alone and 12% more from the super-block order.
-// Every mbarrier wait is bounded (PS_WAIT_NS); on timeout the CTA raises
-// `err`, lets in-flight copies drain, frees its TMEM and returns.
+// K-synchronised producers: the CTAs that share a panel only hit each
+// other's lines in L2 while they read the same K range at about the same
+// time.  Over the ~54 rounds of tiles at nv = 32768 the persistent CTAs drift
+// apart and the operand was re-read ~55x from DRAM (224 GB per launch for a
+// 4 GB operand).  So the producers meet at a grid-wide counter every
+// `sync_kb` k-blocks (cooperative launch: all CTAs are resident): a producer
+// does not issue chunk m of its round-r tile before every CTA has issued all
+// earlier chunks.
+// Every mbarrier and counter wait is bounded (PS_WAIT_NS); on timeout the CTA
+// raises `err`, lets in-flight copies drain, frees its TMEM and returns.
 #include "ps_internal.cuh"
 
 #include <cuda.h>
@@ -184,6 +192,28 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
   for (int t = 0; t < 32; ++t) v[t] = __uint_as_float(r[t]);
 }
 
+// Bounded wait until the grid-wide chunk counter reaches `need`.
+template <class SM>
+__device__ __forceinline__ bool counter_wait(SM& sm, const unsigned* c, unsigned need, int* err) {
+  auto load = [c]() {
+    unsigned v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(c) : "memory");
+    return v;
+  };
+  if (load() >= need) return true;
+  const unsigned long long t0 = globaltimer();
+  for (;;) {
+    __nanosleep(32);
+    if (load() >= need) return true;
+    if (*(volatile int*)&sm.abort) return false;
+    if (globaltimer() - t0 > PS_WAIT_NS) {
+      *(volatile int*)&sm.abort = 1;
+      atomicExch(err, 1);
+      return false;
+    }
+  }
+}
+
 // Tile walk: every (I, J) with I*TM < (J+1)*TN (some i < j in the tile),
 // listed on the host in G x G super-blocks of (row block, column block), so
 // that the CTAs running at the same time share their operand panels in L2.
@@ -209,7 +239,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     thermo_gemm_kernel(const __grid_constant__ CUtensorMap mapA,
                        const __grid_constant__ CUtensorMap mapB, int nkb, int nv,
                        const int2* __restrict__ tiles, int64_t ntiles, const int* __restrict__ SQ,
-                       void* __restrict__ out, int out_f64, int* __restrict__ err) {
+                       void* __restrict__ out, int out_f64, int* __restrict__ err,
+                       unsigned* __restrict__ sync, int sync_kb) {
   extern __shared__ unsigned char smem_raw[];
   using CF = TCfg<MH>;
   constexpr int TM = CF::TM, TSTAGES = CF::STAGES, A_BYTES = CF::A_BYTES, B_BYTES = CF::B_BYTES;
@@ -247,14 +278,24 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       int stage = 0;
       uint32_t phase = 0;
       bool ok = true;
-      for (int64_t t = blockIdx.x; ok && t < ntiles; t += gridDim.x) {
+      const unsigned cpt = sync_kb > 0 ? (unsigned)((nkb + sync_kb - 1) / sync_kb) : 0u;
+      int64_t r = 0;  // round: this CTA's r-th tile
+      for (int64_t t = blockIdx.x; ok && t < ntiles; t += gridDim.x, ++r) {
         const int I = tiles[t].x, J = tiles[t].y;
+        // CTAs holding a tile in this round
+        const unsigned P = (unsigned)min((int64_t)gridDim.x, ntiles - r * (int64_t)gridDim.x);
         for (int kb = 0; kb < nkb; ++kb) {
+          if (cpt && kb % sync_kb == 0 && (r | kb) != 0) {
+            // chunks issued before chunk kb/sync_kb of round r, over all CTAs
+            const unsigned need = (unsigned)r * cpt * gridDim.x + (unsigned)(kb / sync_kb) * P;
+            if (!counter_wait(sm, sync, need, err)) { ok = false; break; }
+          }
           if (!mbar_wait(sm, &sm.empty[stage], phase ^ 1, err)) { ok = false; break; }
           mbar_arrive_expect_tx(&sm.full[stage], A_BYTES + B_BYTES);
           tma_load_2d(sm.A[stage], &mapA, kb * TKB, I * TM, &sm.full[stage]);
           tma_load_2d(sm.B[stage], &mapB, kb * TKB, J * TN, &sm.full[stage]);
           if (++stage == TSTAGES) { stage = 0; phase ^= 1; }
+          if (cpt && ((kb + 1) % sync_kb == 0 || kb + 1 == nkb)) atomicAdd(sync, 1u);
         }
       }
     }
@@ -389,7 +430,7 @@ uint64_t g_thermo_attr_devices[3] = {};
 
 template <int MH>
 cudaError_t launch_mh(ps_ctx* h, const uint8_t* T, int64_t Kpad, int nv, int nv_pad, const int* SQ,
-                      void* out, int out_f64, int* err, cudaStream_t s) {
+                      void* out, int out_f64, int* err, unsigned* sync, cudaStream_t s) {
   constexpr int TM = TCfg<MH>::TM;
   if (Kpad % TKB != 0 || nv_pad % TN != 0 || nv_pad % TM != 0 || ((uintptr_t)T % 16) != 0)
     return cudaErrorInvalidValue;
@@ -414,18 +455,34 @@ cudaError_t launch_mh(ps_ctx* h, const uint8_t* T, int64_t Kpad, int nv, int nv_
   if (e != cudaSuccess) return e;
   const int nkb = (int)(Kpad / TKB);
   const int grid = (int)std::min<int64_t>(ntiles, h->num_sms);
-  thermo_gemm_kernel<MH><<<grid, NTHREADS, smem, s>>>(mA, mB, nkb, nv, dtl, ntiles, SQ, out, out_f64,
-                                                      err);
-  return cudaGetLastError();
+  // producers meet only when there is more than one round of tiles
+  const int sync_kb = (ntiles > grid && h->thermo_sync_kb > 0) ? h->thermo_sync_kb : 0;
+  if (sync_kb) {
+    e = cudaMemsetAsync(sync, 0, sizeof(unsigned), s);
+    if (e != cudaSuccess) return e;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3(NTHREADS);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = sync_kb ? 1 : 0;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, thermo_gemm_kernel<MH>, mA, mB, nkb, nv, (const int2*)dtl, ntiles, SQ,
+                            out, out_f64, err, sync, sync_kb);
 }
 
 }  // namespace
 
 cudaError_t launch_thermo_gemm(ps_ctx* h, const uint8_t* T, int64_t Kpad, int nv, int nv_pad,
-                               const int* SQ, void* out, int out_f64, int* err, cudaStream_t s) {
+                               const int* SQ, void* out, int out_f64, int* err, unsigned* sync,
+                               cudaStream_t s) {
   if (h->thermo_tile_m == 256)
-    return launch_mh<2>(h, T, Kpad, nv, nv_pad, SQ, out, out_f64, err, s);
-  return launch_mh<1>(h, T, Kpad, nv, nv_pad, SQ, out, out_f64, err, s);
+    return launch_mh<2>(h, T, Kpad, nv, nv_pad, SQ, out, out_f64, err, sync, s);
+  return launch_mh<1>(h, T, Kpad, nv, nv_pad, SQ, out, out_f64, err, sync, s);
 }
 
 }  // namespace ps

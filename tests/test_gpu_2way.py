@@ -153,3 +153,33 @@ def test_host_output_banded_path_matches_device(ps, handle):
     np.testing.assert_array_equal(host, dev)
     host64 = metrics_2way(ps, handle, V, on_host=True, out_dtype=np.float64)
     np.testing.assert_array_equal(host64, metrics_2way(ps, handle, V, out_dtype=np.float64))
+
+
+@pytest.mark.parametrize("band", [1, 2, 3])
+def test_tile_walk_bands(ps, handle, band, monkeypatch):
+    # the 2-way tile walk in bands of `band` tile rows (the default band is
+    # wider than these small cases, so narrow bands exercise the diagonal
+    # triangles, the column chunks and the ragged last band): every pair is
+    # computed once, whole-matrix, by parts and through the host-output bands
+    import torch
+    monkeypatch.setenv("PS_MGEMM_BAND", str(band))
+    h = ps.Handle(0)
+    try:
+        nv, nf = 1300, 77
+        V = synth.zero_inflated(nv, nf, synth.seed_for(1, 51 + band))
+        ref = oracle.c2_packed(oracle.to_vector_major(V))
+        got = metrics_2way(ps, h, V)
+        assert_rel(got, ref, RTOL32, f"band {band}")
+        np.testing.assert_array_equal(metrics_2way(ps, h, V, on_host=True), got)
+        X = torch.from_numpy(V).cuda()
+        m = ps.matrix(X)
+        out = torch.full((nv * (nv - 1) // 2,), float("nan"), device="cuda")
+        for p in range(3):
+            ps.check(ps.ps_metrics_2way_part(h.h, ctypes.byref(m), 3, p, out.data_ptr(), 0,
+                                             torch.cuda.current_stream().cuda_stream), h.h)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(out.cpu().numpy(), got)
+        half = metrics_2way(ps, h, V, path=ps.PS_PATH_HALF2)
+        assert_rel(half, ref, 1e-3, f"half2 band {band}")
+    finally:
+        h.close()

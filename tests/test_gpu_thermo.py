@@ -99,3 +99,20 @@ def test_thermo_config2_full_size_sampled(ps, handle):
     err = np.abs(got.astype(np.float64) - orig)
     print(f"quantization error vs FP64 oracle: max {err.max():.4f} mean {err.mean():.5f} "
           f"p99 {np.percentile(err, 99):.4f}")
+
+
+@pytest.mark.parametrize("sync_kb", [0, 1, 7])
+def test_thermo_multi_round_producer_sync(ps, handle, sync_kb, monkeypatch):
+    # 20 x 20 tile blocks of 256 -> 210 tiles over 152 persistent CTAs (two
+    # rounds); 30 k-blocks per tile; the producers meet every sync_kb
+    # k-blocks (0: never, 7: a ragged last chunk).  Results stay bit-exact.
+    monkeypatch.setenv("PS_THERMO_SYNC_KB", str(sync_kb))
+    h = ps.Handle(0)
+    try:
+        nv, nf, L = 5000, 200, 16
+        V = synth.zero_inflated(nv, nf, synth.seed_for(2, 90))
+        ref = _levels_c2(V, L)
+        got = metrics_2way(ps, h, V, path=ps.PS_PATH_THERMO, levels=L)
+        np.testing.assert_array_equal(got, ref.astype(np.float32))
+    finally:
+        h.close()
