@@ -41,6 +41,10 @@ WORKLOADS = {
     # small cases of the same kernels for profiler captures
     "2way_8192x8192_f32": dict(way=2, nv=8192, nf=8192, number=2),
     "3way_1024x4096_f32": dict(way=3, nv=1024, nf=4096, number=3),
+    # output-bound shapes (few fields)
+    "2way_32768x16_f32": dict(way=2, nv=32768, nf=16, number=2),
+    "2way_32768x64_f32": dict(way=2, nv=32768, nf=64, number=2),
+    "2way_32768x385_f32": dict(way=2, nv=32768, nf=385, number=2),
 }
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 
@@ -529,6 +533,42 @@ def main():
         secondary = {"3way_2048x4096_f32": {"value": c3 / (ms3 / 1e3), "unit": UNIT, "ms_per_step": ms3,
                                             "mgemm3_ms": k3, "frac_of_peak": c3 / (k3 / 1e3) / peak_cmp}}
         del o3, X3
+        torch.cuda.empty_cache()
+        # output-bound shapes: 32768 vectors with few fields, FP32 output
+        # (2.15 GB per call) against the measured HBM copy bandwidth
+        hbm = float(peaks.get("hbm_gbs", 6800.0))
+        nvs = 32768
+        os_ = torch.empty(nvs * (nvs - 1) // 2, dtype=torch.float32, device="cuda")
+        small = {}
+        for nfs in (16, 64, 385):
+            Vs = synth.zero_inflated(nvs, nfs, synth.seed_for(2, 1000 + nfs))
+            Xs = torch.from_numpy(Vs).cuda()
+            ms_ = ps.matrix(Xs)
+            for _ in range(3):
+                ps.check(ps.ps_metrics_2way(h.h, ctypes.byref(ms_), ps.PS_PATH_FP32, 0, os_.data_ptr(), 0,
+                                            sptr), h.h)
+            ps.check(ps.ps_timing_enable(h.h, 1), h.h)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for _ in range(10):
+                ps.check(ps.ps_metrics_2way(h.h, ctypes.byref(ms_), ps.PS_PATH_FP32, 0, os_.data_ptr(), 0,
+                                            sptr), h.h)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            mss = e0.elapsed_time(e1) / 10
+            ps.check(ps.ps_timing_read(h.h, b"mgemm2", ctypes.byref(n_launch), ctypes.byref(k_ms)), h.h)
+            ps.check(ps.ps_timing_enable(h.h, 0), h.h)
+            ks = k_ms.value / max(n_launch.value, 1)
+            byts = Vs.nbytes + os_.numel() * 4
+            cs = nfs * nvs * (nvs - 1) // 2
+            small[f"2way_32768x{nfs}_f32"] = {
+                "ms_per_step": mss, "mgemm2_ms": ks, "value": cs / (mss / 1e3), "unit": UNIT,
+                "algorithmic_gb": byts / 1e9, "achieved_gbs": byts / (ks / 1e3) / 1e9,
+                "frac_of_hbm": byts / (ks / 1e3) / 1e9 / hbm,
+                "frac_of_alu_peak": cs / (ks / 1e3) / peak_cmp}
+            del Xs
+        secondary["small_nf_output_bound"] = small
+        del os_
 
     # ---- thresholded 3-way search with proposals (8192 x 2048 latent profiles) ----
     thresh = None

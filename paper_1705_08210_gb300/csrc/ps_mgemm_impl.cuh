@@ -335,9 +335,13 @@ __host__ __device__ __forceinline__ int64_t pair_index(int64_t nv, int64_t i, in
 }
 
 // Upper-triangle tile index t -> (I, J), I <= J < T, row-major.
+// Row i is the largest with i*T - i(i-1)/2 <= t: an FP32 estimate from the
+// quadratic formula (no FP64, whose pipe is slow on this part), made exact by
+// the integer steps below.
 __host__ __device__ __forceinline__ void tri_tile(int64_t t, int T, int& I, int& J) {
-  double disc = (2.0 * T + 1) * (2.0 * T + 1) - 8.0 * (double)t;
-  int i = (int)floor(((2.0 * T + 1) - sqrt(disc)) * 0.5);
+  const float b = 2.0f * (float)T + 1.0f;
+  const float disc = fmaxf(b * b - 8.0f * (float)t, 0.0f);
+  int i = (int)((b - sqrtf(disc)) * 0.5f);
   i = max(0, min(i, T - 1));
   while (i > 0 && (int64_t)i * T - (int64_t)i * (i - 1) / 2 > t) --i;
   while (i + 1 < T && (int64_t)(i + 1) * T - (int64_t)(i + 1) * i / 2 <= t) ++i;
@@ -416,29 +420,66 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
     band_tile(t, T, R0, R1, G, I, J);
     const int row0 = I * C::BM, col0 = J * C::BN;
     tile_minsum<C, false, PACKED, KU>(sm, V, row0, col0, 0, L.am, L.bn, acc);
+    if (mode == OUT2_N2_SQUARE_F32) {
 #pragma unroll
-    for (int r = 0; r < 8; ++r) {
-      const int i = row0 + L.row(r);
-      if (i >= nv) continue;
-      const double Si = S ? S[i] : 0.0;
+      for (int r = 0; r < 8; ++r) {
+        const int i = row0 + L.row(r);
+        if (i >= nv) continue;
 #pragma unroll
-      for (int c = 0; c < C::NJ; ++c) {
-        const int j = col0 + L.col(c);
-        if (j <= i || j >= nv) continue;
-        const float2 hl = acc.hl(r, c);
-        if (mode == OUT2_C2_F32) {
-          const float n2 = __fadd_rn(hl.x, hl.y);
-          const float d = (float)(Si + S[j]);
-          static_cast<float*>(out)[pair_index(nv, i, j)] = (d == 0.0f) ? 0.0f : __fdiv_rn(2.0f * n2, d);
-        } else if (mode == OUT2_C2_F64) {
-          const double n2 = (double)hl.x + (double)hl.y;
-          const double d = Si + S[j];
-          static_cast<double*>(out)[pair_index(nv, i, j)] = (d == 0.0) ? 0.0 : (2.0 * n2) / d;
-        } else {
+        for (int c = 0; c < C::NJ; ++c) {
+          const int j = col0 + L.col(c);
+          if (j <= i || j >= nv) continue;
+          const float2 hl = acc.hl(r, c);
           const float n2 = __fadd_rn(hl.x, hl.y);
           float* tab = static_cast<float*>(out);
           tab[(int64_t)i * nv + j] = n2;
           tab[(int64_t)j * nv + i] = n2;
+        }
+      }
+      continue;
+    }
+    if (mode == OUT2_C2_F32) {
+      // FP32 output: d = fl32(fl32(S_i) + fl32(S_j)); exact, like the FP64
+      // sum, whenever the sums are integers below 2^24 (the FP64 pipe, at a
+      // small fraction of the FP32 rate, otherwise bounds the epilogue at
+      // small n_f)
+      float Sjf[C::NJ];
+#pragma unroll
+      for (int c = 0; c < C::NJ; ++c) {
+        const int j = col0 + L.col(c);
+        Sjf[c] = j < nv ? (float)S[j] : 0.0f;
+      }
+#pragma unroll
+      for (int r = 0; r < 8; ++r) {
+        const int i = row0 + L.row(r);
+        if (i >= nv) continue;
+        const float Sif = (float)S[i];
+        float* orow = static_cast<float*>(out) + (pair_index(nv, i, i + 1) - (i + 1));
+#pragma unroll
+        for (int c = 0; c < C::NJ; ++c) {
+          const int j = col0 + L.col(c);
+          if (j <= i || j >= nv) continue;
+          const float2 hl = acc.hl(r, c);
+          const float n2 = __fadd_rn(hl.x, hl.y);
+          const float d = __fadd_rn(Sif, Sjf[c]);
+          orow[j] = (d == 0.0f) ? 0.0f : __fdiv_rn(2.0f * n2, d);
+        }
+      }
+    } else {
+#pragma unroll
+      for (int r = 0; r < 8; ++r) {
+        const int i = row0 + L.row(r);
+        if (i >= nv) continue;
+        const double Si = S[i];
+        double* orow = static_cast<double*>(out) + (pair_index(nv, i, i + 1) - (i + 1));
+#pragma unroll
+        for (int c = 0; c < C::NJ; ++c) {
+          const int j = col0 + L.col(c);
+          if (j <= i || j >= nv) continue;
+          const float2 hl = acc.hl(r, c);
+          const double n2 = (double)hl.x + (double)hl.y;
+          const double d = Si + S[j];
+          orow[j] = (d == 0.0) ? 0.0 : (2.0 * n2) / d;
         }
       }
     }
@@ -465,6 +506,12 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
     band_tile(t, T, 0, T, G, I, J);
     const int row0 = I * C::BM, col0 = J * C::BN;
     tile_minsum<C, false, false, KU, true>(sm, V, row0, col0, 0, L.am, L.bn, acc);
+    float Sjf[C::NJ];
+#pragma unroll
+    for (int c = 0; c < C::NJ; ++c) {
+      const int j = col0 + L.col(c);
+      Sjf[c] = j < nv ? (float)S[j] : 0.0f;
+    }
 #pragma unroll
     for (int r = 0; r < 8; ++r) {
       const int i = row0 + L.row(r);
@@ -481,7 +528,7 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
           static_cast<double*>(out)[pair_index(nv, i, j)] = (d == 0.0) ? 0.0 : (2.0 * n2) / d;
         } else {
           const float n2 = __fmul_rn(__fadd_rn(hl.x, hl.y), inv_scale);
-          const float d = (float)(Si + S[j]);
+          const float d = __fadd_rn((float)Si, Sjf[c]);
           static_cast<float*>(out)[pair_index(nv, i, j)] = (d == 0.0f) ? 0.0f : __fdiv_rn(2.0f * n2, d);
         }
       }
@@ -713,8 +760,9 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
             const double d = Si + __ldcg(p.S + j);
             static_cast<double*>(p.out)[pair_index(nv, i, j)] = (d == 0.0) ? 0.0 : (2.0 * n2) / d;
           } else {
+            // the denominator as in mgemm2_kernel's FP32 output
             const float n2 = __fadd_rn(hl.x, hl.y);
-            const float d = (float)(Si + __ldcg(p.S + j));
+            const float d = __fadd_rn((float)Si, (float)__ldcg(p.S + j));
             static_cast<float*>(p.out)[pair_index(nv, i, j)] =
                 (d == 0.0f) ? 0.0f : __fdiv_rn(2.0f * n2, d);
           }
