@@ -424,6 +424,21 @@ def main():
         e2e = {"value": ws * cmp_per_step / dt, "unit": UNIT, "ms_per_step": dt * 1e3,
                "h2d_bytes_per_step": int(Vh.numel() * Vh.element_size()),
                "d2h_bytes_per_step": int(outh.numel() * outh.element_size())}
+        if w["way"] == 2 and ws == 1:
+            # the same call with one-byte metric codes (PS_U8) as the output
+            outu = torch.empty(out.numel(), dtype=torch.uint8).pin_memory()
+
+            def ustep():
+                ps.check(ps.ps_metrics_2way(h.h, ctypes.byref(mh), ps.PS_PATH_FP32, 0, outu.data_ptr(),
+                                            ps.PS_U8, sptr), h.h)
+            ustep()
+            t0 = time.perf_counter()
+            for _ in range(args.steps):
+                ustep()
+            du = (time.perf_counter() - t0) / args.steps
+            e2e["u8_codes"] = {"value": cmp_per_step / du, "unit": UNIT, "ms_per_step": du * 1e3,
+                               "d2h_bytes_per_step": int(outu.numel())}
+            del outu
         del Vh, outh
 
     # ---- sampled outputs of the timed run (checked in the CPU-baseline leg) ----

@@ -82,7 +82,13 @@ typedef enum {
   PS_ERR_UNSUPPORTED = 6
 } ps_status;
 
-typedef enum { PS_F32 = 0, PS_F64 = 1 } ps_dtype;
+/* PS_U8 is an output type only (ps_metrics_2way and ps_metrics_2way_part,
+ * paths PS_PATH_FP32 and PS_PATH_THERMO): the one-byte metric code of the
+ * realistic sample problem of Section 6.8 (one unsigned byte per metric,
+ * about 2.5 significant figures).  code = rint(255 * c2), round half to even,
+ * evaluated in FP32 on the FP32 metric; decode c2 ~ code / 255, absolute
+ * error <= 1/510 plus the FP32 error of c2. */
+typedef enum { PS_F32 = 0, PS_F64 = 1, PS_U8 = 2 } ps_dtype;
 
 typedef enum {
   /* FP32 min + FP32 add on the CUDA cores, chunked and compensated
@@ -149,7 +155,8 @@ ps_status ps_vector_sums(ps_handle h, const ps_matrix* V, double* S,
  *   path      : ps_path.
  *   levels    : PS_PATH_THERMO only, number of quantization levels L in
  *               [2, 16]; ignored otherwise.
- *   out       : nv*(nv-1)/2 values of out_dtype (PS_F32 or PS_F64), packed
+ *   out       : nv*(nv-1)/2 values of out_dtype (PS_F32, PS_F64, or PS_U8
+ *               codes with PS_PATH_FP32 / PS_PATH_THERMO), packed
  *               strict upper triangle, row-major:
  *                 out[i*(2*nv-i-1)/2 + (j-i-1)] = c2(v_i, v_j),  i < j.
  *               For PS_PATH_THERMO the metric is that of the quantized

@@ -28,6 +28,7 @@ __all__ = [
     "n3prime", "n2_packed", "c2_packed", "c2_pairs", "c3_triples",
     "n3prime_triples", "slab_size", "c3_slab", "threshold_3way",
     "percentile_nonzero", "quantize", "pair_index", "to_vector_major",
+    "metric_code",
 ]
 
 _lib = None
@@ -204,3 +205,15 @@ def quantize(x, levels: int, P: float) -> np.ndarray:
     q = np.empty(x.shape, dtype=np.int32)
     _load().oracle_quantize(_ptr(x), x.size, int(levels), ctypes.c_float(P), _ptr(q))
     return q
+
+
+def metric_code(c) -> np.ndarray:
+    """One-byte code of metric values (Section 6.8, the realistic sample
+    problem: every metric is written as one unsigned byte holding about 2.5
+    significant figures; the paper gives no formula).  Reading: the linear
+    code rint(255 c), round half to even, with the decision taken in FP32 on
+    the FP32-rounded metric (the precision the kernels decide in); codes above
+    255 clamp to 255.  Decoding code / 255 is within 1/510 of c in [0, 1]."""
+    c32 = np.asarray(c, dtype=np.float64).astype(np.float32)
+    q = np.rint(np.float32(255.0) * c32)
+    return np.minimum(q, np.float32(255.0)).astype(np.uint8)

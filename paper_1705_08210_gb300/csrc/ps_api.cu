@@ -114,7 +114,10 @@ ps_status ptr_kind(ps_ctx* h, const void* p, PtrKind* kind) {
   }
 }
 
-size_t dtype_size(int32_t dt) { return dt == PS_F64 ? 8 : 4; }
+size_t dtype_size(int32_t dt) { return dt == PS_F64 ? 8 : (dt == PS_U8 ? 1 : 4); }
+int out2_mode(int32_t out_dtype) {
+  return out_dtype == PS_F64 ? OUT2_C2_F64 : (out_dtype == PS_U8 ? OUT2_C2_U8 : OUT2_C2_F32);
+}
 
 // Elements spanned by the matrix in its own layout.
 int64_t matrix_span(const ps_matrix& V) {
@@ -246,7 +249,7 @@ ps_status run_percentile(ps_ctx* h, const VF32& v, cudaStream_t st, SelectState*
 }
 
 // Thermometer path of ps_metrics_2way (quantize, encode, tensor-core GEMM).
-ps_status thermo_2way(ps_ctx* h, const VF32& v, int levels, void* out, int out_f64, cudaStream_t st) {
+ps_status thermo_2way(ps_ctx* h, const VF32& v, int levels, void* out, int out_mode, cudaStream_t st) {
   SelectState* sel = nullptr;
   ps_status s = run_percentile(h, v, st, &sel);
   if (s != PS_OK) return s;
@@ -264,7 +267,7 @@ ps_status thermo_2way(ps_ctx* h, const VF32& v, int levels, void* out, int out_f
   }
   {
     ScopedTimer tm(h, "thermo_gemm", st);
-    PS_CUDA_TRY(h, launch_thermo_gemm(h, T, Kpad, v.nv, nv_pad, SQ, out, out_f64, err, sync, st));
+    PS_CUDA_TRY(h, launch_thermo_gemm(h, T, Kpad, v.nv, nv_pad, SQ, out, out_mode, err, sync, st));
   }
   int herr = 0;
   PS_CUDA_TRY(h, cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -472,10 +475,12 @@ ps_status ps_metrics_2way(ps_handle h, const ps_matrix* V, int32_t path, int32_t
   ps_status s = check_matrix(h, V, 2);
   if (s != PS_OK) return s;
   if (!out) return fail(h, PS_ERR_INVALID_ARG, "null out");
-  if (out_dtype != PS_F32 && out_dtype != PS_F64)
-    return fail(h, PS_ERR_INVALID_ARG, "out_dtype %d is not PS_F32/PS_F64", out_dtype);
+  if (out_dtype != PS_F32 && out_dtype != PS_F64 && out_dtype != PS_U8)
+    return fail(h, PS_ERR_INVALID_ARG, "out_dtype %d is not PS_F32/PS_F64/PS_U8", out_dtype);
   if (path != PS_PATH_FP32 && path != PS_PATH_FP64 && path != PS_PATH_THERMO && path != PS_PATH_HALF2)
     return fail(h, PS_ERR_INVALID_ARG, "path %d is not a ps_path", path);
+  if (out_dtype == PS_U8 && path != PS_PATH_FP32 && path != PS_PATH_THERMO)
+    return fail(h, PS_ERR_INVALID_ARG, "PS_U8 output needs PS_PATH_FP32 or PS_PATH_THERMO");
   if (path == PS_PATH_THERMO && (levels < 2 || levels > 16))
     return fail(h, PS_ERR_INVALID_ARG, "levels=%d outside [2,16]", levels);
   Guard g(h->device);
@@ -489,7 +494,7 @@ ps_status ps_metrics_2way(ps_handle h, const ps_matrix* V, int32_t path, int32_t
   if (path == PS_PATH_THERMO) {
     s = prepare(h, *V, st, true, &P, false);
     if (s != PS_OK) return s;
-    s = thermo_2way(h, P.f32, levels, o.dev, out_dtype == PS_F64, st);
+    s = thermo_2way(h, P.f32, levels, o.dev, out2_mode(out_dtype), st);
     if (s != PS_OK) return s;
   } else if (path == PS_PATH_HALF2) {
     s = prepare(h, *V, st, true, &P);
@@ -526,8 +531,8 @@ ps_status ps_metrics_2way(ps_handle h, const ps_matrix* V, int32_t path, int32_t
       partition_2way(V->nv, NB, b, &rb, &re);
       {
         ScopedTimer tm(h, "mgemm2", st);
-        e = launch_mgemm2(h, P.f32, P.S, o.dev, out_dtype == PS_F64 ? OUT2_C2_F64 : OUT2_C2_F32, st,
-                          (int)(rb / 128), (int)ceil_div(re, 128));
+        e = launch_mgemm2(h, P.f32, P.S, o.dev, out2_mode(out_dtype), st, (int)(rb / 128),
+                          (int)ceil_div(re, 128));
       }
       if (e == cudaSuccess) e = cudaEventRecord(ev[b], st);
       if (e == cudaSuccess) e = cudaStreamWaitEvent(h->copy_stream, ev[b], 0);
@@ -545,8 +550,7 @@ ps_status ps_metrics_2way(ps_handle h, const ps_matrix* V, int32_t path, int32_t
     s = prepare(h, *V, st, true, &P);
     if (s != PS_OK) return s;
     ScopedTimer tm(h, "mgemm2", st);
-    PS_CUDA_TRY(h, launch_mgemm2(h, P.f32, P.S, o.dev,
-                                 out_dtype == PS_F64 ? OUT2_C2_F64 : OUT2_C2_F32, st));
+    PS_CUDA_TRY(h, launch_mgemm2(h, P.f32, P.S, o.dev, out2_mode(out_dtype), st));
   } else {  // PS_PATH_FP64: FP64 field-major operand
     s = prepare(h, *V, st, false, &P);
     if (s != PS_OK) return s;
@@ -594,8 +598,8 @@ ps_status ps_metrics_2way_part(ps_handle h, const ps_matrix* V, int32_t nparts, 
   if (s != PS_OK) return s;
   if (nparts < 1 || part < 0 || part >= nparts) return fail(h, PS_ERR_INVALID_ARG, "part %d of %d", part, nparts);
   if (!out) return fail(h, PS_ERR_INVALID_ARG, "null out");
-  if (out_dtype != PS_F32 && out_dtype != PS_F64)
-    return fail(h, PS_ERR_INVALID_ARG, "out_dtype %d is not PS_F32/PS_F64", out_dtype);
+  if (out_dtype != PS_F32 && out_dtype != PS_F64 && out_dtype != PS_U8)
+    return fail(h, PS_ERR_INVALID_ARG, "out_dtype %d is not PS_F32/PS_F64/PS_U8", out_dtype);
   Guard g(h->device);
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   int64_t rb = 0, re = 0;
@@ -613,8 +617,8 @@ ps_status ps_metrics_2way_part(ps_handle h, const ps_matrix* V, int32_t nparts, 
     // row bands are whole 128-row tiles; the kernels use 128-wide tiles here
     const int keep_tile = h->mgemm_tile;
     h->mgemm_tile = 128;  // (8 or 16 warps per 128 x 128 tile as configured)
-    const cudaError_t e = launch_mgemm2(h, P.f32, P.S, o.dev, out_dtype == PS_F64 ? OUT2_C2_F64 : OUT2_C2_F32,
-                                        st, (int)(rb / 128), (int)ceil_div(re, 128));
+    const cudaError_t e = launch_mgemm2(h, P.f32, P.S, o.dev, out2_mode(out_dtype), st, (int)(rb / 128),
+                                        (int)ceil_div(re, 128));
     h->mgemm_tile = keep_tile;
     PS_CUDA_TRY(h, e);
   }

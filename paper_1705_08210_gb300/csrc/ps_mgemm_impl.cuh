@@ -438,7 +438,7 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
       }
       continue;
     }
-    if (mode == OUT2_C2_F32) {
+    if (mode == OUT2_C2_F32 || mode == OUT2_C2_U8) {
       // FP32 output: d = fl32(fl32(S_i) + fl32(S_j)); exact, like the FP64
       // sum, whenever the sums are integers below 2^24 (the FP64 pipe, at a
       // small fraction of the FP32 rate, otherwise bounds the epilogue at
@@ -454,7 +454,7 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
         const int i = row0 + L.row(r);
         if (i >= nv) continue;
         const float Sif = (float)S[i];
-        float* orow = static_cast<float*>(out) + (pair_index(nv, i, i + 1) - (i + 1));
+        const int64_t base = pair_index(nv, i, i + 1) - (i + 1);
 #pragma unroll
         for (int c = 0; c < C::NJ; ++c) {
           const int j = col0 + L.col(c);
@@ -462,7 +462,11 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
           const float2 hl = acc.hl(r, c);
           const float n2 = __fadd_rn(hl.x, hl.y);
           const float d = __fadd_rn(Sif, Sjf[c]);
-          orow[j] = (d == 0.0f) ? 0.0f : __fdiv_rn(2.0f * n2, d);
+          const float c2 = (d == 0.0f) ? 0.0f : __fdiv_rn(2.0f * n2, d);
+          if (mode == OUT2_C2_U8)
+            static_cast<unsigned char*>(out)[base + j] = c2_code(c2);
+          else
+            static_cast<float*>(out)[base + j] = c2;
         }
       }
     } else {

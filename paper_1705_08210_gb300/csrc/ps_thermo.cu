@@ -239,7 +239,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     thermo_gemm_kernel(const __grid_constant__ CUtensorMap mapA,
                        const __grid_constant__ CUtensorMap mapB, int nkb, int nv,
                        const int2* __restrict__ tiles, int64_t ntiles, const int* __restrict__ SQ,
-                       void* __restrict__ out, int out_f64, int* __restrict__ err,
+                       void* __restrict__ out, int out_mode, int* __restrict__ err,
                        unsigned* __restrict__ sync, int sync_kb) {
   extern __shared__ unsigned char smem_raw[];
   using CF = TCfg<MH>;
@@ -363,12 +363,16 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             if (i >= nv || j >= nv || j <= i) continue;
             const float n2 = xp[rr][lane];
             const int64_t o = pair_index(nv, i, j);
-            if (out_f64) {
+            if (out_mode == OUT2_C2_F64) {
               const double d = (double)si + (double)sq_j;
               static_cast<double*>(out)[o] = d == 0.0 ? 0.0 : (2.0 * (double)n2) / d;
             } else {
               const float d = (float)(si + sq_j);
-              static_cast<float*>(out)[o] = d == 0.0f ? 0.0f : __fdiv_rn(2.0f * n2, d);
+              const float c2 = d == 0.0f ? 0.0f : __fdiv_rn(2.0f * n2, d);
+              if (out_mode == OUT2_C2_U8)
+                static_cast<unsigned char*>(out)[o] = c2_code(c2);
+              else
+                static_cast<float*>(out)[o] = c2;
             }
           }
           __syncwarp();
@@ -430,7 +434,7 @@ uint64_t g_thermo_attr_devices[3] = {};
 
 template <int MH>
 cudaError_t launch_mh(ps_ctx* h, const uint8_t* T, int64_t Kpad, int nv, int nv_pad, const int* SQ,
-                      void* out, int out_f64, int* err, unsigned* sync, cudaStream_t s) {
+                      void* out, int out_mode, int* err, unsigned* sync, cudaStream_t s) {
   constexpr int TM = TCfg<MH>::TM;
   if (Kpad % TKB != 0 || nv_pad % TN != 0 || nv_pad % TM != 0 || ((uintptr_t)T % 16) != 0)
     return cudaErrorInvalidValue;
@@ -472,17 +476,17 @@ cudaError_t launch_mh(ps_ctx* h, const uint8_t* T, int64_t Kpad, int nv, int nv_
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   return cudaLaunchKernelEx(&cfg, thermo_gemm_kernel<MH>, mA, mB, nkb, nv, (const int2*)dtl, ntiles, SQ,
-                            out, out_f64, err, sync, sync_kb);
+                            out, out_mode, err, sync, sync_kb);
 }
 
 }  // namespace
 
 cudaError_t launch_thermo_gemm(ps_ctx* h, const uint8_t* T, int64_t Kpad, int nv, int nv_pad,
-                               const int* SQ, void* out, int out_f64, int* err, unsigned* sync,
+                               const int* SQ, void* out, int out_mode, int* err, unsigned* sync,
                                cudaStream_t s) {
   if (h->thermo_tile_m == 256)
-    return launch_mh<2>(h, T, Kpad, nv, nv_pad, SQ, out, out_f64, err, sync, s);
-  return launch_mh<1>(h, T, Kpad, nv, nv_pad, SQ, out, out_f64, err, sync, s);
+    return launch_mh<2>(h, T, Kpad, nv, nv_pad, SQ, out, out_mode, err, sync, s);
+  return launch_mh<1>(h, T, Kpad, nv, nv_pad, SQ, out, out_mode, err, sync, s);
 }
 
 }  // namespace ps

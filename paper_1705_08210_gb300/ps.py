@@ -23,7 +23,7 @@ if not os.path.exists(LIB_PATH):
 _lib = ctypes.CDLL(LIB_PATH)
 
 PS_OK, PS_ERR_INVALID_ARG, PS_ERR_OOM, PS_ERR_CUDA, PS_ERR_CAPACITY, PS_ERR_TIMEOUT, PS_ERR_UNSUPPORTED = range(7)
-PS_F32, PS_F64 = 0, 1
+PS_F32, PS_F64, PS_U8 = 0, 1, 2  # PS_U8: one-byte metric codes (2-way output only)
 PS_PATH_FP32, PS_PATH_FP64, PS_PATH_THERMO, PS_PATH_HALF2 = 0, 1, 2, 3
 PS_LAYOUT_FIELD_MAJOR, PS_LAYOUT_VECTOR_MAJOR = 0, 1
 

@@ -25,13 +25,14 @@ def metrics_2way(ps, handle, V, path=0, out_dtype=np.float32, layout=0, levels=0
         optr = out.ctypes.data
     else:
         X = torch.from_numpy(np.ascontiguousarray(V)).cuda()
-        out_t = torch.empty(npairs, dtype=torch.float32 if out_dtype == np.float32 else torch.float64,
-                            device="cuda")
+        tdt = {np.float32: torch.float32, np.float64: torch.float64, np.uint8: torch.uint8}[out_dtype]
+        out_t = torch.empty(npairs, dtype=tdt, device="cuda")
         m = ps.matrix(X, layout)
         optr = out_t.data_ptr()
     st = torch.cuda.current_stream() if stream is None else stream
     ps.check(ps.ps_metrics_2way(handle.h, ctypes.byref(m), path, levels, optr,
-                                0 if out_dtype == np.float32 else 1, st.cuda_stream), handle.h)
+                                {np.float32: 0, np.float64: 1, np.uint8: 2}[out_dtype], st.cuda_stream),
+             handle.h)
     torch.cuda.synchronize()
     return out if on_host else out_t.cpu().numpy()
 

@@ -183,3 +183,39 @@ def test_tile_walk_bands(ps, handle, band, monkeypatch):
         assert_rel(half, ref, 1e-3, f"half2 band {band}")
     finally:
         h.close()
+
+
+def test_u8_metric_codes(ps, handle):
+    # one-byte codes (PS_U8): integer data bit-exact; general data equal to
+    # the oracle's code except where 255*c2 lies within the FP32 tolerance of
+    # a rounding boundary (there the two sides may differ by one)
+    import torch
+    V = synth.integer_levels(700, 301, synth.seed_for(1, 61))
+    ref = oracle.c2_packed(oracle.to_vector_major(V))
+    np.testing.assert_array_equal(metrics_2way(ps, handle, V, out_dtype=np.uint8), oracle.metric_code(ref))
+    V = synth.zero_inflated(1100, 500, synth.seed_for(1, 62))
+    ref = oracle.c2_packed(oracle.to_vector_major(V))
+    got = metrics_2way(ps, handle, V, out_dtype=np.uint8).astype(np.int64)
+    want = oracle.metric_code(ref).astype(np.int64)
+    diff = got != want
+    assert np.all(np.abs(got - want) <= 1)
+    x = 255.0 * ref[diff]
+    assert np.all(np.abs(x - np.floor(x) - 0.5) <= 255.0 * RTOL32 * ref[diff] + 1e-6), x
+    print(f"u8 codes: {int(diff.sum())} of {diff.size} at a rounding boundary")
+    # host output (row bands with overlapped copies) and parts give the same bytes
+    np.testing.assert_array_equal(metrics_2way(ps, handle, V, out_dtype=np.uint8, on_host=True), got)
+    X = torch.from_numpy(V).cuda()
+    m = ps.matrix(X)
+    out = torch.zeros(ref.size, dtype=torch.uint8, device="cuda")
+    for p in range(3):
+        ps.check(ps.ps_metrics_2way_part(handle.h, ctypes.byref(m), 3, p, out.data_ptr(), ps.PS_U8,
+                                         torch.cuda.current_stream().cuda_stream), handle.h)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(out.cpu().numpy(), got)
+
+
+def test_u8_rejected_on_other_paths(ps, handle):
+    V = synth.zero_inflated(10, 5, synth.seed_for(1, 63))
+    for path in (ps.PS_PATH_FP64, ps.PS_PATH_HALF2):
+        with pytest.raises(ps.PSError):
+            metrics_2way(ps, handle, V, path=path, out_dtype=np.uint8)

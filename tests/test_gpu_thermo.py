@@ -116,3 +116,12 @@ def test_thermo_multi_round_producer_sync(ps, handle, sync_kb, monkeypatch):
         np.testing.assert_array_equal(got, ref.astype(np.float32))
     finally:
         h.close()
+
+
+def test_thermo_u8_codes_bit_exact(ps, handle):
+    # one-byte codes of the quantized-level metric: the FP32 metric is exact
+    # on both sides, so the codes match bit for bit
+    V = synth.zero_inflated(600, 300, synth.seed_for(2, 91))
+    ref = _levels_c2(V, 16)
+    got = metrics_2way(ps, handle, V, path=ps.PS_PATH_THERMO, levels=16, out_dtype=np.uint8)
+    np.testing.assert_array_equal(got, oracle.metric_code(ref))

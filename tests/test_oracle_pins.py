@@ -292,3 +292,29 @@ def test_thermometer_identity_matches_min_sum():
     for i in range(10):
         for j in range(i + 1, 10):
             assert via_matmul[i, j] == n2[oracle.pair_index(10, i, j)]
+
+
+def test_metric_code_grid_and_rounding():
+    # the 256 exact grid points k/255 encode to k; points 0.3/255 either side
+    # still round to k (a floor or ceiling instead of rounding fails here), and
+    # the ends map to 0 and 255 (a missing or wrong 255 scale fails here)
+    k = np.arange(256)
+    np.testing.assert_array_equal(oracle.metric_code(k / 255.0), k)
+    kk = np.arange(1, 255)
+    np.testing.assert_array_equal(oracle.metric_code((kk - 0.3) / 255.0), kk)
+    np.testing.assert_array_equal(oracle.metric_code((kk + 0.3) / 255.0), kk)
+    assert oracle.metric_code([0.0])[0] == 0 and oracle.metric_code([1.0])[0] == 255
+    # clamp above 1 (FP32 metrics may exceed 1 by an ulp)
+    assert oracle.metric_code([1.0 + 1e-7, 1.01])[1] == 255
+
+
+def test_metric_code_error_bound_and_monotone():
+    # |code/255 - c| <= 1/510 (+ FP32 rounding of c) on [0, 1]; non-decreasing
+    rng = np.random.default_rng(7)
+    c = np.sort(rng.random(200_000))
+    q = oracle.metric_code(c).astype(np.int64)
+    assert np.all(np.diff(q) >= 0)
+    assert np.max(np.abs(q / 255.0 - c)) <= 1.0 / 510.0 + 1e-6
+    # about 2.4 significant figures near 1: relative error at c >= 0.5 below 0.4%
+    hi = c >= 0.5
+    assert np.max(np.abs(q[hi] / 255.0 - c[hi]) / c[hi]) < 0.004
