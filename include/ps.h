@@ -118,6 +118,12 @@ typedef struct {
   int32_t layout; /* ps_layout */
 } ps_matrix;
 
+/* One thresholded 2-way result: indices i<j and c2 (FP32). */
+typedef struct {
+  int32_t i, j;
+  float value;
+} ps_pair;
+
 /* One thresholded 3-way result: indices i<j<k and c3 (FP32). */
 typedef struct {
   int32_t i, j, k;
@@ -216,6 +222,24 @@ ps_status ps_metrics_3way(ps_handle h, const ps_matrix* V, int64_t j_begin,
 ps_status ps_threshold_3way(ps_handle h, const ps_matrix* V, float tau,
                             int32_t use_proposal, ps_triple* out,
                             int64_t capacity, int64_t* count,
+                            ps_stream stream);
+
+/* ---------------------------------------------------------------------------
+ * Thresholded 2-way metrics: every pair i < j with c2(v_i, v_j) >= tau
+ * (Section 2.1's metric; thresholding the output, as Section 6.8's
+ * discussion of the metric data volume suggests, instead of writing all
+ * nv(nv-1)/2 values).  Values are bit-identical to ps_metrics_2way with
+ * PS_PATH_FP32 and PS_F32 output; pairs are sorted by (i, j).
+ *   out      : `capacity` ps_pair slots (device or host).
+ *   count    : one int64 (device or host) receiving the total number of
+ *              pairs found, also when it exceeds `capacity`.
+ * Returns PS_ERR_CAPACITY when the total exceeds `capacity`; the first
+ * `capacity` pairs in sorted order are then written.
+ * Synchronous: returns once the result and count are written.
+ * Errors: PS_ERR_INVALID_ARG for nv < 2 or nv > 2^31 - 1, capacity < 0 or
+ *   null pointers; PS_ERR_OOM if the hit buffer cannot grow. */
+ps_status ps_threshold_2way(ps_handle h, const ps_matrix* V, float tau,
+                            ps_pair* out, int64_t capacity, int64_t* count,
                             ps_stream stream);
 
 /* ---------------------------------------------------------------------------

@@ -28,7 +28,7 @@ __all__ = [
     "n3prime", "n2_packed", "c2_packed", "c2_pairs", "c3_triples",
     "n3prime_triples", "slab_size", "c3_slab", "threshold_3way",
     "percentile_nonzero", "quantize", "pair_index", "to_vector_major",
-    "metric_code",
+    "metric_code", "threshold_2way",
 ]
 
 _lib = None
@@ -217,3 +217,14 @@ def metric_code(c) -> np.ndarray:
     c32 = np.asarray(c, dtype=np.float64).astype(np.float32)
     q = np.rint(np.float32(255.0) * c32)
     return np.minimum(q, np.float32(255.0)).astype(np.uint8)
+
+
+def threshold_2way(V, tau: float):
+    """Every pair i < j with c2 >= tau (inclusive), sorted by (i, j): the
+    plain definition over c2_packed.  Returns (pairs[n, 2], values[n])."""
+    V = _f64(V)
+    nv = V.shape[0]
+    c = c2_packed(V)
+    ii, jj = np.triu_indices(nv, 1)  # row-major strict upper triangle = packed order
+    keep = c >= tau
+    return np.stack([ii[keep], jj[keep]], axis=1).astype(np.int64), c[keep]

@@ -721,6 +721,80 @@ ps_status ps_threshold_3way(ps_handle h, const ps_matrix* V, float tau, int32_t 
   return threshold_blocks(h, v, S, perm, blk, tau, out, capacity, count, st);
 }
 
+ps_status ps_threshold_2way(ps_handle h, const ps_matrix* V, float tau, ps_pair* out, int64_t capacity,
+                            int64_t* count, ps_stream stream) {
+  if (!h) return fail(nullptr, PS_ERR_INVALID_ARG, "null handle");
+  ps_status s = check_matrix(h, V, 2);
+  if (s != PS_OK) return s;
+  if (V->nv > 2147483647LL) return fail(h, PS_ERR_INVALID_ARG, "nv=%lld above 2^31-1", (long long)V->nv);
+  if (capacity < 0) return fail(h, PS_ERR_INVALID_ARG, "capacity < 0");
+  if (!count) return fail(h, PS_ERR_INVALID_ARG, "null count");
+  if (capacity > 0 && !out) return fail(h, PS_ERR_INVALID_ARG, "null out");
+  Guard g(h->device);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  Prepared P;
+  s = prepare(h, *V, st, true, &P);
+  if (s != PS_OK) return s;
+  const int bits = key_bits_for((int)V->nv);
+  int64_t cap = std::max<int64_t>({capacity, (int64_t)1 << 20, h->thresh_cap});
+  unsigned long long* counter = static_cast<unsigned long long*>(ws_get(h, WS_AUX3, 256));
+  if (!counter) return PS_ERR_OOM;
+  int64_t total = 0;
+  unsigned char* hits = nullptr;
+  for (int attempt = 0; attempt < 2; ++attempt) {
+    hits = static_cast<unsigned char*>(ws_get(h, WS_HITS, (size_t)cap * 24));
+    if (!hits) return PS_ERR_OOM;
+    ThreshArgs ta;
+    ta.tau = tau;
+    ta.bits = bits;
+    ta.keys = reinterpret_cast<unsigned long long*>(hits);
+    ta.vals = reinterpret_cast<float*>(hits + (size_t)cap * 16);
+    ta.counter = counter;
+    ta.cap = cap;
+    ta.perm = nullptr;
+    PS_CUDA_TRY(h, cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st));
+    {
+      ScopedTimer tm(h, "threshold2", st);
+      PS_CUDA_TRY(h, launch_mgemm2_thresh(h->num_sms, h->mgemm_band, P.f32, P.S, ta, st));
+    }
+    unsigned long long c = 0;
+    PS_CUDA_TRY(h, cudaMemcpyAsync(&c, counter, sizeof(c), cudaMemcpyDeviceToHost, st));
+    PS_CUDA_TRY(h, cudaStreamSynchronize(st));
+    total = (int64_t)c;
+    if (total <= cap) break;
+    cap = total;  // grow and compute once more
+    h->thresh_cap = cap;
+  }
+  if (total > cap) return fail(h, PS_ERR_CUDA, "threshold hit buffer could not hold %lld hits", (long long)total);
+  unsigned long long* keys = reinterpret_cast<unsigned long long*>(hits);
+  float* vals = reinterpret_cast<float*>(hits + (size_t)cap * 16);
+  const size_t words = radix_sort_scratch_words(total);
+  unsigned* scratch = static_cast<unsigned*>(ws_get(h, WS_SORT, words * sizeof(unsigned)));
+  if (!scratch) return PS_ERR_OOM;
+  {
+    ScopedTimer tm(h, "sort", st);
+    PS_CUDA_TRY(h, launch_radix_sort(h, keys, vals, keys + cap, vals + cap, total, 2 * bits, scratch, words, st));
+  }
+  const int64_t nout = std::min(total, capacity);
+  OutBuf o;
+  if (nout > 0) {
+    s = resolve_out(h, out, (size_t)nout * sizeof(ps_pair), WS_OUTPUT, &o);
+    if (s != PS_OK) return s;
+    PS_CUDA_TRY(h, launch_write_pairs(keys, vals, nout, bits, static_cast<ps_pair*>(o.dev), st));
+  }
+  OutBuf oc;
+  s = resolve_out(h, count, sizeof(int64_t), WS_AUX1, &oc);
+  if (s != PS_OK) return s;
+  const int64_t tot64 = total;
+  PS_CUDA_TRY(h, cudaMemcpyAsync(oc.dev, &tot64, sizeof(int64_t), cudaMemcpyHostToDevice, st));
+  if (o.host && o.bytes) PS_CUDA_TRY(h, cudaMemcpyAsync(o.user, o.dev, o.bytes, cudaMemcpyDeviceToHost, st));
+  if (oc.host) PS_CUDA_TRY(h, cudaMemcpyAsync(count, oc.dev, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+  PS_CUDA_TRY(h, cudaStreamSynchronize(st));
+  if (total > capacity)
+    return fail(h, PS_ERR_CAPACITY, "%lld pairs found, capacity %lld", (long long)total, (long long)capacity);
+  return PS_OK;
+}
+
 ps_status ps_proposal_last_stats(ps_handle h, double* kept_fraction, int64_t* blocks) {
   if (!h || !kept_fraction || !blocks) return fail(h, PS_ERR_INVALID_ARG, "null argument");
   *kept_fraction = h->last_kept;

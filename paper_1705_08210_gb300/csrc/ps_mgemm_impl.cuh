@@ -491,6 +491,67 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
 }
 
 // ---------------------------------------------------------------------------
+// Thresholded 2-way: every pair with c2 >= tau, the value computed exactly as
+// mgemm2_kernel's FP32 output.  Hits are appended warp-aggregated (one atomic
+// per warp and output position) as key i << bits | j; appends past `cap` are
+// counted but not stored.
+template <class C, bool PACKED, int KU>
+__global__ void __launch_bounds__(C::NT, C::MINB)
+    mgemm2_thresh_kernel(VF32 V, const double* __restrict__ S, int T, int G, int64_t ntiles,
+                         ThreshArgs ta) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Smem<C>& sm = *reinterpret_cast<Smem<C>*>(smem_raw);
+  const Lanes<C> L;
+  Acc<PACKED, C::NJ> acc;
+  const int64_t nv = V.nv;
+  const int lane = threadIdx.x & 31;
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    int I, J;
+    band_tile(t, T, 0, T, G, I, J);
+    const int row0 = I * C::BM, col0 = J * C::BN;
+    tile_minsum<C, false, PACKED, KU>(sm, V, row0, col0, 0, L.am, L.bn, acc);
+    float Sjf[C::NJ];
+#pragma unroll
+    for (int c = 0; c < C::NJ; ++c) {
+      const int j = col0 + L.col(c);
+      Sjf[c] = j < nv ? (float)S[j] : 0.0f;
+    }
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      const int i = row0 + L.row(r);
+      const float Sif = i < nv ? (float)S[i] : 0.0f;
+#pragma unroll
+      for (int c = 0; c < C::NJ; ++c) {
+        const int j = col0 + L.col(c);
+        float c2 = 0.0f;
+        bool hit = false;
+        if (i < nv && j > i && j < nv) {
+          const float2 hl = acc.hl(r, c);
+          const float n2 = __fadd_rn(hl.x, hl.y);
+          const float d = __fadd_rn(Sif, Sjf[c]);
+          c2 = (d == 0.0f) ? 0.0f : __fdiv_rn(2.0f * n2, d);
+          hit = c2 >= ta.tau;
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, hit);
+        if (m) {
+          const int leader = __ffs(m) - 1;
+          unsigned long long base = 0;
+          if (lane == leader) base = atomicAdd(ta.counter, (unsigned long long)__popc(m));
+          base = __shfl_sync(0xffffffffu, base, leader);
+          if (hit) {
+            const unsigned long long pos = base + (unsigned)__popc(m & ((1u << lane) - 1u));
+            if (pos < (unsigned long long)ta.cap) {
+              ta.keys[pos] = ((unsigned long long)i << ta.bits) | (unsigned long long)j;
+              ta.vals[pos] = c2;
+            }
+          }
+        }
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
 // 2-way on half2 field pairs (PS_PATH_HALF2): V holds (field 2p, field 2p+1)
 // of every vector, scaled by a power of two `scale` before rounding to FP16;
 // n2 = (hi + lo) / scale is exact rescaling.  Denominators S come from the

@@ -60,4 +60,25 @@ cudaError_t launch_thresh_t128(int num_sms, const VF32& V, const double* S, cons
   return cudaGetLastError();
 }
 
+cudaError_t launch_mgemm2_thresh(int num_sms, int band, const VF32& V, const double* S,
+                                 const ThreshArgs& ta, cudaStream_t st) {
+  using C = mg::T128;
+  static bool attrs_done[64] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const size_t smem = sizeof(mg::Smem<C>);
+  if (!attrs_done[dev & 63]) {
+    cudaError_t e = cudaFuncSetAttribute(mg::mgemm2_thresh_kernel<C, true, 8>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attrs_done[dev & 63] = true;
+  }
+  const int T = (int)ceil_div(V.nv, C::BM);
+  const int64_t ntiles = (int64_t)T * (T + 1) / 2;
+  if (ntiles == 0) return cudaSuccess;
+  const unsigned grid = (unsigned)std::min<int64_t>(ntiles, (int64_t)num_sms * C::MINB);
+  mg::mgemm2_thresh_kernel<C, true, 8><<<grid, C::NT, smem, st>>>(V, S, T, std::max(1, band), ntiles, ta);
+  return cudaGetLastError();
+}
+
 }  // namespace ps

@@ -151,6 +151,21 @@ __global__ void write_triples_kernel(const unsigned long long* __restrict__ keys
   }
 }
 
+__global__ void write_pairs_kernel(const unsigned long long* __restrict__ keys,
+                                   const float* __restrict__ vals, int64_t n, int bits,
+                                   ps_pair* __restrict__ out) {
+  const unsigned long long mask = (1ull << bits) - 1ull;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    const unsigned long long k = keys[p];
+    ps_pair q;
+    q.i = (int32_t)(k >> bits);
+    q.j = (int32_t)(k & mask);
+    q.value = vals[p];
+    out[p] = q;
+  }
+}
+
 }  // namespace
 
 size_t radix_sort_scratch_words(int64_t n) {
@@ -192,6 +207,14 @@ cudaError_t launch_radix_sort(ps_ctx* h, unsigned long long* keys, float* vals,
     e = cudaMemcpyAsync(vals, va, (size_t)n * sizeof(float), cudaMemcpyDeviceToDevice, st);
   }
   return e;
+}
+
+cudaError_t launch_write_pairs(const unsigned long long* keys, const float* vals, int64_t n,
+                               int bits, ps_pair* out, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  const unsigned grid = (unsigned)std::min<int64_t>(ceil_div(n, 256), 152 * 8);
+  write_pairs_kernel<<<grid, 256, 0, st>>>(keys, vals, n, bits, out);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_write_triples(const unsigned long long* keys, const float* vals, int64_t n,

@@ -41,6 +41,10 @@ class ps_problem(ctypes.Structure):
 PS_BATCH_PERSISTENT, PS_BATCH_PER_INSTANCE = 0, 1
 
 
+class ps_pair(ctypes.Structure):
+    _fields_ = [("i", ctypes.c_int32), ("j", ctypes.c_int32), ("value", ctypes.c_float)]
+
+
 class ps_triple(ctypes.Structure):
     _fields_ = [("i", ctypes.c_int32), ("j", ctypes.c_int32), ("k", ctypes.c_int32),
                 ("value", ctypes.c_float)]
@@ -70,6 +74,7 @@ ps_slab_size = _sig("ps_slab_size", _i64, [_i64, _i64, _i64])
 ps_metrics_3way = _sig("ps_metrics_3way", ctypes.c_int, [_h, _M, _i64, _i64, _p, _p])
 ps_threshold_3way = _sig("ps_threshold_3way", ctypes.c_int,
                          [_h, _M, ctypes.c_float, _i32, _p, _i64, _p, _p])
+ps_threshold_2way = _sig("ps_threshold_2way", ctypes.c_int, [_h, _M, ctypes.c_float, _p, _i64, _p, _p])
 ps_quantize = _sig("ps_quantize", ctypes.c_int, [_h, _M, _i32, _p, _p, _p])
 ps_timing_enable = _sig("ps_timing_enable", ctypes.c_int, [_h, _i32])
 ps_timing_read = _sig("ps_timing_read", ctypes.c_int,
@@ -96,7 +101,7 @@ ps_probe_minadd_peak = _sig("ps_probe_minadd_peak", ctypes.c_int,
                             [_h, _i32, ctypes.POINTER(ctypes.c_double)])
 
 EXPORTED = [n for n in globals() if n.startswith("ps_") and callable(globals()[n])
-            and n not in ("ps_matrix", "ps_triple", "ps_problem")]
+            and n not in ("ps_matrix", "ps_pair", "ps_triple", "ps_problem")]
 
 
 class PSError(RuntimeError):

@@ -98,3 +98,27 @@ def threshold_3way(ps, handle, V, tau, capacity, use_proposal=0, on_host=False):
     trip = raw[:n, :3].astype(np.int64)
     vals = raw[:n, 3].copy().view(np.float32)
     return st, count, trip, vals
+
+
+def threshold_2way(ps, handle, V, tau, capacity, on_host=False):
+    """Returns (status, count, pairs as (n,2) int array, values float32)."""
+    torch = _torch()
+    X = torch.from_numpy(np.ascontiguousarray(V)).cuda()
+    m = ps.matrix(X)
+    if on_host:
+        out = (ps.ps_pair * max(capacity, 1))()
+        cnt = ctypes.c_int64(-1)
+        st = ps.ps_threshold_2way(handle.h, ctypes.byref(m), float(tau), ctypes.addressof(out), capacity,
+                                  ctypes.addressof(cnt), 0)
+        raw = np.frombuffer(out, dtype=np.int32).reshape(-1, 3)
+        count = cnt.value
+    else:
+        out = torch.empty((max(capacity, 1), 3), dtype=torch.int32, device="cuda")
+        cnt = torch.full((1,), -1, dtype=torch.int64, device="cuda")
+        st = ps.ps_threshold_2way(handle.h, ctypes.byref(m), float(tau), out.data_ptr(), capacity,
+                                  cnt.data_ptr(), torch.cuda.current_stream().cuda_stream)
+        torch.cuda.synchronize()
+        raw = out.cpu().numpy()
+        count = int(cnt.item())
+    n = min(count, capacity) if count >= 0 else 0
+    return st, count, raw[:n, :2].astype(np.int64), raw[:n, 2].copy().view(np.float32)

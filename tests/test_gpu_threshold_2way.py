@@ -1,0 +1,76 @@
+"""GPU parity of the thresholded 2-way output (every pair with c2 >= tau,
+sorted by (i, j)) against the oracle.  Pairs within the FP32/FP64
+disagreement band |c2 - tau| <= 1e-5 tau may appear on either side; every
+reported value equals the full FP32 2-way output bit for bit."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1705_08210_gb300 import synth
+from gpu_run import metrics_2way, threshold_2way
+
+pytestmark = pytest.mark.gpu
+RTOL32 = 1e-5
+
+
+def _pair_pos(nv, p):
+    i, j = p[:, 0], p[:, 1]
+    return i * (2 * nv - i - 1) // 2 + (j - i - 1)
+
+
+def _check(ps, handle, V, tau, on_host=False):
+    nv = V.shape[1]
+    Vv = oracle.to_vector_major(V)
+    rp, rv = oracle.threshold_2way(Vv, tau)
+    st, count, pairs, vals = threshold_2way(ps, handle, V, tau, capacity=max(2 * len(rp), 16),
+                                            on_host=on_host)
+    assert st == ps.PS_OK and count == len(pairs)
+    if len(pairs):
+        assert np.all(pairs[:, 0] < pairs[:, 1])
+        key = pairs[:, 0] * nv + pairs[:, 1]
+        assert np.all(np.diff(key) > 0), "not sorted by (i, j) or repeated"
+    full = metrics_2way(ps, handle, V)
+    np.testing.assert_array_equal(vals, full[_pair_pos(nv, pairs)] if len(pairs) else vals)
+    ref = set(map(tuple, rp.tolist()))
+    got = set(map(tuple, pairs.tolist()))
+    c_all = oracle.c2_packed(Vv)
+    for p in ref ^ got:
+        c = c_all[_pair_pos(nv, np.array([p]))[0]]
+        assert abs(c - tau) <= RTOL32 * tau, (p, c)
+    return count
+
+
+@pytest.mark.parametrize("nv,nf,tau", [(2, 1, 0.0), (5, 3, 0.4), (300, 50, 0.3), (1100, 200, 0.25)])
+def test_threshold_2way_matches_oracle(ps, handle, nv, nf, tau):
+    V = synth.zero_inflated(nv, nf, synth.seed_for(6, nv))
+    _check(ps, handle, V, tau)
+
+
+def test_threshold_2way_latent_profiles_host_buffers(ps, handle):
+    V, _ = synth.latent_profiles(700, 120, synth.seed_for(6, 1), n_profiles=16, sigma=0.3)
+    assert _check(ps, handle, V, 0.6, on_host=True) > 0
+
+
+def test_threshold_2way_integer_data_exact(ps, handle):
+    V = synth.integer_levels(400, 90, synth.seed_for(6, 2))
+    Vv = oracle.to_vector_major(V)
+    rp, rv = oracle.threshold_2way(Vv, 0.5)
+    st, count, pairs, vals = threshold_2way(ps, handle, V, 0.5, capacity=len(rp) + 5)
+    assert st == ps.PS_OK and count == len(rp)
+    np.testing.assert_array_equal(pairs, rp)
+    np.testing.assert_array_equal(vals, rv.astype(np.float32))
+
+
+def test_threshold_2way_capacity_overflow_and_all_pairs(ps, handle):
+    nv = 600
+    V = synth.zero_inflated(nv, 40, synth.seed_for(6, 3))
+    n = nv * (nv - 1) // 2
+    st, count, pairs, vals = threshold_2way(ps, handle, V, 0.0, capacity=n)
+    assert st == ps.PS_OK and count == n
+    np.testing.assert_array_equal(pairs, np.stack(np.triu_indices(nv, 1), axis=1))
+    np.testing.assert_array_equal(vals, metrics_2way(ps, handle, V))
+    st, count, p2, v2 = threshold_2way(ps, handle, V, 0.0, capacity=1000)
+    assert st == ps.PS_ERR_CAPACITY and count == n
+    np.testing.assert_array_equal(p2, pairs[:1000])
+    st, count, p3, _ = threshold_2way(ps, handle, V, 1.5, capacity=0)
+    assert st == ps.PS_OK and count == 0

@@ -318,3 +318,18 @@ def test_metric_code_error_bound_and_monotone():
     # about 2.4 significant figures near 1: relative error at c >= 0.5 below 0.4%
     hi = c >= 0.5
     assert np.max(np.abs(q[hi] / 255.0 - c[hi]) / c[hi]) < 0.004
+
+
+def test_threshold_2way_hand_example():
+    # identical vectors give c2 = 1, disjoint supports 0, half overlap
+    # 2*1/(2+2) = 0.5; tau is inclusive; output sorted by (i, j)
+    V = np.array([[1.0, 1.0, 0.0, 0.0],
+                  [1.0, 1.0, 0.0, 0.0],
+                  [0.0, 0.0, 1.0, 1.0],
+                  [1.0, 0.0, 1.0, 0.0]])
+    pairs, vals = oracle.threshold_2way(V, 0.5)
+    np.testing.assert_array_equal(pairs, [[0, 1], [0, 3], [1, 3], [2, 3]])
+    np.testing.assert_allclose(vals, [1.0, 0.5, 0.5, 0.5], rtol=0, atol=1e-15)
+    pairs, vals = oracle.threshold_2way(V, 0.75)
+    np.testing.assert_array_equal(pairs, [[0, 1]])
+    assert oracle.threshold_2way(V, 1.5)[0].shape == (0, 2)
