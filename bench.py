@@ -584,6 +584,35 @@ def main():
             del Xs
         secondary["small_nf_output_bound"] = small
         del os_
+        torch.cuda.empty_cache()
+        # bit-packed 0/1 input (Sorenson case): bits straight into the tensor
+        # cores vs. the FP32 CUDA-core path on the same (unpacked) data
+        nvb, nfb = 32768, 8192
+        _, words = synth.binary_bits(nvb, nfb, synth.seed_for(7), junk_tail=False)
+        Wb = torch.from_numpy(words.view(np.int32)).cuda()
+        mb = ps.bit_matrix(Wb, nfb)
+        ob = torch.empty(nvb * (nvb - 1) // 2, dtype=torch.float32, device="cuda")
+        sor = {}
+        for name, path, kern in (("tensor_core_bits", ps.PS_PATH_THERMO, b"thermo_gemm"),
+                                 ("fp32_cuda_core", ps.PS_PATH_FP32, b"mgemm2")):
+            for _ in range(2):
+                ps.check(ps.ps_metrics_2way(h.h, ctypes.byref(mb), path, 0, ob.data_ptr(), 0, sptr), h.h)
+            ps.check(ps.ps_timing_enable(h.h, 1), h.h)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for _ in range(3):
+                ps.check(ps.ps_metrics_2way(h.h, ctypes.byref(mb), path, 0, ob.data_ptr(), 0, sptr), h.h)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            msb = e0.elapsed_time(e1) / 3
+            ps.check(ps.ps_timing_read(h.h, kern, ctypes.byref(n_launch), ctypes.byref(k_ms)), h.h)
+            ps.check(ps.ps_timing_enable(h.h, 0), h.h)
+            sor[name] = {"ms_per_step": msb, "kernel_ms": k_ms.value / max(n_launch.value, 1),
+                         "value": nfb * nvb * (nvb - 1) // 2 / (msb / 1e3), "unit": UNIT}
+        sor["speedup_tensor_vs_fp32"] = sor["fp32_cuda_core"]["ms_per_step"] / sor["tensor_core_bits"]["ms_per_step"]
+        sor["input"] = f"{nvb} x {nfb} bit-packed 0/1 (p_one 0.15), {words.nbytes / 1e6:.1f} MB"
+        secondary["sorenson_b1_32768x8192"] = sor
+        del Wb, ob
 
     # ---- thresholded 3-way search with proposals (8192 x 2048 latent profiles) ----
     thresh = None

@@ -87,8 +87,16 @@ typedef enum {
  * realistic sample problem of Section 6.8 (one unsigned byte per metric,
  * about 2.5 significant figures).  code = rint(255 * c2), round half to even,
  * evaluated in FP32 on the FP32 metric; decode c2 ~ code / 255, absolute
- * error <= 1/510 plus the FP32 error of c2. */
-typedef enum { PS_F32 = 0, PS_F64 = 1, PS_U8 = 2 } ps_dtype;
+ * error <= 1/510 plus the FP32 error of c2.
+ *
+ * PS_B1 is an input type: a bit-packed 0/1 matrix (Section 2.3, where the
+ * metric is the Sorenson metric).  Layout must be PS_LAYOUT_VECTOR_MAJOR;
+ * field q of vector i is bit (q % 32) of the 32-bit word data[i*ld + q/32]
+ * (ld in words, ld >= ceil(nf/32)); bits at q >= nf are ignored.  With
+ * PS_PATH_THERMO the bits are the tensor-core operand directly (no
+ * quantization; `levels` is ignored) and the result is exact; every other
+ * path and call unpacks the bits to 0.0 / 1.0 first. */
+typedef enum { PS_F32 = 0, PS_F64 = 1, PS_U8 = 2, PS_B1 = 3 } ps_dtype;
 
 typedef enum {
   /* FP32 min + FP32 add on the CUDA cores, chunked and compensated

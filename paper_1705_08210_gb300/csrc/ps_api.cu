@@ -114,6 +114,7 @@ ps_status ptr_kind(ps_ctx* h, const void* p, PtrKind* kind) {
   }
 }
 
+// bytes per stored element (a 32-bit word of 32 fields for PS_B1)
 size_t dtype_size(int32_t dt) { return dt == PS_F64 ? 8 : (dt == PS_U8 ? 1 : 4); }
 int out2_mode(int32_t out_dtype) {
   return out_dtype == PS_F64 ? OUT2_C2_F64 : (out_dtype == PS_U8 ? OUT2_C2_U8 : OUT2_C2_F32);
@@ -122,21 +123,25 @@ int out2_mode(int32_t out_dtype) {
 // Elements spanned by the matrix in its own layout.
 int64_t matrix_span(const ps_matrix& V) {
   if (V.nv == 0 || V.nf == 0) return 0;
+  if (V.dtype == PS_B1) return (V.nv - 1) * V.ld + ceil_div(V.nf, 32);
   if (V.layout == PS_LAYOUT_FIELD_MAJOR) return (V.nf - 1) * V.ld + V.nv;
   return (V.nv - 1) * V.ld + V.nf;
 }
 
 ps_status check_matrix(ps_ctx* h, const ps_matrix* V, int64_t min_nv) {
   if (!V) return fail(h, PS_ERR_INVALID_ARG, "null matrix descriptor");
-  if (V->dtype != PS_F32 && V->dtype != PS_F64)
-    return fail(h, PS_ERR_INVALID_ARG, "dtype %d is not PS_F32/PS_F64", V->dtype);
+  if (V->dtype != PS_F32 && V->dtype != PS_F64 && V->dtype != PS_B1)
+    return fail(h, PS_ERR_INVALID_ARG, "dtype %d is not PS_F32/PS_F64/PS_B1", V->dtype);
   if (V->layout != PS_LAYOUT_FIELD_MAJOR && V->layout != PS_LAYOUT_VECTOR_MAJOR)
     return fail(h, PS_ERR_INVALID_ARG, "layout %d is not a ps_layout", V->layout);
+  if (V->dtype == PS_B1 && V->layout != PS_LAYOUT_VECTOR_MAJOR)
+    return fail(h, PS_ERR_INVALID_ARG, "PS_B1 needs PS_LAYOUT_VECTOR_MAJOR");
   if (V->nv < min_nv) return fail(h, PS_ERR_INVALID_ARG, "nv=%lld < %lld", (long long)V->nv, (long long)min_nv);
   if (V->nf < 0) return fail(h, PS_ERR_INVALID_ARG, "nf=%lld < 0", (long long)V->nf);
   if (V->nv > (int64_t)1 << 30 || V->nf > (int64_t)1 << 30)
     return fail(h, PS_ERR_INVALID_ARG, "nv or nf exceeds 2^30");
-  const int64_t need = V->layout == PS_LAYOUT_FIELD_MAJOR ? V->nv : V->nf;
+  const int64_t need =
+      V->dtype == PS_B1 ? ceil_div(V->nf, 32) : (V->layout == PS_LAYOUT_FIELD_MAJOR ? V->nv : V->nf);
   if (V->ld < need || V->ld < 1)
     return fail(h, PS_ERR_INVALID_ARG, "ld=%lld smaller than the contiguous extent %lld",
                 (long long)V->ld, (long long)need);
@@ -268,6 +273,34 @@ ps_status thermo_2way(ps_ctx* h, const VF32& v, int levels, void* out, int out_m
   {
     ScopedTimer tm(h, "thermo_gemm", st);
     PS_CUDA_TRY(h, launch_thermo_gemm(h, T, Kpad, v.nv, nv_pad, SQ, out, out_mode, err, sync, st));
+  }
+  int herr = 0;
+  PS_CUDA_TRY(h, cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  PS_CUDA_TRY(h, cudaStreamSynchronize(st));
+  if (herr) return fail(h, PS_ERR_TIMEOUT, "tensor-core pipeline wait timed out");
+  return PS_OK;
+}
+
+// Bit-packed 0/1 input on the tensor cores: the bits are the operand (the
+// thermometer code of two levels), SQ the popcounts; exact.
+ps_status binary_2way(ps_ctx* h, const ps_matrix& Vdev, void* out, int out_mode, cudaStream_t st) {
+  const int nv = (int)Vdev.nv;
+  const int nv_pad = (int)round_up(nv, 256);
+  const int64_t Kpad = round_up(std::max<int64_t>(Vdev.nf, 1), 128);
+  uint8_t* T = static_cast<uint8_t*>(ws_get(h, WS_QUANT, (size_t)nv_pad * Kpad));
+  int* SQ = static_cast<int*>(ws_get(h, WS_AUX2, (size_t)nv_pad * sizeof(int)));
+  int* err = static_cast<int*>(ws_get(h, WS_AUX3, 256));
+  if (!T || !SQ || !err) return PS_ERR_OOM;
+  PS_CUDA_TRY(h, cudaMemsetAsync(err, 0, sizeof(int), st));
+  unsigned* sync = reinterpret_cast<unsigned*>(err + 32);
+  {
+    ScopedTimer tm(h, "b1_encode", st);
+    PS_CUDA_TRY(h, launch_b1_encode(static_cast<const uint32_t*>(Vdev.data), Vdev.ld, nv, Vdev.nf, T, Kpad,
+                                    nv_pad, SQ, st));
+  }
+  {
+    ScopedTimer tm(h, "thermo_gemm", st);
+    PS_CUDA_TRY(h, launch_thermo_gemm(h, T, Kpad, nv, nv_pad, SQ, out, out_mode, err, sync, st));
   }
   int herr = 0;
   PS_CUDA_TRY(h, cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -481,7 +514,8 @@ ps_status ps_metrics_2way(ps_handle h, const ps_matrix* V, int32_t path, int32_t
     return fail(h, PS_ERR_INVALID_ARG, "path %d is not a ps_path", path);
   if (out_dtype == PS_U8 && path != PS_PATH_FP32 && path != PS_PATH_THERMO)
     return fail(h, PS_ERR_INVALID_ARG, "PS_U8 output needs PS_PATH_FP32 or PS_PATH_THERMO");
-  if (path == PS_PATH_THERMO && (levels < 2 || levels > 16))
+  const bool binary = V->dtype == PS_B1 && path == PS_PATH_THERMO;
+  if (path == PS_PATH_THERMO && !binary && (levels < 2 || levels > 16))
     return fail(h, PS_ERR_INVALID_ARG, "levels=%d outside [2,16]", levels);
   Guard g(h->device);
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
@@ -491,7 +525,12 @@ ps_status ps_metrics_2way(ps_handle h, const ps_matrix* V, int32_t path, int32_t
   s = resolve_out(h, out, obytes, WS_OUTPUT, &o);
   if (s != PS_OK) return s;
   Prepared P;
-  if (path == PS_PATH_THERMO) {
+  if (binary) {
+    s = prepare(h, *V, st, false, &P, false);
+    if (s != PS_OK) return s;
+    s = binary_2way(h, P.dev, o.dev, out2_mode(out_dtype), st);
+    if (s != PS_OK) return s;
+  } else if (path == PS_PATH_THERMO) {
     s = prepare(h, *V, st, true, &P, false);
     if (s != PS_OK) return s;
     s = thermo_2way(h, P.f32, levels, o.dev, out2_mode(out_dtype), st);

@@ -88,6 +88,44 @@ __global__ void __launch_bounds__(256) pack_vm(const T* __restrict__ X, int64_t 
   }
 }
 
+// Bit-packed 0/1 input (PS_B1, Section 2.3's Sorenson case): field q of
+// vector i is bit q % 32 of word X[i*ld + q/32]; bits at q >= nf are ignored.
+__device__ __forceinline__ uint32_t b1_word(const uint32_t* __restrict__ X, int64_t ld, int64_t i,
+                                            int64_t w, int64_t nf) {
+  uint32_t x = __ldg(X + i * ld + w);
+  const int64_t rem = nf - w * 32;
+  if (rem < 32) x &= rem <= 0 ? 0u : ((1u << rem) - 1u);
+  return x;
+}
+
+// S_i = number of ones of vector i (exact in FP64), one warp per vector.
+__global__ void __launch_bounds__(256) vector_sums_b1(const uint32_t* __restrict__ X, int64_t ld,
+                                                      int64_t nv, int64_t nf,
+                                                      double* __restrict__ S) {
+  const int lane = threadIdx.x & 31;
+  const int64_t i = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (i >= nv) return;
+  long long c = 0;
+  for (int64_t w = lane; w * 32 < nf; w += 32) c += __popc(b1_word(X, ld, i, w, nf));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+  if (lane == 0) S[i] = (double)c;
+}
+
+// Bit-packed -> field-major 0/1 (FP32 or FP64), zero padding for i in
+// [nv, ldp): lane -> vector, warp -> word; each warp writes 32 rows q of 32
+// consecutive vectors.
+template <typename U>
+__global__ void __launch_bounds__(256) pack_b1(const uint32_t* __restrict__ X, int64_t ld, int64_t nv,
+                                               int64_t nf, U* __restrict__ out, int64_t ldp) {
+  const int64_t i = (int64_t)blockIdx.x * 32 + (threadIdx.x & 31);
+  const int64_t w = (int64_t)blockIdx.y * 8 + (threadIdx.x >> 5);
+  if (w * 32 >= nf || i >= ldp) return;
+  const uint32_t x = i < nv ? b1_word(X, ld, i, w, nf) : 0u;
+  const int nq = (int)min((int64_t)32, nf - w * 32);
+  for (int b = 0; b < nq; ++b) out[(w * 32 + b) * ldp + i] = (U)((x >> b) & 1u);
+}
+
 // Largest value of the matrix (non-negative data: unsigned order of the bit
 // patterns is the numeric order).
 __global__ void max_bits_kernel(VF32 V, unsigned* __restrict__ mx) {
@@ -142,7 +180,9 @@ cudaError_t launch_pack_half2(const VF32& V, uint32_t* out, int64_t ldo, unsigne
 
 cudaError_t launch_vector_sums(const ps_matrix& V, double* S, cudaStream_t st) {
   if (V.nv <= 0) return cudaSuccess;
-  if (V.layout == PS_LAYOUT_FIELD_MAJOR) {
+  if (V.dtype == PS_B1) {
+    vector_sums_b1<<<(unsigned)ceil_div(V.nv, 8), 256, 0, st>>>((const uint32_t*)V.data, V.ld, V.nv, V.nf, S);
+  } else if (V.layout == PS_LAYOUT_FIELD_MAJOR) {
     dim3 grid((unsigned)ceil_div(V.nv, 32));
     if (V.dtype == PS_F32)
       vector_sums_fm<float><<<grid, 256, 0, st>>>((const float*)V.data, V.ld, V.nv, V.nf, S);
@@ -161,7 +201,11 @@ cudaError_t launch_vector_sums(const ps_matrix& V, double* S, cudaStream_t st) {
 template <typename U>
 static cudaError_t launch_pack(const ps_matrix& V, U* out, int64_t ldp, cudaStream_t st) {
   if (V.nf <= 0 || ldp <= 0) return cudaSuccess;
-  if (V.layout == PS_LAYOUT_FIELD_MAJOR) {
+  if (V.dtype == PS_B1) {
+    if (ceil_div(ceil_div(V.nf, 32), 8) > 65535) return cudaErrorInvalidConfiguration;
+    dim3 grid((unsigned)ceil_div(ldp, 32), (unsigned)ceil_div(ceil_div(V.nf, 32), 8));
+    pack_b1<U><<<grid, 256, 0, st>>>((const uint32_t*)V.data, V.ld, V.nv, V.nf, out, ldp);
+  } else if (V.layout == PS_LAYOUT_FIELD_MAJOR) {
     const int64_t total = V.nf * ldp;
     const unsigned grid = (unsigned)std::min<int64_t>(ceil_div(total, 256), 152 * 64);
     if (V.dtype == PS_F32)

@@ -256,4 +256,49 @@ cudaError_t launch_thermo_encode(const VF32& V, int levels, const SelectState* s
   return cudaGetLastError();
 }
 
+namespace {
+
+// Bit-packed 0/1 vectors (PS_B1) straight into the tensor-core operand: row
+// i of T is vector i, byte q = 0x38 (FP8 E4M3 1.0) where bit q is set, zero
+// elsewhere and in the padding (q >= nf, i >= nv); SQ[i] = number of ones.
+// One warp per row, lane -> word; a word's 32 bits become 32 bytes: each
+// nibble is spread to one bit per byte by a multiply whose shifted copies
+// of the nibble (shifts 0, 7, 14, 21) occupy disjoint bit ranges.
+__global__ void __launch_bounds__(256) b1_encode_kernel(const uint32_t* __restrict__ X, int64_t ld,
+                                                        int nv, int64_t nf, uint8_t* __restrict__ T,
+                                                        int64_t Kpad, int nv_pad, int* __restrict__ SQ) {
+  const int lane = threadIdx.x & 31;
+  const int64_t i = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (i >= nv_pad) return;
+  const int64_t nw = Kpad / 32;
+  int c = 0;
+  for (int64_t w = lane; w < nw; w += 32) {
+    uint32_t x = 0;
+    if (i < nv && w * 32 < nf) {
+      x = __ldg(X + i * ld + w);
+      const int64_t rem = nf - w * 32;
+      if (rem < 32) x &= (1u << rem) - 1u;
+    }
+    c += __popc(x);
+    uint32_t b[8];
+#pragma unroll
+    for (int n = 0; n < 8; ++n) b[n] = (((x >> (4 * n)) & 0xFu) * 0x00204081u & 0x01010101u) * 0x38u;
+    uint4* dst = reinterpret_cast<uint4*>(T + i * Kpad + w * 32);
+    dst[0] = make_uint4(b[0], b[1], b[2], b[3]);
+    dst[1] = make_uint4(b[4], b[5], b[6], b[7]);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+  if (lane == 0) SQ[i] = c;
+}
+
+}  // namespace
+
+cudaError_t launch_b1_encode(const uint32_t* X, int64_t ld, int nv, int64_t nf, uint8_t* T, int64_t Kpad,
+                             int nv_pad, int* SQ, cudaStream_t s) {
+  if (Kpad % 32 != 0 || nv_pad <= 0) return cudaErrorInvalidValue;
+  b1_encode_kernel<<<(unsigned)ceil_div(nv_pad, 8), 256, 0, s>>>(X, ld, nv, nf, T, Kpad, nv_pad, SQ);
+  return cudaGetLastError();
+}
+
 }  // namespace ps

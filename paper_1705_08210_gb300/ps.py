@@ -23,7 +23,7 @@ if not os.path.exists(LIB_PATH):
 _lib = ctypes.CDLL(LIB_PATH)
 
 PS_OK, PS_ERR_INVALID_ARG, PS_ERR_OOM, PS_ERR_CUDA, PS_ERR_CAPACITY, PS_ERR_TIMEOUT, PS_ERR_UNSUPPORTED = range(7)
-PS_F32, PS_F64, PS_U8 = 0, 1, 2  # PS_U8: one-byte metric codes (2-way output only)
+PS_F32, PS_F64, PS_U8, PS_B1 = 0, 1, 2, 3  # PS_U8: one-byte codes (output); PS_B1: bit-packed 0/1 input
 PS_PATH_FP32, PS_PATH_FP64, PS_PATH_THERMO, PS_PATH_HALF2 = 0, 1, 2, 3
 PS_LAYOUT_FIELD_MAJOR, PS_LAYOUT_VECTOR_MAJOR = 0, 1
 
@@ -181,6 +181,18 @@ def matrix(X, layout: int = PS_LAYOUT_FIELD_MAJOR) -> ps_matrix:
     else:
         nv, nf = X.shape
     return ps_matrix(_ptr_of(X), nv, nf, max(int(s0), cols, 1), _dtype_of(X), layout)
+
+
+def bit_matrix(words, nf: int) -> ps_matrix:
+    """ps_matrix (PS_B1) for bit-packed 0/1 vectors: `words` is an (nv, ld)
+    uint32 array (torch or numpy), field q of vector i in bit q % 32 of
+    word [i, q // 32]."""
+    if hasattr(words, "stride") and callable(words.stride):
+        ld = words.stride()[0]
+    else:
+        ld = words.strides[0] // 4
+    nv = words.shape[0]
+    return ps_matrix(_ptr_of(words), nv, int(nf), max(int(ld), 1), PS_B1, PS_LAYOUT_VECTOR_MAJOR)
 
 
 def stream_ptr(stream) -> int:

@@ -115,3 +115,27 @@ def sample_triples(nv: int, n: int, seed: int) -> np.ndarray:
         out[c:c + len(t)] = t
         c += len(t)
     return out
+
+
+def binary_bits(nv: int, nf: int, seed: int, p_one: float = 0.15, ld_words: int | None = None,
+                junk_tail: bool = True):
+    """0/1 vectors (each field 1 with probability p_one), returned twice:
+    as the (nf, nv) field-major float32 matrix the oracle reads, and packed
+    for the library's PS_B1 input: an (nv, ld_words) uint32 array, field q
+    of vector i in bit q % 32 of word [i, q // 32].  With junk_tail the bits
+    at q >= nf (and the words past ceil(nf/32)) are filled with random bits,
+    which the library must ignore."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    dense = (rng.random((nf, nv)) < p_one).astype(np.float32)
+    nw = (nf + 31) // 32
+    ld = nw if ld_words is None else int(ld_words)
+    words = rng.integers(0, 2**32, size=(nv, max(ld, 1)), dtype=np.uint64).astype(np.uint32) \
+        if junk_tail else np.zeros((nv, max(ld, 1)), dtype=np.uint32)
+    bits = np.zeros((nv, nw * 32), dtype=np.uint8)
+    bits[:, :nf] = dense.T.astype(np.uint8)
+    if junk_tail and nf % 32:
+        bits[:, nf:] = rng.integers(0, 2, size=(nv, nw * 32 - nf), dtype=np.uint8)
+    packed = np.packbits(bits.reshape(nv, nw, 32)[:, :, ::-1], axis=2).reshape(nv, nw, 4)
+    words[:, :nw] = (packed[:, :, 0].astype(np.uint32) << 24 | packed[:, :, 1].astype(np.uint32) << 16
+                     | packed[:, :, 2].astype(np.uint32) << 8 | packed[:, :, 3].astype(np.uint32))
+    return dense, words

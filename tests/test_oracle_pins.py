@@ -333,3 +333,25 @@ def test_threshold_2way_hand_example():
     pairs, vals = oracle.threshold_2way(V, 0.75)
     np.testing.assert_array_equal(pairs, [[0, 1]])
     assert oracle.threshold_2way(V, 1.5)[0].shape == (0, 2)
+
+
+def test_sorenson_special_case_set_closed_forms():
+    # Section 2.3: for 0/1 vectors the metric is the Sorenson index
+    # 2|A & B| / (|A| + |B|); eq. (1) on sets: n3 = |A&B| + |A&C| + |B&C| -
+    # |A&B&C| (a field where exactly two vectors are 1 counts once, where all
+    # three are 1 twice)
+    rng = np.random.default_rng(23)
+    V = (rng.random((9, 70)) < 0.3).astype(np.float64)
+    sets = [set(np.nonzero(v)[0].tolist()) for v in V]
+    pairs = np.array([(i, j) for i in range(9) for j in range(i + 1, 9)])
+    want2 = [2 * len(sets[i] & sets[j]) / (len(sets[i]) + len(sets[j])) for i, j in pairs]
+    np.testing.assert_allclose(oracle.c2_pairs(V, pairs), want2, rtol=0, atol=1e-15)
+    trip = np.array([(i, j, k) for i in range(9) for j in range(i + 1, 9) for k in range(j + 1, 9)])
+    want3 = []
+    for i, j, k in trip:
+        A, B, C = sets[i], sets[j], sets[k]
+        n3 = len(A & B) + len(A & C) + len(B & C) - len(A & B & C)
+        two = sum(1 for q in range(70) if (q in A) + (q in B) + (q in C) == 2)
+        assert n3 == two + 2 * len(A & B & C)
+        want3.append(1.5 * n3 / (len(A) + len(B) + len(C)))
+    np.testing.assert_allclose(oracle.c3_triples(V, trip), want3, rtol=0, atol=1e-15)
