@@ -484,7 +484,8 @@ cudaError_t launch_mh(ps_ctx* h, const uint8_t* T, int64_t Kpad, int nv, int nv_
 cudaError_t launch_thermo_gemm(ps_ctx* h, const uint8_t* T, int64_t Kpad, int nv, int nv_pad,
                                const int* SQ, void* out, int out_mode, int* err, unsigned* sync,
                                cudaStream_t s) {
-  if (h->thermo_tile_m == 256)
+  const int tm = h->thermo_tile_m ? h->thermo_tile_m : (Kpad >= 16384 ? 256 : 128);
+  if (tm == 256)
     return launch_mh<2>(h, T, Kpad, nv, nv_pad, SQ, out, out_mode, err, sync, s);
   return launch_mh<1>(h, T, Kpad, nv, nv_pad, SQ, out, out_mode, err, sync, s);
 }

@@ -101,12 +101,15 @@ def test_thermo_config2_full_size_sampled(ps, handle):
           f"p99 {np.percentile(err, 99):.4f}")
 
 
+@pytest.mark.parametrize("tile_m", [128, 256])
 @pytest.mark.parametrize("sync_kb", [0, 1, 7])
-def test_thermo_multi_round_producer_sync(ps, handle, sync_kb, monkeypatch):
+def test_thermo_multi_round_producer_sync(ps, handle, sync_kb, tile_m, monkeypatch):
     # 20 x 20 tile blocks of 256 -> 210 tiles over 152 persistent CTAs (two
     # rounds); 30 k-blocks per tile; the producers meet every sync_kb
     # k-blocks (0: never, 7: a ragged last chunk).  Results stay bit-exact.
+    # (tile_m: the 128 x 256 tile with two accumulators, or the 256 x 256 tile)
     monkeypatch.setenv("PS_THERMO_SYNC_KB", str(sync_kb))
+    monkeypatch.setenv("PS_THERMO_TILE_M", str(tile_m))
     h = ps.Handle(0)
     try:
         nv, nf, L = 5000, 200, 16
