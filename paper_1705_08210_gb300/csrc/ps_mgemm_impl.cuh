@@ -292,7 +292,8 @@ __device__ __forceinline__ void compute_slice(const Smem<C>& sm, int buf, int am
 // Full k loop over n_f for one (row0, col0) tile, with optional pivot j.
 template <class C, bool PIVOT, bool PACKED, int KU, bool HALF = false>
 __device__ __forceinline__ void tile_minsum(Smem<C>& sm, const VF32& V, int row0, int col0,
-                                            int jpiv, int am, int bn, Acc<PACKED, C::NJ>& acc) {
+                                            int jpiv, int am, int bn, Acc<PACKED, C::NJ>& acc,
+                                            bool active = true) {
   acc.zero();
   const int nst = (V.nf + BK - 1) / BK;
 #pragma unroll
@@ -308,7 +309,8 @@ __device__ __forceinline__ void tile_minsum(Smem<C>& sm, const VF32& V, int row0
     const int sn = s + STAGES - 1;
     if (sn < nst) issue_slice<C, PIVOT>(sm, sn % STAGES, V, row0, col0, sn * BK, jpiv);
     cp_async_commit();
-    compute_slice<C, PACKED, KU, HALF>(sm, buf, am, bn, acc);
+    // (a warp with no valid output in this tile only helps stage the ring)
+    if (active) compute_slice<C, PACKED, KU, HALF>(sm, buf, am, bn, acc);
     if ((s + 1) % FOLD == 0) acc.fold();
   }
   acc.fold();
@@ -626,7 +628,11 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
     const int k0t = (j + 1) / C::BN;
     const int nK = Tk - k0t;
     const int row0 = (int)(local / nK) * C::BM, col0 = (k0t + (int)(local % nK)) * C::BN;
-    tile_minsum<C, true, PACKED, KU>(sm, V, row0, col0, j, L.am, L.bn, acc);
+    // a warp whose 64 rows all lie at or past the pivot (i >= j) has no
+    // output here: it skips the min-add loop, which frees the ALU pipe of
+    // its sub-partition for the other warp (the pivot's partial row tile)
+    tile_minsum<C, true, PACKED, KU>(sm, V, row0, col0, j, L.am, L.bn, acc,
+                                     row0 + (int)(threadIdx.x >> 5) / C::WN * 64 < j);
     const int64_t w = nv - 1 - j;
     const int64_t base = slab_offset(nv, jb, j);
     const double Sj = S[j];
@@ -672,7 +678,11 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
     const int row0 = I * B, col0 = K * B;
     // CTA-uniform skip: no row i < j or no column k > j in this item
     if (j >= nv || row0 >= j || col0 + B - 1 <= j || col0 >= nv) continue;
-    tile_minsum<C, true, PACKED, KU>(sm, V, row0, col0, j, L.am, L.bn, acc);
+    // a warp whose 64 rows all lie at or past the pivot (i >= j) has no
+    // output here: it skips the min-add loop, which frees the ALU pipe of
+    // its sub-partition for the other warp (the pivot's partial row tile)
+    tile_minsum<C, true, PACKED, KU>(sm, V, row0, col0, j, L.am, L.bn, acc,
+                                     row0 + (int)(threadIdx.x >> 5) / C::WN * 64 < j);
     const int oj = perm ? perm[j] : j;
 #pragma unroll
     for (int r = 0; r < 8; ++r) {
@@ -842,7 +852,11 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
     const int k0t = (j + 1) / C::BN;
     const int nK = Tk - k0t;
     const int row0 = (w.b / nK) * C::BM, col0 = (k0t + w.b % nK) * C::BN;
-    tile_minsum<C, true, PACKED, KU>(sm, V, row0, col0, j, L.am, L.bn, acc);
+    // a warp whose 64 rows all lie at or past the pivot (i >= j) has no
+    // output here: it skips the min-add loop, which frees the ALU pipe of
+    // its sub-partition for the other warp (the pivot's partial row tile)
+    tile_minsum<C, true, PACKED, KU>(sm, V, row0, col0, j, L.am, L.bn, acc,
+                                     row0 + (int)(threadIdx.x >> 5) / C::WN * 64 < j);
     if (!cta_wait_count(&n2_done[w.prob], p.n2_tiles, err, &s_flag)) continue;
     const int64_t wdt = nv - 1 - j;
     const int64_t base = slab_offset(nv, 0, j);
