@@ -380,14 +380,17 @@ __host__ __device__ __forceinline__ void band_tile(int64_t t, int T, int R0, int
   }
 }
 
-// Section 2.2 eq. (1): n3 = n2(ij) + n2(ik) + n2(jk) - n3' in FP64, then
-// c3 = (3/2) n3 / d3 rounded to FP32 (d3 = S_i + S_j + S_k from FP64 sums).
-__device__ __forceinline__ float c3_value(float2 n3p_hl, double n2ij, double n2ik, double n2jk,
-                                          double d3) {
-  const double n3p = (double)n3p_hl.x + (double)n3p_hl.y;
-  const double n3 = ((n2ij + n2ik) + n2jk) - n3p;
-  const float d = (float)d3;
-  return (d == 0.0f) ? 0.0f : __fdiv_rn(1.5f * (float)n3, d);
+// Section 2.2 eq. (1): n3 = ((n2(ij) + n2(ik)) + n2(jk)) - n3', then
+// c3 = (3/2) n3 / d3 with d3 = (S_i + S_j) + S_k, all in FP32 (the FP64
+// pipe runs at a small fraction of the FP32 rate on this part).  Exact for
+// integer data whose sums stay below 2^24; otherwise a few FP32 roundings:
+// per field (a <= b <= c) the n2 terms add to 2a + b <= 1.5 (a + b), so n3
+// suffers no cancellation.
+__device__ __forceinline__ float c3_value(float2 n3p_hl, float n2ij, float n2ik, float n2jk,
+                                          float d3) {
+  const float n3p = __fadd_rn(n3p_hl.x, n3p_hl.y);
+  const float n3 = __fsub_rn(__fadd_rn(__fadd_rn(n2ij, n2ik), n2jk), n3p);
+  return (d3 == 0.0f) ? 0.0f : __fdiv_rn(1.5f * n3, d3);
 }
 
 // Pivot-slab offset: sum_{j'=jb}^{j-1} j'(n-1-j') = F(j) - F(jb),
@@ -635,20 +638,26 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
                                      row0 + (int)(threadIdx.x >> 5) / C::WN * 64 < j);
     const int64_t w = nv - 1 - j;
     const int64_t base = slab_offset(nv, jb, j);
-    const double Sj = S[j];
+    const float Sj = (float)S[j];
+    float Skf[C::NJ];
+#pragma unroll
+    for (int c = 0; c < C::NJ; ++c) {
+      const int k = col0 + L.col(c);
+      Skf[c] = k < nv ? (float)S[k] : 0.0f;
+    }
 #pragma unroll
     for (int r = 0; r < 8; ++r) {
       const int i = row0 + L.row(r);
       if (i >= j) continue;
-      const double Sij = S[i] + Sj;
-      const double n2ij = (double)n2sq[(int64_t)i * nv + j];
+      const float Sij = __fadd_rn((float)S[i], Sj);
+      const float n2ij = n2sq[(int64_t)i * nv + j];
 #pragma unroll
       for (int c = 0; c < C::NJ; ++c) {
         const int k = col0 + L.col(c);
         if (k <= j || k >= nv) continue;
         out[base + (int64_t)i * w + (k - j - 1)] =
-            c3_value(acc.hl(r, c), n2ij, (double)n2sq[(int64_t)i * nv + k],
-                     (double)n2sq[(int64_t)j * nv + k], Sij + S[k]);
+            c3_value(acc.hl(r, c), n2ij, n2sq[(int64_t)i * nv + k], n2sq[(int64_t)j * nv + k],
+                     __fadd_rn(Sij, Skf[c]));
       }
     }
   }
@@ -702,9 +711,9 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
           if (bb > cc) { int x = bb; bb = cc; cc = x; x = pb; pb = pc; pc = x; }
           if (a > bb) { int x = a; a = bb; bb = x; x = pa; pa = pb; pb = x; }
         }
-        const float v = c3_value(acc.hl(r, c), (double)n2sq[(int64_t)pa * nv + pb],
-                                 (double)n2sq[(int64_t)pa * nv + pc], (double)n2sq[(int64_t)pb * nv + pc],
-                                 (S[pa] + S[pb]) + S[pc]);
+        const float v = c3_value(acc.hl(r, c), n2sq[(int64_t)pa * nv + pb], n2sq[(int64_t)pa * nv + pc],
+                                 n2sq[(int64_t)pb * nv + pc],
+                                 __fadd_rn(__fadd_rn((float)S[pa], (float)S[pb]), (float)S[pc]));
         if (v >= ta.tau) {
           const unsigned long long pos = atomicAdd(ta.counter, 1ull);
           if (pos < (unsigned long long)ta.cap) {
@@ -860,21 +869,21 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
     if (!cta_wait_count(&n2_done[w.prob], p.n2_tiles, err, &s_flag)) continue;
     const int64_t wdt = nv - 1 - j;
     const int64_t base = slab_offset(nv, 0, j);
-    const double Sj = __ldcg(p.S + j);
+    const float Sj = (float)__ldcg(p.S + j);
     float* out = static_cast<float*>(p.out);
 #pragma unroll
     for (int r = 0; r < 8; ++r) {
       const int i = row0 + L.row(r);
       if (i >= j) continue;
-      const double Sij = __ldcg(p.S + i) + Sj;
-      const double n2ij = (double)__ldcg(p.n2 + (int64_t)i * nv + j);
+      const float Sij = __fadd_rn((float)__ldcg(p.S + i), Sj);
+      const float n2ij = __ldcg(p.n2 + (int64_t)i * nv + j);
 #pragma unroll
       for (int c = 0; c < C::NJ; ++c) {
         const int k = col0 + L.col(c);
         if (k <= j || k >= nv) continue;
         out[base + (int64_t)i * wdt + (k - j - 1)] =
-            c3_value(acc.hl(r, c), n2ij, (double)__ldcg(p.n2 + (int64_t)i * nv + k),
-                     (double)__ldcg(p.n2 + (int64_t)j * nv + k), Sij + __ldcg(p.S + k));
+            c3_value(acc.hl(r, c), n2ij, __ldcg(p.n2 + (int64_t)i * nv + k), __ldcg(p.n2 + (int64_t)j * nv + k),
+                     __fadd_rn(Sij, (float)__ldcg(p.S + k)));
       }
     }
   }
