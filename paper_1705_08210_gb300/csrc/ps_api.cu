@@ -449,7 +449,7 @@ ps_status ps_create(ps_handle* out, int device) {
     if (ku == 4 || ku == 8 || ku == 16) h->mgemm_ku = ku;
   }
   if (const char* v = getenv("PS_MGEMM_TILE")) h->mgemm_tile = atoi(v) == 64 ? 64 : 128;
-  if (const char* v = getenv("PS_MGEMM_WARPS")) h->mgemm_warps = atoi(v) == 16 ? 16 : 8;
+  if (const char* v = getenv("PS_MGEMM_WARPS")) h->mgemm_warps = atoi(v) == 16 ? 16 : (atoi(v) == 8 ? 8 : 0);
   if (const char* v = getenv("PS_MGEMM_BAND")) h->mgemm_band = std::max(1, std::min(atoi(v), 64));
   if (const char* v = getenv("PS_THERMO_TILE_M")) h->thermo_tile_m = atoi(v) == 128 ? 128 : (atoi(v) == 256 ? 256 : 0);
   if (const char* v = getenv("PS_THERMO_SYNC_KB")) h->thermo_sync_kb = std::max(0, atoi(v));

@@ -139,15 +139,16 @@ const MgemmVariant* mgemm_variant_of(int code) {
   return mgemm_variant_t128(packed, ku);
 }
 
-int mgemm_variant_code(const ps_ctx* h) {
-  const int shape = h->mgemm_tile == 64 ? 1 : (h->mgemm_warps == 16 ? 2 : 0);
+int mgemm_variant_code(const ps_ctx* h, bool two_way) {
+  const int warps = h->mgemm_warps ? h->mgemm_warps : (two_way ? 16 : 8);
+  const int shape = h->mgemm_tile == 64 ? 1 : (warps == 16 ? 2 : 0);
   const int packed = shape ? 1 : (h->mgemm_packed_add ? 1 : 0);
   return shape * 1000 + packed * 100 + h->mgemm_ku;
 }
 
 cudaError_t launch_mgemm2(ps_ctx* h, const VF32& V, const double* S, void* out, int mode,
                           cudaStream_t st, int tile_begin, int tile_end) {
-  const int code = mgemm_variant_code(h);
+  const int code = mgemm_variant_code(h, true);
   const MgemmVariant* v = mgemm_variant_of(code);
   cudaError_t e = ensure_attrs(h, code, v);
   if (e != cudaSuccess) return e;
