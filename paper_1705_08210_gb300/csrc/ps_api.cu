@@ -550,7 +550,7 @@ ps_status ps_metrics_2way(ps_handle h, const ps_matrix* V, int32_t path, int32_t
     }
     const VF32 hv{reinterpret_cast<const float*>(vh), ldh, (int)V->nv, (int)np};
     ScopedTimer tm(h, "mgemm2_half", st);
-    PS_CUDA_TRY(h, launch_mgemm2_half(h->num_sms, h->mgemm_band, hv, P.S, o.dev, out_dtype == PS_F64, inv_scale, st));
+    PS_CUDA_TRY(h, launch_mgemm2_half(h->num_sms, h->mgemm_band, h->mgemm_warps, hv, P.S, o.dev, out_dtype == PS_F64, inv_scale, st));
   } else if (path == PS_PATH_FP32 && o.host && V->nv >= 8 * 128) {
     // host output: compute in equal-work row bands and copy each finished
     // band (a contiguous packed range) to the host on the handle's copy

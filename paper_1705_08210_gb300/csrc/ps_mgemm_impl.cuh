@@ -263,11 +263,16 @@ __device__ __forceinline__ void compute_slice(const Smem<C>& sm, int buf, int am
     for (int kk = 0; kk < BK; ++kk) {
       const uint4 a0 = *reinterpret_cast<const uint4*>(As + kk * C::BM);
       const uint4 a1 = *reinterpret_cast<const uint4*>(As + kk * C::BM + 32);
-      const uint4 b0 = *reinterpret_cast<const uint4*>(Bs + kk * C::BN);
-      const uint4 b1 = *reinterpret_cast<const uint4*>(Bs + kk * C::BN + 16);
       const uint32_t a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-      const uint32_t b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
-      acc.step_h(a, b);
+      const uint4 b0 = *reinterpret_cast<const uint4*>(Bs + kk * C::BN);
+      if constexpr (C::NJ == 8) {
+        const uint4 b1 = *reinterpret_cast<const uint4*>(Bs + kk * C::BN + 16);
+        const uint32_t b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+        acc.step_h(a, b);
+      } else {
+        const uint32_t b[4] = {b0.x, b0.y, b0.z, b0.w};
+        acc.step_h(a, b);
+      }
     }
     return;
   } else {

@@ -28,3 +28,17 @@ def test_half2_integer_data_bit_exact(ps, handle):
     ref = oracle.c2_packed(oracle.to_vector_major(V))
     np.testing.assert_array_equal(metrics_2way(ps, handle, V, path=ps.PS_PATH_HALF2), ref.astype(np.float32))
     np.testing.assert_array_equal(metrics_2way(ps, handle, V, path=ps.PS_PATH_HALF2, out_dtype=np.float64), ref)
+
+
+@pytest.mark.parametrize("warps", [8, 16])
+def test_half2_tile_warps(ps, monkeypatch, warps):
+    # both tile configurations of the half2 kernel (8 x 8 or 8 x 4 outputs
+    # per lane) give the same values
+    monkeypatch.setenv("PS_MGEMM_WARPS", str(warps))
+    h = ps.Handle(0)
+    try:
+        V = synth.zero_inflated(700, 333, synth.seed_for(2, 70))
+        ref = oracle.c2_packed(oracle.to_vector_major(V))
+        assert_rel(metrics_2way(ps, h, V, path=ps.PS_PATH_HALF2), ref, RTOL_HALF, f"half2 warps={warps}")
+    finally:
+        h.close()
