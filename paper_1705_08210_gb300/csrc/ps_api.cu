@@ -60,6 +60,30 @@ void* ws_get(ps_ctx* h, WsSlot slot, size_t bytes) {
   return p;
 }
 
+int* async_err_word(ps_ctx* h) {
+  if (!h->async_err_dev) {
+    void* p = nullptr;
+    cudaError_t e = cudaHostAlloc(&p, 256, cudaHostAllocMapped);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      fail(h, PS_ERR_OOM, "cudaHostAlloc(mapped error word): %s", cudaGetErrorString(e));
+      return nullptr;
+    }
+    void* d = nullptr;
+    e = cudaHostGetDevicePointer(&d, p, 0);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      cudaFreeHost(p);
+      fail(h, PS_ERR_CUDA, "cudaHostGetDevicePointer(mapped error word): %s", cudaGetErrorString(e));
+      return nullptr;
+    }
+    h->async_err_host = static_cast<int*>(p);
+    *(volatile int*)h->async_err_host = 0;
+    h->async_err_dev = static_cast<int*>(d);
+  }
+  return h->async_err_dev;
+}
+
 ScopedTimer::ScopedTimer(ps_ctx* h_, const char* name, cudaStream_t st_) : h(h_), st(st_) {
   if (!h || !h->timing) return;
   TimingRec r{name, nullptr, nullptr};
@@ -234,10 +258,27 @@ ps_status resolve_out(ps_ctx* h, void* user, size_t bytes, WsSlot slot, OutBuf* 
   return o->dev ? PS_OK : PS_ERR_OOM;
 }
 
+// A pipeline wait of the TMA-fed kernel timed out (2 s) in this call, if it
+// synchronised, or in an earlier asynchronous call on the handle: report it
+// once.
+ps_status take_async_error(ps_ctx* h) {
+  if (h->async_err_host && *(volatile int*)h->async_err_host) {
+    *(volatile int*)h->async_err_host = 0;
+    return fail(h, PS_ERR_TIMEOUT,
+                "a min-product pipeline wait timed out in this or an earlier asynchronous call on this "
+                "handle; that call's output is incomplete");
+  }
+  return PS_OK;
+}
+
 ps_status finish(ps_ctx* h, const OutBuf& o, bool any_host, cudaStream_t st) {
   if (o.host && o.bytes)
     PS_CUDA_TRY(h, cudaMemcpyAsync(o.user, o.dev, o.bytes, cudaMemcpyDeviceToHost, st));
-  if (any_host) PS_CUDA_TRY(h, cudaStreamSynchronize(st));
+  if (any_host) {
+    PS_CUDA_TRY(h, cudaStreamSynchronize(st));
+    const ps_status s = take_async_error(h);
+    if (s != PS_OK) return s;
+  }
   PS_CUDA_TRY(h, cudaGetLastError());
   return PS_OK;
 }
@@ -451,6 +492,16 @@ ps_status ps_create(ps_handle* out, int device) {
   if (const char* v = getenv("PS_MGEMM_TILE")) h->mgemm_tile = atoi(v) == 64 ? 64 : 128;
   if (const char* v = getenv("PS_MGEMM_WARPS")) h->mgemm_warps = atoi(v) == 16 ? 16 : (atoi(v) == 8 ? 8 : 0);
   if (const char* v = getenv("PS_MGEMM_BAND")) h->mgemm_band = std::max(1, std::min(atoi(v), 64));
+  if (const char* v = getenv("PS_MGEMM_FEED")) h->mgemm_feed_tma = strcmp(v, "cpasync") != 0;
+  if (const char* v = getenv("PS_MGEMM_TMA_BK")) {
+    const int bk = atoi(v);
+    h->mgemm_tma_bk = (bk == 16 || bk == 32 || bk == 64) ? bk : 0;
+  }
+  if (const char* v = getenv("PS_MGEMM_TMA_KU")) {
+    const int ku = atoi(v);
+    h->mgemm_tma_ku = (ku == 8 || ku == 16 || ku == 32) ? ku : 0;
+  }
+  if (const char* v = getenv("PS_MGEMM_TMA_STAGES")) h->mgemm_tma_stages = atoi(v) == 6 ? 6 : 4;
   if (const char* v = getenv("PS_THERMO_TILE_M")) h->thermo_tile_m = atoi(v) == 128 ? 128 : (atoi(v) == 256 ? 256 : 0);
   if (const char* v = getenv("PS_THERMO_SYNC_KB")) h->thermo_sync_kb = std::max(0, atoi(v));
   if (prop.major < 10) {
@@ -473,6 +524,7 @@ ps_status ps_destroy(ps_handle h) {
     mlp_free(h);
     for (int s = 0; s < WS_NUM_SLOTS; ++s)
       if (h->ws.ptr[s]) cudaFree(h->ws.ptr[s]);
+    if (h->async_err_host) cudaFreeHost(h->async_err_host);
   }
   delete h;
   return PS_OK;
@@ -505,6 +557,7 @@ ps_status ps_vector_sums(ps_handle h, const ps_matrix* V, double* S, ps_stream s
 ps_status ps_metrics_2way(ps_handle h, const ps_matrix* V, int32_t path, int32_t levels, void* out,
                           int32_t out_dtype, ps_stream stream) {
   if (!h) return fail(nullptr, PS_ERR_INVALID_ARG, "null handle");
+  if (const ps_status ae = take_async_error(h); ae != PS_OK) return ae;
   ps_status s = check_matrix(h, V, 2);
   if (s != PS_OK) return s;
   if (!out) return fail(h, PS_ERR_INVALID_ARG, "null out");
@@ -633,6 +686,7 @@ ps_status ps_partition(int64_t nv, int32_t way, int32_t nparts, int32_t part, in
 ps_status ps_metrics_2way_part(ps_handle h, const ps_matrix* V, int32_t nparts, int32_t part,
                                void* out, int32_t out_dtype, ps_stream stream) {
   if (!h) return fail(nullptr, PS_ERR_INVALID_ARG, "null handle");
+  if (const ps_status ae = take_async_error(h); ae != PS_OK) return ae;
   ps_status s = check_matrix(h, V, 2);
   if (s != PS_OK) return s;
   if (nparts < 1 || part < 0 || part >= nparts) return fail(h, PS_ERR_INVALID_ARG, "part %d of %d", part, nparts);
@@ -667,6 +721,7 @@ ps_status ps_metrics_2way_part(ps_handle h, const ps_matrix* V, int32_t nparts, 
 ps_status ps_metrics_3way(ps_handle h, const ps_matrix* V, int64_t j_begin, int64_t j_end,
                           float* out_slab, ps_stream stream) {
   if (!h) return fail(nullptr, PS_ERR_INVALID_ARG, "null handle");
+  if (const ps_status ae = take_async_error(h); ae != PS_OK) return ae;
   ps_status s = check_matrix(h, V, 3);
   if (s != PS_OK) return s;
   if (j_begin < 0 || j_end < j_begin || j_end > V->nv)
@@ -699,6 +754,7 @@ ps_status ps_metrics_3way(ps_handle h, const ps_matrix* V, int64_t j_begin, int6
 ps_status ps_threshold_3way(ps_handle h, const ps_matrix* V, float tau, int32_t use_proposal,
                             ps_triple* out, int64_t capacity, int64_t* count, ps_stream stream) {
   if (!h) return fail(nullptr, PS_ERR_INVALID_ARG, "null handle");
+  if (const ps_status ae = take_async_error(h); ae != PS_OK) return ae;
   ps_status s = check_matrix(h, V, 3);
   if (s != PS_OK) return s;
   if (V->nv > (1 << 21)) return fail(h, PS_ERR_INVALID_ARG, "nv=%lld above 2^21", (long long)V->nv);

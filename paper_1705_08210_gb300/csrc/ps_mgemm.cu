@@ -158,6 +158,12 @@ cudaError_t launch_mgemm2(ps_ctx* h, const VF32& V, const double* S, void* out, 
   // tiles in rows [0, I) of the triangle: I*T - I(I-1)/2
   const int64_t tbase = I0 * T - I0 * (I0 - 1) / 2;
   const int64_t ntiles = (I1 * T - I1 * (I1 - 1) / 2) - tbase;
+  if (code / 1000 == 2 && h->mgemm_feed_tma && V.nf > 0) {
+    int* err = async_err_word(h);
+    if (!err) return cudaErrorMemoryAllocation;
+    return launch_mgemm2_tma(h, V, S, out, mode, st, T, (int)I0, (int)I1, std::max(1, h->mgemm_band), ntiles,
+                             err);
+  }
   const unsigned grid = (unsigned)std::min<int64_t>(ntiles, (int64_t)h->num_sms * v->minb);
   v->mgemm2(grid, st, V, S, out, mode, T, (int)I0, (int)I1, std::max(1, h->mgemm_band), ntiles);
   return cudaGetLastError();

@@ -414,6 +414,105 @@ __host__ __device__ __forceinline__ int64_t pivot_tiles(int nv, int64_t j, int B
   return nI * nK;
 }
 
+// Epilogue of one 2-way tile (Section 2.1): the n2 table (both triangles), or
+// c2 = 2 n2 / (S_i + S_j) into the packed strict upper triangle as FP32,
+// FP64 or one-byte codes.  FP32 output: d = fl32(fl32(S_i) + fl32(S_j));
+// exact, like the FP64 sum, whenever the sums are integers below 2^24 (the
+// FP64 pipe, at a small fraction of the FP32 rate, would otherwise bound the
+// epilogue at small n_f).  Tiles strictly above the diagonal and inside the
+// matrix (every i < j < nv) take a path without per-output checks.
+template <class C, bool PACKED>
+__device__ __forceinline__ void store_tile2(const Acc<PACKED, C::NJ>& acc, const Lanes<C>& L, int row0,
+                                            int col0, int64_t nv, const double* __restrict__ S,
+                                            void* __restrict__ out, int mode) {
+  const bool interior = col0 >= row0 + C::BM && col0 + C::BN <= nv;
+  if (mode == OUT2_N2_SQUARE_F32) {
+    float* tab = static_cast<float*>(out);
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      const int i = row0 + L.row(r);
+      if (i >= nv) continue;
+#pragma unroll
+      for (int c = 0; c < C::NJ; ++c) {
+        const int j = col0 + L.col(c);
+        if (j <= i || j >= nv) continue;
+        const float2 hl = acc.hl(r, c);
+        const float n2 = __fadd_rn(hl.x, hl.y);
+        tab[(int64_t)i * nv + j] = n2;
+        tab[(int64_t)j * nv + i] = n2;
+      }
+    }
+    return;
+  }
+  if (mode == OUT2_C2_F32 || mode == OUT2_C2_U8) {
+    float Sjf[C::NJ];
+#pragma unroll
+    for (int c = 0; c < C::NJ; ++c) {
+      const int j = col0 + L.col(c);
+      Sjf[c] = j < nv ? (float)S[j] : 0.0f;
+    }
+    const bool u8 = mode == OUT2_C2_U8;
+    if (interior) {
+#pragma unroll
+      for (int r = 0; r < 8; ++r) {
+        const int i = row0 + L.row(r);
+        const float Sif = (float)S[i];
+        const int64_t base = pair_index(nv, i, i + 1) - (i + 1);
+#pragma unroll
+        for (int c = 0; c < C::NJ; ++c) {
+          const int j = col0 + L.col(c);
+          const float2 hl = acc.hl(r, c);
+          const float n2 = __fadd_rn(hl.x, hl.y);
+          const float d = __fadd_rn(Sif, Sjf[c]);
+          const float c2 = (d == 0.0f) ? 0.0f : __fdiv_rn(2.0f * n2, d);
+          if (u8)
+            static_cast<unsigned char*>(out)[base + j] = c2_code(c2);
+          else
+            static_cast<float*>(out)[base + j] = c2;
+        }
+      }
+      return;
+    }
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      const int i = row0 + L.row(r);
+      if (i >= nv) continue;
+      const float Sif = (float)S[i];
+      const int64_t base = pair_index(nv, i, i + 1) - (i + 1);
+#pragma unroll
+      for (int c = 0; c < C::NJ; ++c) {
+        const int j = col0 + L.col(c);
+        if (j <= i || j >= nv) continue;
+        const float2 hl = acc.hl(r, c);
+        const float n2 = __fadd_rn(hl.x, hl.y);
+        const float d = __fadd_rn(Sif, Sjf[c]);
+        const float c2 = (d == 0.0f) ? 0.0f : __fdiv_rn(2.0f * n2, d);
+        if (u8)
+          static_cast<unsigned char*>(out)[base + j] = c2_code(c2);
+        else
+          static_cast<float*>(out)[base + j] = c2;
+      }
+    }
+    return;
+  }
+#pragma unroll
+  for (int r = 0; r < 8; ++r) {
+    const int i = row0 + L.row(r);
+    if (i >= nv) continue;
+    const double Si = S[i];
+    double* orow = static_cast<double*>(out) + (pair_index(nv, i, i + 1) - (i + 1));
+#pragma unroll
+    for (int c = 0; c < C::NJ; ++c) {
+      const int j = col0 + L.col(c);
+      if (j <= i || j >= nv) continue;
+      const float2 hl = acc.hl(r, c);
+      const double n2 = (double)hl.x + (double)hl.y;
+      const double d = Si + S[j];
+      orow[j] = (d == 0.0) ? 0.0 : (2.0 * n2) / d;
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------
 // 2-way: all c2 (or the n2 table) over the upper triangle of tiles.
 template <class C, bool PACKED, int KU>
@@ -430,73 +529,7 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
     band_tile(t, T, R0, R1, G, I, J);
     const int row0 = I * C::BM, col0 = J * C::BN;
     tile_minsum<C, false, PACKED, KU>(sm, V, row0, col0, 0, L.am, L.bn, acc);
-    if (mode == OUT2_N2_SQUARE_F32) {
-#pragma unroll
-      for (int r = 0; r < 8; ++r) {
-        const int i = row0 + L.row(r);
-        if (i >= nv) continue;
-#pragma unroll
-        for (int c = 0; c < C::NJ; ++c) {
-          const int j = col0 + L.col(c);
-          if (j <= i || j >= nv) continue;
-          const float2 hl = acc.hl(r, c);
-          const float n2 = __fadd_rn(hl.x, hl.y);
-          float* tab = static_cast<float*>(out);
-          tab[(int64_t)i * nv + j] = n2;
-          tab[(int64_t)j * nv + i] = n2;
-        }
-      }
-      continue;
-    }
-    if (mode == OUT2_C2_F32 || mode == OUT2_C2_U8) {
-      // FP32 output: d = fl32(fl32(S_i) + fl32(S_j)); exact, like the FP64
-      // sum, whenever the sums are integers below 2^24 (the FP64 pipe, at a
-      // small fraction of the FP32 rate, otherwise bounds the epilogue at
-      // small n_f)
-      float Sjf[C::NJ];
-#pragma unroll
-      for (int c = 0; c < C::NJ; ++c) {
-        const int j = col0 + L.col(c);
-        Sjf[c] = j < nv ? (float)S[j] : 0.0f;
-      }
-#pragma unroll
-      for (int r = 0; r < 8; ++r) {
-        const int i = row0 + L.row(r);
-        if (i >= nv) continue;
-        const float Sif = (float)S[i];
-        const int64_t base = pair_index(nv, i, i + 1) - (i + 1);
-#pragma unroll
-        for (int c = 0; c < C::NJ; ++c) {
-          const int j = col0 + L.col(c);
-          if (j <= i || j >= nv) continue;
-          const float2 hl = acc.hl(r, c);
-          const float n2 = __fadd_rn(hl.x, hl.y);
-          const float d = __fadd_rn(Sif, Sjf[c]);
-          const float c2 = (d == 0.0f) ? 0.0f : __fdiv_rn(2.0f * n2, d);
-          if (mode == OUT2_C2_U8)
-            static_cast<unsigned char*>(out)[base + j] = c2_code(c2);
-          else
-            static_cast<float*>(out)[base + j] = c2;
-        }
-      }
-    } else {
-#pragma unroll
-      for (int r = 0; r < 8; ++r) {
-        const int i = row0 + L.row(r);
-        if (i >= nv) continue;
-        const double Si = S[i];
-        double* orow = static_cast<double*>(out) + (pair_index(nv, i, i + 1) - (i + 1));
-#pragma unroll
-        for (int c = 0; c < C::NJ; ++c) {
-          const int j = col0 + L.col(c);
-          if (j <= i || j >= nv) continue;
-          const float2 hl = acc.hl(r, c);
-          const double n2 = (double)hl.x + (double)hl.y;
-          const double d = Si + S[j];
-          orow[j] = (d == 0.0) ? 0.0 : (2.0 * n2) / d;
-        }
-      }
-    }
+    store_tile2<C, PACKED>(acc, L, row0, col0, nv, S, out, mode);
   }
 }
 

@@ -1,0 +1,222 @@
+// ps_mgemm_tma.cu -- the 2-way FP32 min-product (Section 3.1's mGEMM) fed by
+// the tensor memory accelerator.
+//
+// Same tile (128 x 128 outputs, upper-triangle tiles only, banded walk),
+// same micro-kernel (a lane owns 8 x 4 outputs; one FP32 min + one packed
+// FP32 add per comparison; TwoSum fold every 64 fields) and same epilogue as
+// the cp.async kernel of ps_mgemm_impl.cuh, but the operands arrive through
+// the TMA: per BK-field slice, two 2-D tensor loads (the 128-vector row
+// panel and the 128-vector column panel of V, field-major, zero-filled past
+// nv and nf) into an STAGES-deep shared-memory ring guarded by full/empty
+// mbarriers.  Lane 0 of warp 0 is the producer: before computing slice s it
+// loads slice s + STAGES - 1 (the walk over this CTA's tiles is one flat
+// sequence of slices, so near the end of a tile it already loads the next
+// tile's first slices, which then land while the warps write outputs).  A
+// warp releases a slice with one arrival when it is done with it.  The 16
+// warps compute no addresses and never meet at a CTA barrier.  (A separate
+// producer warp would make 17 warps; the SM's register file, split across
+// four schedulers, would then cap every thread at 96 registers.)
+// Every wait is bounded (ps_sync.cuh); on a timeout the kernel raises the
+// handle's mapped error word, lets issued copies land and returns.
+#include "ps_mgemm_impl.cuh"
+#include "ps_sync.cuh"
+
+#include <algorithm>
+#include <mutex>
+
+namespace ps {
+namespace {
+
+using C = mg::T128W16;  // 128 x 128 tile, 16 warps of 8 x 4 outputs per lane
+constexpr int NW = C::NT / 32;
+
+template <int BK, int STAGES>
+struct __align__(128) SmemT {
+  float A[STAGES][BK][C::BM];  // rows: field q of the slice; 128 consecutive vectors
+  float B[STAGES][BK][C::BN];
+  unsigned long long full[STAGES];
+  unsigned long long empty[STAGES];
+  int abort;
+};
+
+// BK k-steps of the micro-kernel on one landed slice.
+template <int BK, int KU>
+__device__ __forceinline__ void compute_slice_tma(const float* As, const float* Bs,
+                                                  mg::Acc<true, C::NJ>& acc) {
+#pragma unroll KU
+  for (int kk = 0; kk < BK; ++kk) {
+    const float4 a0 = *reinterpret_cast<const float4*>(As + kk * C::BM);
+    const float4 a1 = *reinterpret_cast<const float4*>(As + kk * C::BM + 32);
+    const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+    const float4 b0 = *reinterpret_cast<const float4*>(Bs + kk * C::BN);
+    const float b[4] = {b0.x, b0.y, b0.z, b0.w};
+    acc.step(a, b);
+  }
+}
+
+template <int BK, int STAGES, int KU>
+__global__ void __launch_bounds__(C::NT, 1)
+    mgemm2_tma_kernel(const __grid_constant__ CUtensorMap mapV, int nv, int nf,
+                      const double* __restrict__ S, void* __restrict__ out, int mode, int T, int R0,
+                      int R1, int G, int64_t ntiles, int* err) {
+  static_assert(mg::FOLD * mg::BK % BK == 0, "a fold boundary ends a slice");
+  constexpr int FOLD_SLICES = mg::FOLD * mg::BK / BK;  // 64 fields per compensated fold
+  constexpr uint32_t SLICE_BYTES = 2u * BK * C::BM * sizeof(float);
+  // (cast straight from the shared array, so that the compiler keeps shared
+  // loads for the operands: realigning through an integer made them generic)
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  SmemT<BK, STAGES>& sm = *reinterpret_cast<SmemT<BK, STAGES>*>(smem_raw);
+  const int lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      sy::bar_init(&sm.full[s], 1);
+      sy::bar_init(&sm.empty[s], NW);
+    }
+    sm.abort = 0;
+    sy::bar_init_fence();
+  }
+  __syncthreads();
+  const int nkb = (nf + BK - 1) / BK;
+  // this CTA's tiles: blockIdx.x, blockIdx.x + gridDim.x, ...
+  const int64_t my_tiles = ntiles > blockIdx.x ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  const uint64_t n_slices = (uint64_t)my_tiles * (uint64_t)nkb;
+
+  // producer state (lane 0 of warp 0): next slice to load and its tile
+  const bool producer = threadIdx.x == 0;
+  uint64_t g_next = 0;
+  int pI = 0, pJ = 0;
+  // loads slice g_next (waiting until its ring stage is free); false on abort
+  auto issue_one = [&]() -> bool {
+    if (g_next >= n_slices) return true;
+    const int s = (int)(g_next % STAGES);
+    const uint32_t ph = (uint32_t)(g_next / STAGES) & 1u;
+    const int kb = (int)(g_next % (uint64_t)nkb);
+    if (kb == 0) mg::band_tile(blockIdx.x + (int64_t)(g_next / nkb) * gridDim.x, T, R0, R1, G, pI, pJ);
+    if (!sy::bar_wait(&sm.empty[s], ph ^ 1u, &sm.abort, err)) return false;
+    sy::bar_arrive_tx(&sm.full[s], SLICE_BYTES);
+    sy::tma_load_2d(&sm.A[s][0][0], &mapV, pI * C::BM, kb * BK, &sm.full[s]);
+    sy::tma_load_2d(&sm.B[s][0][0], &mapV, pJ * C::BN, kb * BK, &sm.full[s]);
+    ++g_next;
+    return true;
+  };
+  if (producer)
+    for (int p = 0; p < STAGES - 1; ++p)
+      if (!issue_one()) break;
+
+  const mg::Lanes<C> L;
+  mg::Acc<true, C::NJ> acc;
+  uint64_t it = 0;
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    int I, J;
+    mg::band_tile(t, T, R0, R1, G, I, J);
+    const int row0 = I * C::BM, col0 = J * C::BN;
+    acc.zero();
+    bool ok = true;
+    for (int kb = 0; kb < nkb; ++kb, ++it) {
+      if (producer) ok = issue_one();  // slice it + STAGES - 1
+      const int s = (int)(it % STAGES);
+      const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
+      // every lane waits (each gets the barrier's acquire); the warp follows
+      // the common verdict so that it never diverges here
+      const bool mine = ok && sy::bar_wait(&sm.full[s], ph, &sm.abort, err);
+      if (!__all_sync(0xffffffffu, mine)) { ok = false; break; }
+      compute_slice_tma<BK, KU>(&sm.A[s][0][L.am], &sm.B[s][0][L.bn], acc);
+      __syncwarp();
+      if (lane == 0) sy::bar_arrive(&sm.empty[s]);
+      if ((kb + 1) % FOLD_SLICES == 0) acc.fold();
+    }
+    if (!ok) break;
+    acc.fold();
+    mg::store_tile2<C, true>(acc, L, row0, col0, nv, S, out, mode);
+  }
+  __syncthreads();
+  if (*(volatile int*)&sm.abort) sy::drain_after_abort();
+}
+
+// ---- host side ----
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                   const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                   const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+    cudaGetLastError();
+  });
+  return fn;
+}
+
+// V as a 2-D FP32 tensor: x = vector index (contiguous, nv), y = field (nf,
+// ld floats apart); box 128 vectors x BK fields, zero fill outside.
+bool make_map_v(CUtensorMap* m, const VF32& V, int bk) {
+  EncodeTiledFn enc = encode_fn();
+  if (!enc) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)V.nv, (cuuint64_t)std::max(V.nf, 1)};
+  const cuuint64_t strides[1] = {(cuuint64_t)V.ld * sizeof(float)};
+  const cuuint32_t box[2] = {(cuuint32_t)C::BM, (cuuint32_t)bk};
+  const cuuint32_t estr[2] = {1, 1};
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(V.p), dims, strides, box, estr,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int BK, int STAGES, int KU>
+struct TmaLaunch {
+  static constexpr size_t smem = sizeof(SmemT<BK, STAGES>);
+  static cudaError_t run(ps_ctx* h, const VF32& V, const double* S, void* out, int mode, cudaStream_t st,
+                         int T, int R0, int R1, int G, int64_t ntiles, int* err) {
+    static std::mutex mu;
+    static uint64_t attr_done = 0;
+    {
+      std::lock_guard<std::mutex> lk(mu);
+      const uint64_t bit = 1ull << (h->device & 63);
+      if (!(attr_done & bit)) {
+        const cudaError_t e = cudaFuncSetAttribute(mgemm2_tma_kernel<BK, STAGES, KU>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr_done |= bit;
+      }
+    }
+    CUtensorMap map;
+    if (!make_map_v(&map, V, BK)) return cudaErrorInvalidValue;
+    const unsigned grid = (unsigned)std::min<int64_t>(ntiles, (int64_t)h->num_sms);
+    mgemm2_tma_kernel<BK, STAGES, KU><<<grid, C::NT, smem, st>>>(map, V.nv, V.nf, S, out, mode, T, R0, R1, G,
+                                                              ntiles, err);
+    return cudaGetLastError();
+  }
+};
+
+}  // namespace
+
+cudaError_t launch_mgemm2_tma(ps_ctx* h, const VF32& V, const double* S, void* out, int mode, cudaStream_t st,
+                              int T, int R0, int R1, int G, int64_t ntiles, int* err) {
+  // TMA: 16-byte aligned base and row pitch; the tile walk assumes 128-wide tiles
+  if ((uintptr_t)V.p % 16 != 0 || V.ld % 4 != 0 || V.nv < 1) return cudaErrorInvalidValue;
+  // slice width: 16 fields up to n_f = 32 (wider slices would be mostly zero
+  // fill), else the configured width (32 by default: fewer waits and
+  // releases per comparison)
+  const int bk = V.nf <= 32 ? 16 : (h->mgemm_tma_bk ? h->mgemm_tma_bk : 32);
+  // k-steps per unrolled loop iteration: 16 (0 = automatic), 8 or 32
+  const int ku = h->mgemm_tma_ku ? h->mgemm_tma_ku : 16;
+  const int stages = h->mgemm_tma_stages;
+#define PS_TMA_RUN(BK_, ST_, KU_) TmaLaunch<BK_, ST_, KU_>::run(h, V, S, out, mode, st, T, R0, R1, G, ntiles, err)
+  if (bk == 64) return PS_TMA_RUN(64, 3, 16);
+  if (bk == 32) {
+    if (stages == 6) return PS_TMA_RUN(32, 6, 16);
+    if (ku == 8) return PS_TMA_RUN(32, 4, 8);
+    if (ku == 32) return PS_TMA_RUN(32, 4, 32);
+    return PS_TMA_RUN(32, 4, 16);
+  }
+  return PS_TMA_RUN(16, 8, 8);
+#undef PS_TMA_RUN
+}
+
+}  // namespace ps

@@ -96,6 +96,7 @@ extern "C" ps_status ps_metrics_2way_static(const ps_matrix* V, void* out, int32
   if (e != cudaSuccess) return cuda_fail(nullptr, e, "cudaGetSymbolAddress(g_static_sums)");
   ps_ctx ctx;  // stack context: no workspace is touched by the calls below
   ctx.device = dev;
+  ctx.mgemm_feed_tma = 0;  // the cp.async kernel: it needs no error word
   e = cudaDeviceGetAttribute(&ctx.num_sms, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return cuda_fail(nullptr, e, "cudaDeviceGetAttribute");
 

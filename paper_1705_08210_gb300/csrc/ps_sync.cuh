@@ -1,0 +1,105 @@
+// ps_sync.cuh -- shared-memory mbarriers, tensor-memory-accelerator (TMA)
+// tile loads and bounded waits for the warp-specialised kernels.
+//
+// Every wait here is bounded: after PS_SYNC_WAIT_NS of %globaltimer time the
+// waiter raises the CTA's abort word and a device error flag and gives up,
+// so a lost copy cannot hang the GPU.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace ps {
+namespace sy {
+
+constexpr unsigned long long PS_SYNC_WAIT_NS = 2000000000ull;  // 2 s per wait
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ unsigned long long now_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void bar_init(unsigned long long* b, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(b)), "r"(count) : "memory");
+}
+
+// Makes the initialised barriers visible to the async (TMA) proxy.
+__device__ __forceinline__ void bar_init_fence() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void bar_arrive(unsigned long long* b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(b)) : "memory");
+}
+
+// One arrival plus `bytes` of expected transaction count (the TMA copies
+// that complete the phase).
+__device__ __forceinline__ void bar_arrive_tx(unsigned long long* b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(b)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool bar_test(unsigned long long* b, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_addr(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Wait for the completion of the barrier phase with `parity`.  Returns false
+// when the CTA is aborting (abort word set by another waiter) or when this
+// wait passed the time limit (then it sets the abort word and *err).
+__device__ __forceinline__ bool bar_wait(unsigned long long* b, uint32_t parity, int* abort_word,
+                                         int* err) {
+  if (bar_test(b, parity)) return true;
+  const unsigned long long t0 = now_ns();
+  for (uint32_t it = 1;; ++it) {
+    if (bar_test(b, parity)) return true;
+    if ((it & 31) == 0) {
+      if (*(volatile int*)abort_word) return false;
+      if (now_ns() - t0 > PS_SYNC_WAIT_NS) {
+        *(volatile int*)abort_word = 1;
+        if (err) {
+          atomicExch(err, 1);
+          __threadfence_system();
+        }
+        return false;
+      }
+    }
+  }
+}
+
+// 2-D tiled TMA load of the box at element coordinates (x, y) (x innermost)
+// into shared memory; completion is signalled on barrier `b` as transaction
+// bytes.  x times the element size must be a multiple of 16 bytes.
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y,
+                                            unsigned long long* b) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, "
+      "%3}], [%4];" ::"r"(smem_addr(dst)),
+      "l"(map), "r"(x), "r"(y), "r"(smem_addr(b))
+      : "memory");
+}
+
+// After an abort: keep the CTA (and its shared memory) alive for 1 ms so
+// that copies already issued land before the memory is released.
+__device__ __forceinline__ void drain_after_abort() {
+  const unsigned long long t0 = now_ns();
+  while (now_ns() - t0 < 1000000ull) {
+  }
+}
+
+}  // namespace sy
+}  // namespace ps

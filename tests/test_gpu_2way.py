@@ -219,3 +219,40 @@ def test_u8_rejected_on_other_paths(ps, handle):
     for path in (ps.PS_PATH_FP64, ps.PS_PATH_HALF2):
         with pytest.raises(ps.PSError):
             metrics_2way(ps, handle, V, path=path, out_dtype=np.uint8)
+
+
+@pytest.mark.parametrize("nv,nf", [(129, 33), (300, 1000), (1300, 77), (700, 16)])
+def test_operand_feeds_bit_identical(ps, handle, monkeypatch, nv, nf):
+    # the TMA-fed kernel (16- and 32-field slices) and the cp.async kernel
+    # run the same micro-kernel in the same order: every output bit-identical,
+    # for FP32, FP64 and one-byte outputs, by parts, and in the 3-way n2 table
+    import torch
+    V = synth.zero_inflated(nv, nf, synth.seed_for(1, 71 + nv + nf))
+    ref = oracle.c2_packed(oracle.to_vector_major(V))
+    results = {}
+    for feed, bk in (("cpasync", "16"), ("tma", "16"), ("tma", "32"), ("tma", "64")):
+        monkeypatch.setenv("PS_MGEMM_FEED", feed)
+        monkeypatch.setenv("PS_MGEMM_TMA_BK", bk)
+        h = ps.Handle(0)
+        try:
+            r = [metrics_2way(ps, h, V), metrics_2way(ps, h, V, out_dtype=np.float64),
+                 metrics_2way(ps, h, V, out_dtype=np.uint8)]
+            X = torch.from_numpy(V).cuda()
+            m = ps.matrix(X)
+            out = torch.full((nv * (nv - 1) // 2,), float("nan"), device="cuda")
+            for p in range(3):
+                ps.check(ps.ps_metrics_2way_part(h.h, ctypes.byref(m), 3, p, out.data_ptr(), 0,
+                                                 torch.cuda.current_stream().cuda_stream), h.h)
+            torch.cuda.synchronize()
+            r.append(out.cpu().numpy())
+            if nv <= 300:
+                from gpu_run import metrics_3way
+                r.append(metrics_3way(ps, h, V))
+            results[(feed, bk)] = r
+        finally:
+            h.close()
+    assert_rel(results[("tma", "16")][0], ref, RTOL32, f"tma nv={nv} nf={nf}")
+    base = results[("cpasync", "16")]
+    for key, r in results.items():
+        for a, b in zip(r, base):
+            np.testing.assert_array_equal(a, b, err_msg=str(key))
