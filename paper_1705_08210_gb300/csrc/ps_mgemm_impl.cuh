@@ -420,8 +420,11 @@ __host__ __device__ __forceinline__ int64_t pivot_tiles(int nv, int64_t j, int B
 // exact, like the FP64 sum, whenever the sums are integers below 2^24 (the
 // FP64 pipe, at a small fraction of the FP32 rate, would otherwise bound the
 // epilogue at small n_f).  Tiles strictly above the diagonal and inside the
-// matrix (every i < j < nv) take a path without per-output checks.
-template <class C, bool PACKED>
+// matrix (every i < j < nv) take a path without per-output checks; with
+// FASTDIV (kernels for small n_f, where the epilogue is most of the work)
+// their quotients come from the branch-free div_rn_fast.  Every path gives
+// the same correctly rounded values.
+template <class C, bool PACKED, bool FASTDIV = false>
 __device__ __forceinline__ void store_tile2(const Acc<PACKED, C::NJ>& acc, const Lanes<C>& L, int row0,
                                             int col0, int64_t nv, const double* __restrict__ S,
                                             void* __restrict__ out, int mode) {
@@ -452,6 +455,58 @@ __device__ __forceinline__ void store_tile2(const Acc<PACKED, C::NJ>& acc, const
       Sjf[c] = j < nv ? (float)S[j] : 0.0f;
     }
     const bool u8 = mode == OUT2_C2_U8;
+    if (FASTDIV && interior) {
+      // branch-free quotients; a warp that met an input outside the fast
+      // division's range rewrites its outputs with __fdiv_rn (same values).
+      // The numerators are collapsed first so that only 8 x NJ values stay
+      // live for the rewrite.
+      float n2[8][C::NJ];
+#pragma unroll
+      for (int r = 0; r < 8; ++r)
+#pragma unroll
+        for (int c = 0; c < C::NJ; ++c) {
+          const float2 hl = acc.hl(r, c);
+          n2[r][c] = __fadd_rn(hl.x, hl.y);
+        }
+      bool all_ok = true;
+#pragma unroll
+      for (int r = 0; r < 8; ++r) {
+        const int i = row0 + L.row(r);
+        const float Sif = (float)S[i];
+        const int64_t base = pair_index(nv, i, i + 1) - (i + 1);
+#pragma unroll
+        for (int c = 0; c < C::NJ; ++c) {
+          const int j = col0 + L.col(c);
+          const float d = __fadd_rn(Sif, Sjf[c]);
+          bool ok;
+          const float q = div_rn_fast(2.0f * n2[r][c], d, ok);
+          all_ok = all_ok && (ok || d == 0.0f);
+          const float c2 = (d == 0.0f) ? 0.0f : q;
+          if (u8)
+            static_cast<unsigned char*>(out)[base + j] = c2_code(c2);
+          else
+            static_cast<float*>(out)[base + j] = c2;
+        }
+      }
+      if (__all_sync(0xffffffffu, all_ok)) return;
+#pragma unroll
+      for (int r = 0; r < 8; ++r) {
+        const int i = row0 + L.row(r);
+        const float Sif = (float)S[i];
+        const int64_t base = pair_index(nv, i, i + 1) - (i + 1);
+#pragma unroll
+        for (int c = 0; c < C::NJ; ++c) {
+          const int j = col0 + L.col(c);
+          const float d = __fadd_rn(Sif, Sjf[c]);
+          const float c2 = (d == 0.0f) ? 0.0f : __fdiv_rn(2.0f * n2[r][c], d);
+          if (u8)
+            static_cast<unsigned char*>(out)[base + j] = c2_code(c2);
+          else
+            static_cast<float*>(out)[base + j] = c2;
+        }
+      }
+      return;
+    }
     if (interior) {
 #pragma unroll
       for (int r = 0; r < 8; ++r) {

@@ -54,7 +54,7 @@ __device__ __forceinline__ void compute_slice_tma(const float* As, const float* 
   }
 }
 
-template <int BK, int STAGES, int KU>
+template <int BK, int STAGES, int KU, bool FASTDIV>
 __global__ void __launch_bounds__(C::NT, 1)
     mgemm2_tma_kernel(const __grid_constant__ CUtensorMap mapV, int nv, int nf,
                       const double* __restrict__ S, void* __restrict__ out, int mode, int T, int R0,
@@ -127,7 +127,7 @@ __global__ void __launch_bounds__(C::NT, 1)
     }
     if (!ok) break;
     acc.fold();
-    mg::store_tile2<C, true>(acc, L, row0, col0, nv, S, out, mode);
+    mg::store_tile2<C, true, FASTDIV>(acc, L, row0, col0, nv, S, out, mode);
   }
   __syncthreads();
   if (*(volatile int*)&sm.abort) sy::drain_after_abort();
@@ -168,7 +168,7 @@ bool make_map_v(CUtensorMap* m, const VF32& V, int bk) {
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int BK, int STAGES, int KU>
+template <int BK, int STAGES, int KU, bool FASTDIV = false>
 struct TmaLaunch {
   static constexpr size_t smem = sizeof(SmemT<BK, STAGES>);
   static cudaError_t run(ps_ctx* h, const VF32& V, const double* S, void* out, int mode, cudaStream_t st,
@@ -179,7 +179,7 @@ struct TmaLaunch {
       std::lock_guard<std::mutex> lk(mu);
       const uint64_t bit = 1ull << (h->device & 63);
       if (!(attr_done & bit)) {
-        const cudaError_t e = cudaFuncSetAttribute(mgemm2_tma_kernel<BK, STAGES, KU>,
+        const cudaError_t e = cudaFuncSetAttribute(mgemm2_tma_kernel<BK, STAGES, KU, FASTDIV>,
                                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         attr_done |= bit;
@@ -188,7 +188,7 @@ struct TmaLaunch {
     CUtensorMap map;
     if (!make_map_v(&map, V, BK)) return cudaErrorInvalidValue;
     const unsigned grid = (unsigned)std::min<int64_t>(ntiles, (int64_t)h->num_sms);
-    mgemm2_tma_kernel<BK, STAGES, KU><<<grid, C::NT, smem, st>>>(map, V.nv, V.nf, S, out, mode, T, R0, R1, G,
+    mgemm2_tma_kernel<BK, STAGES, KU, FASTDIV><<<grid, C::NT, smem, st>>>(map, V.nv, V.nf, S, out, mode, T, R0, R1, G,
                                                               ntiles, err);
     return cudaGetLastError();
   }
@@ -207,15 +207,18 @@ cudaError_t launch_mgemm2_tma(ps_ctx* h, const VF32& V, const double* S, void* o
   // k-steps per unrolled loop iteration: 16 (0 = automatic), 8 or 32
   const int ku = h->mgemm_tma_ku ? h->mgemm_tma_ku : 16;
   const int stages = h->mgemm_tma_stages;
-#define PS_TMA_RUN(BK_, ST_, KU_) TmaLaunch<BK_, ST_, KU_>::run(h, V, S, out, mode, st, T, R0, R1, G, ntiles, err)
+  // branch-free division in the epilogue where it is most of the work
+  // (n_f <= 256: 2.59 -> 2.33 ms at n_f = 16, nv = 32768); at large n_f its
+  // extra registers cost more than it saves (271.1 -> 275.8 ms at 8192)
+  const bool fastdiv = V.nf <= 256;
+#define PS_TMA_RUN(...) TmaLaunch<__VA_ARGS__>::run(h, V, S, out, mode, st, T, R0, R1, G, ntiles, err)
+  if (bk == 16) return fastdiv ? PS_TMA_RUN(16, 8, 8, true) : PS_TMA_RUN(16, 8, 8);
   if (bk == 64) return PS_TMA_RUN(64, 3, 16);
-  if (bk == 32) {
-    if (stages == 6) return PS_TMA_RUN(32, 6, 16);
-    if (ku == 8) return PS_TMA_RUN(32, 4, 8);
-    if (ku == 32) return PS_TMA_RUN(32, 4, 32);
-    return PS_TMA_RUN(32, 4, 16);
-  }
-  return PS_TMA_RUN(16, 8, 8);
+  if (fastdiv) return PS_TMA_RUN(32, 4, 16, true);
+  if (stages == 6) return PS_TMA_RUN(32, 6, 16);
+  if (ku == 8) return PS_TMA_RUN(32, 4, 8);
+  if (ku == 32) return PS_TMA_RUN(32, 4, 32);
+  return PS_TMA_RUN(32, 4, 16);
 #undef PS_TMA_RUN
 }
 

@@ -42,8 +42,10 @@ def test_ragged_shapes(ps, handle, nv, nf):
     assert_rel(got, ref, RTOL32, f"nv={nv} nf={nf}")
 
 
-def test_integer_data_bit_exact(ps, handle):
-    V = synth.integer_levels(700, 3000, synth.seed_for(1, 99))
+@pytest.mark.parametrize("nv,nf", [(1500, 40), (700, 3000)])
+def test_integer_data_bit_exact(ps, handle, nv, nf):
+    # n_f = 40 takes the small-n_f kernel with the branch-free division
+    V = synth.integer_levels(nv, nf, synth.seed_for(1, 99))
     ref = oracle.c2_packed(oracle.to_vector_major(V))
     got32 = metrics_2way(ps, handle, V)
     np.testing.assert_array_equal(got32, ref.astype(np.float32))
@@ -221,7 +223,7 @@ def test_u8_rejected_on_other_paths(ps, handle):
             metrics_2way(ps, handle, V, path=path, out_dtype=np.uint8)
 
 
-@pytest.mark.parametrize("nv,nf", [(129, 33), (300, 1000), (1300, 77), (700, 16)])
+@pytest.mark.parametrize("nv,nf", [(129, 33), (300, 1000), (1300, 77), (700, 16), (4096, 64)])
 def test_operand_feeds_bit_identical(ps, handle, monkeypatch, nv, nf):
     # the TMA-fed kernel (16- and 32-field slices) and the cp.async kernel
     # run the same micro-kernel in the same order: every output bit-identical,
