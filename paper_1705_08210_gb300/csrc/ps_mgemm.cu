@@ -130,7 +130,30 @@ cudaError_t ensure_attrs(ps_ctx* h, int code, const MgemmVariant* v) {
   return e;
 }
 
+// One block per pivot: its (I, K) tiles in row-major order.
+__global__ void __launch_bounds__(256) pivot_items_kernel(int nv, int jb, int B, const int64_t* __restrict__ pref,
+                                                          int2* __restrict__ items) {
+  const int x = blockIdx.x;
+  const int j = jb + x;
+  const int Tk = (nv + B - 1) / B;
+  const int k0t = (j + 1) / B;
+  const int nK = Tk - k0t;
+  const int64_t n = pref[x + 1] - pref[x];
+  for (int64_t u = threadIdx.x; u < n; u += blockDim.x) {
+    const int I = (int)(u / nK), K = k0t + (int)(u % nK);
+    items[pref[x] + u] = make_int2(j, (I << 16) | K);
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_pivot_items(int nv, int jb, int npiv, int B, const int64_t* pref, int2* items,
+                               cudaStream_t st) {
+  if (npiv <= 0) return cudaSuccess;
+  if (ceil_div(nv, B) >= 65536) return cudaErrorInvalidValue;  // (I, K) packed in 16 bits each
+  pivot_items_kernel<<<npiv, 256, 0, st>>>(nv, jb, B, pref, items);
+  return cudaGetLastError();
+}
 
 const MgemmVariant* mgemm_variant_of(int code) {
   const int shape = code / 1000, packed = (code / 100) % 10, ku = code % 100;
@@ -219,13 +242,27 @@ int64_t pivot_tile_count(int nv, int64_t jb, int64_t je, int B) {
 
 cudaError_t launch_mgemm3(ps_ctx* h, const VF32& V, const double* S, const float* n2sq,
                           int64_t jb, int64_t je, float* out, cudaStream_t st) {
+  const int nv = V.nv;
+  const int npiv = (int)(je - jb);
+  if (npiv <= 0) return cudaSuccess;
+  if (h->mgemm3_feed_tma && V.nf > 0) {
+    const int64_t ntiles = pivot_tile_count(nv, jb, je, 128);
+    if (ntiles == 0) return cudaSuccess;
+    int64_t* dpref = static_cast<int64_t*>(ws_get(h, WS_AUX0, (npiv + 1) * sizeof(int64_t)));
+    int2* items = static_cast<int2*>(ws_get(h, WS_ITEMS, (size_t)ntiles * sizeof(int2)));
+    int* err = async_err_word(h);
+    if (!dpref || !items || !err) return cudaErrorMemoryAllocation;
+    pivot_prefix_kernel<<<1, 1024, 0, st>>>(nv, (int)jb, npiv, 128, dpref);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    e = launch_pivot_items(nv, (int)jb, npiv, 128, dpref, items, st);
+    if (e != cudaSuccess) return e;
+    return launch_mgemm3_tma(h, V, S, n2sq, items, (int)jb, out, ntiles, err, st);
+  }
   const int code = mgemm_variant_code(h);
   const MgemmVariant* v = mgemm_variant_of(code);
   cudaError_t e = ensure_attrs(h, code, v);
   if (e != cudaSuccess) return e;
-  const int nv = V.nv;
-  const int npiv = (int)(je - jb);
-  if (npiv <= 0) return cudaSuccess;
   const int64_t ntiles = pivot_tile_count(nv, jb, je, v->tile);
   if (ntiles == 0) return cudaSuccess;
   int64_t* dpref = static_cast<int64_t*>(ws_get(h, WS_AUX0, (npiv + 1) * sizeof(int64_t)));

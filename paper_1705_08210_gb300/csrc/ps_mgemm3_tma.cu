@@ -1,0 +1,279 @@
+// ps_mgemm3_tma.cu -- the 3-way pivot-min product of Section 3.2 fed by the
+// tensor memory accelerator.
+//
+// Work item = (pivot j, row tile I, column tile K) with rows i < j and
+// columns k > j (only the part of B_j = X_j^T (min) V that holds i < j < k),
+// the cp.async kernel's (mgemm3_kernel) walk, read from a table written
+// before the launch (one load per tile, fetched a tile ahead).  Per BK-field
+// slice, lane 0 of warp 0 issues three TMA loads into an mbarrier-guarded
+// ring: the 128-vector row panel, the 128-vector column panel, and a
+// 4-vector box holding the pivot column v_j.  X_j = min(V, v_j) is never
+// stored: when a slice lands each warp min-s two of its field rows of the
+// row panel with the pivot value, arrives on the slice's `ready` barrier and
+// waits for the other warps' rows (a bounded mbarrier wait, not a CTA
+// barrier), then runs the 2-way micro-kernel (8 x 4 outputs per lane, FP32
+// min + packed FP32 add, TwoSum fold every 64 fields) on it.
+//
+// Warp placement.  A warp owns a 64-row x 16-column block.  The tile that
+// straddles the pivot has rows i >= j (past the pivot's rectangle) and
+// columns k <= j (before it); warps whose whole block lies outside skip the
+// min-add loop.  A skipped warp only helps if another warp on the same
+// scheduler (warps w, w+4, w+8, w+12 share one) takes the pipe, so warps
+// are placed on blocks so that every scheduler holds two row halves and its
+// four blocks spread across the column groups: warp w = 4g + s (scheduler
+// s) takes block e = (s + g) mod 4 of column group g (columns 32g..32g+31):
+// row half e & 1, column half e >> 1.  Then skipping the lower row half, or
+// any whole number of 32-column groups at the left edge, removes the same
+// number of blocks from every scheduler.
+#include "ps_mgemm_impl.cuh"
+#include "ps_sync.cuh"
+
+#include <algorithm>
+#include <mutex>
+
+namespace ps {
+namespace {
+
+using C = mg::T128W16;  // 128 x 128 tile, 16 warps, 8 x 4 outputs per lane
+constexpr int NW = C::NT / 32;
+constexpr int PBOX = 4;  // pivot box: 4 vectors (16 bytes) x BK fields
+
+// Thread -> output coordinates (same interface as mg::Lanes).
+struct Lanes3 {
+  int am, bn;  // smem column offsets of the A / B fragments
+  int wrow0, wcol0;  // first row / column of this warp's 64 x 16 block
+  __device__ __forceinline__ Lanes3() {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int g = warp >> 2, s = warp & 3, e = (s + g) & 3;
+    const int wm = e & 1, wn = 2 * g + (e >> 1);
+    wrow0 = wm * 64;
+    wcol0 = wn * 16;
+    am = wrow0 + (lane >> 2) * 4;
+    bn = wcol0 + (lane & 3) * 4;
+  }
+  __device__ __forceinline__ int row(int r) const { return am + (r < 4 ? r : 28 + r); }
+  __device__ __forceinline__ int col(int c) const { return bn + c; }
+};
+
+template <int BK, int STAGES>
+struct __align__(128) Smem3 {
+  float A[STAGES][BK][C::BM];  // row panel (min-ed with the pivot in place)
+  float B[STAGES][BK][C::BN];  // column panel
+  float P[STAGES][BK][PBOX];   // pivot column: v_j at [kk][j % 4]
+  int pcol[STAGES];            // j % 4 of the slice's pivot (written by the producer)
+  int2 pitem;                  // the producer's current work item
+  unsigned long long full[STAGES];
+  unsigned long long ready[STAGES];
+  unsigned long long empty[STAGES];
+  int abort;
+};
+
+// BK k-steps of the micro-kernel on one prepared slice.
+template <int BK, int KU>
+__device__ __forceinline__ void compute_slice3(const float* As, const float* Bs, mg::Acc<true, C::NJ>& acc) {
+#pragma unroll KU
+  for (int kk = 0; kk < BK; ++kk) {
+    const float4 a0 = *reinterpret_cast<const float4*>(As + kk * C::BM);
+    const float4 a1 = *reinterpret_cast<const float4*>(As + kk * C::BM + 32);
+    const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+    const float4 b0 = *reinterpret_cast<const float4*>(Bs + kk * C::BN);
+    const float b[4] = {b0.x, b0.y, b0.z, b0.w};
+    acc.step(a, b);
+  }
+}
+
+// Work item {j, (I << 16) | K} -> pivot j and tile origin (row0, col0).
+__device__ __forceinline__ void item3(int2 w, int& j, int& row0, int& col0) {
+  j = w.x;
+  row0 = (w.y >> 16) * C::BM;
+  col0 = (w.y & 0xffff) * C::BN;
+}
+
+template <int BK, int STAGES, int KU>
+__global__ void __launch_bounds__(C::NT, 1)
+    mgemm3_tma_kernel(const __grid_constant__ CUtensorMap mapV, const __grid_constant__ CUtensorMap mapP,
+                      int nv, int nf, const double* __restrict__ S, const float* __restrict__ n2sq,
+                      const int2* __restrict__ items, int jb, float* __restrict__ out, int64_t ntiles,
+                      int* err) {
+  static_assert(mg::FOLD * mg::BK % BK == 0 && BK % NW == 0, "slice shape");
+  constexpr int FOLD_SLICES = mg::FOLD * mg::BK / BK;
+  constexpr int ROWS_PER_WARP = BK / NW;  // field rows of a slice each warp min-s with the pivot
+  constexpr uint32_t SLICE_BYTES = (2u * BK * C::BM + BK * PBOX) * sizeof(float);
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  Smem3<BK, STAGES>& sm = *reinterpret_cast<Smem3<BK, STAGES>*>(smem_raw);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      sy::bar_init(&sm.full[s], 1);
+      sy::bar_init(&sm.ready[s], NW);
+      sy::bar_init(&sm.empty[s], NW);
+    }
+    sm.abort = 0;
+    sy::bar_init_fence();
+  }
+  __syncthreads();
+  const int nkb = (nf + BK - 1) / BK;
+  const int64_t my_tiles = ntiles > blockIdx.x ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  const uint32_t n_slices = (uint32_t)(my_tiles * nkb);  // < 2^32 (checked by the launcher)
+
+  // producer (lane 0 of warp 0): loads slice g (waiting until its ring
+  // stage is free); false on abort.  Its work item is kept in shared memory
+  // (registers are the micro-kernel's).
+  const bool producer = threadIdx.x == 0;
+  auto issue_one = [&](uint32_t g) -> bool {
+    Smem3<BK, STAGES>& sm = *reinterpret_cast<Smem3<BK, STAGES>*>(smem_raw);
+    if (g >= n_slices) return true;
+    const int s = (int)(g % STAGES);
+    const uint32_t ph = (g / STAGES) & 1u;
+    const int kb = (int)(g % (uint32_t)nkb);
+    if (kb == 0) sm.pitem = items[blockIdx.x + (int64_t)(g / nkb) * gridDim.x];
+    int pj, prow0, pcol0;
+    item3(sm.pitem, pj, prow0, pcol0);
+    if (!sy::bar_wait(&sm.empty[s], ph ^ 1u, &sm.abort, err)) return false;
+    sm.pcol[s] = pj & (PBOX - 1);  // published by the arrival below
+    sy::bar_arrive_tx(&sm.full[s], SLICE_BYTES);
+    sy::tma_load_2d(&sm.A[s][0][0], &mapV, prow0, kb * BK, &sm.full[s]);
+    sy::tma_load_2d(&sm.B[s][0][0], &mapV, pcol0, kb * BK, &sm.full[s]);
+    sy::tma_load_2d(&sm.P[s][0][0], &mapP, pj & ~(PBOX - 1), kb * BK, &sm.full[s]);
+    return true;
+  };
+  if (producer)
+    for (uint32_t g = 0; g + 1 < STAGES; ++g)
+      if (!issue_one(g)) break;
+
+  // X_j = min(V, v_j) on this warp's field rows of slice g's row panel,
+  // then one arrival on the slice's `ready` barrier; false on abort
+  auto prepare = [&](uint32_t g) -> bool {
+    // (the shared array itself, not the captured reference: through the
+    // capture the compiler would emit generic loads and stores)
+    Smem3<BK, STAGES>& sm = *reinterpret_cast<Smem3<BK, STAGES>*>(smem_raw);
+    const int s = (int)(g % STAGES);
+    const uint32_t ph = (g / STAGES) & 1u;
+    const bool landed = sy::bar_wait(&sm.full[s], ph, &sm.abort, err);
+    if (!__all_sync(0xffffffffu, landed)) return false;
+    const int pc = sm.pcol[s];
+#pragma unroll
+    for (int rr = 0; rr < ROWS_PER_WARP; ++rr) {
+      const int kk = warp * ROWS_PER_WARP + rr;
+      const float p = sm.P[s][kk][pc];
+      float4* a = reinterpret_cast<float4*>(&sm.A[s][kk][lane * 4]);
+      float4 v = *a;
+      v.x = fminf(v.x, p);
+      v.y = fminf(v.y, p);
+      v.z = fminf(v.z, p);
+      v.w = fminf(v.w, p);
+      *a = v;
+    }
+    // the TMA refill of this stage comes later through the async proxy
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncwarp();
+    if (lane == 0) sy::bar_arrive(&sm.ready[s]);
+    return true;
+  };
+
+  const Lanes3 L;
+  mg::Acc<true, C::NJ> acc;
+  uint32_t it = 0;
+  // slices are prepared one ahead of the compute, so that a warp waiting for
+  // the other warps' rows of slice it waited a whole slice earlier
+  bool ok = n_slices == 0 || prepare(0);
+  for (int64_t t = blockIdx.x; ok && t < ntiles; t += gridDim.x) {
+    int j, row0, col0;
+    item3(items[t], j, row0, col0);
+    // a warp whose 64 x 16 block has no row i < j, no column k > j, or no
+    // column inside the matrix has no output here and skips the min-adds
+    const bool active = row0 + L.wrow0 < j && col0 + L.wcol0 + 15 > j && col0 + L.wcol0 < nv;
+    acc.zero();
+    for (int kb = 0; kb < nkb; ++kb, ++it) {
+      // slice it + STAGES - 1 (its stage was released by every warp after
+      // slice it - 1, which none of them needs this warp for)
+      if (producer) ok = issue_one(it + STAGES - 1);
+      ok = __all_sync(0xffffffffu, ok);
+      if (ok && it + 1 < n_slices) ok = prepare(it + 1);
+      if (!ok) break;
+      const int s = (int)(it % STAGES);
+      const uint32_t ph = (it / STAGES) & 1u;
+      const bool prepared = sy::bar_wait(&sm.ready[s], ph, &sm.abort, err);
+      if (!__all_sync(0xffffffffu, prepared)) { ok = false; break; }
+      if (active) compute_slice3<BK, KU>(&sm.A[s][0][L.am], &sm.B[s][0][L.bn], acc);
+      __syncwarp();
+      if (lane == 0) sy::bar_arrive(&sm.empty[s]);
+      if ((kb + 1) % FOLD_SLICES == 0) acc.fold();
+    }
+    if (!ok) break;
+    acc.fold();
+    // Section 2.2 eq. (1) into pivot j's slab block (rows i < j, columns k > j)
+    const int64_t w = nv - 1 - j;
+    const int64_t base = mg::slab_offset(nv, jb, j);
+    const float Sj = (float)S[j];
+    float Skf[C::NJ];
+#pragma unroll
+    for (int c = 0; c < C::NJ; ++c) {
+      const int k = col0 + L.col(c);
+      Skf[c] = k < nv ? (float)S[k] : 0.0f;
+    }
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      const int i = row0 + L.row(r);
+      if (i >= j) continue;
+      const float Sij = __fadd_rn((float)S[i], Sj);
+      const float n2ij = n2sq[(int64_t)i * nv + j];
+#pragma unroll
+      for (int c = 0; c < C::NJ; ++c) {
+        const int k = col0 + L.col(c);
+        if (k <= j || k >= nv) continue;
+        out[base + (int64_t)i * w + (k - j - 1)] =
+            mg::c3_value(acc.hl(r, c), n2ij, n2sq[(int64_t)i * nv + k], n2sq[(int64_t)j * nv + k],
+                         __fadd_rn(Sij, Skf[c]));
+      }
+    }
+  }
+  __syncthreads();
+  if (*(volatile int*)&sm.abort) sy::drain_after_abort();
+}
+
+// ---- host side ----
+template <int BK, int STAGES, int KU>
+struct Tma3Launch {
+  static constexpr size_t smem = sizeof(Smem3<BK, STAGES>);
+  static cudaError_t run(ps_ctx* h, const VF32& V, const double* S, const float* n2sq, const int2* items, int jb,
+                         float* out, int64_t ntiles, int* err, cudaStream_t st) {
+    static std::mutex mu;
+    static uint64_t attr_done = 0;
+    {
+      std::lock_guard<std::mutex> lk(mu);
+      const uint64_t bit = 1ull << (h->device & 63);
+      if (!(attr_done & bit)) {
+        const cudaError_t e = cudaFuncSetAttribute(mgemm3_tma_kernel<BK, STAGES, KU>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr_done |= bit;
+      }
+    }
+    CUtensorMap mapV, mapP;
+    if (!sy::make_map_f32(&mapV, V.p, V.nv, V.nf, V.ld, C::BM, BK) ||
+        !sy::make_map_f32(&mapP, V.p, V.nv, V.nf, V.ld, PBOX, BK))
+      return cudaErrorInvalidValue;
+    const unsigned grid = (unsigned)std::min<int64_t>(ntiles, (int64_t)h->num_sms);
+    mgemm3_tma_kernel<BK, STAGES, KU><<<grid, C::NT, smem, st>>>(mapV, mapP, V.nv, V.nf, S, n2sq, items, jb,
+                                                                 out, ntiles, err);
+    return cudaGetLastError();
+  }
+};
+
+}  // namespace
+
+cudaError_t launch_mgemm3_tma(ps_ctx* h, const VF32& V, const double* S, const float* n2sq, const int2* items,
+                              int jb, float* out, int64_t ntiles, int* err, cudaStream_t st) {
+  // TMA: 16-byte aligned base and row pitch; 128-wide tiles
+  if ((uintptr_t)V.p % 16 != 0 || V.ld % 4 != 0 || V.nv < 1) return cudaErrorInvalidValue;
+  // slices per CTA counted in 32 bits
+  if ((double)ceil_div(ntiles, h->num_sms) * (double)ceil_div(V.nf, 16) >= 4294967295.0)
+    return cudaErrorInvalidValue;
+  if (V.nf <= 16) return Tma3Launch<16, 8, 8>::run(h, V, S, n2sq, items, jb, out, ntiles, err, st);
+  // 16 k-steps per unrolled iteration: 457.8 ms vs 463.5 with 8 at 2048 x 4096
+  if (h->mgemm_tma_ku == 8) return Tma3Launch<32, 4, 8>::run(h, V, S, n2sq, items, jb, out, ntiles, err, st);
+  return Tma3Launch<32, 4, 16>::run(h, V, S, n2sq, items, jb, out, ntiles, err, st);
+}
+
+}  // namespace ps

@@ -134,40 +134,6 @@ __global__ void __launch_bounds__(C::NT, 1)
 }
 
 // ---- host side ----
-using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
-                                   const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
-                                   const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
-                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-EncodeTiledFn encode_fn() {
-  static EncodeTiledFn fn = nullptr;
-  static std::once_flag once;
-  std::call_once(once, [] {
-    void* p = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
-            cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<EncodeTiledFn>(p);
-    cudaGetLastError();
-  });
-  return fn;
-}
-
-// V as a 2-D FP32 tensor: x = vector index (contiguous, nv), y = field (nf,
-// ld floats apart); box 128 vectors x BK fields, zero fill outside.
-bool make_map_v(CUtensorMap* m, const VF32& V, int bk) {
-  EncodeTiledFn enc = encode_fn();
-  if (!enc) return false;
-  const cuuint64_t dims[2] = {(cuuint64_t)V.nv, (cuuint64_t)std::max(V.nf, 1)};
-  const cuuint64_t strides[1] = {(cuuint64_t)V.ld * sizeof(float)};
-  const cuuint32_t box[2] = {(cuuint32_t)C::BM, (cuuint32_t)bk};
-  const cuuint32_t estr[2] = {1, 1};
-  return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(V.p), dims, strides, box, estr,
-             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
-}
-
 template <int BK, int STAGES, int KU, bool FASTDIV = false>
 struct TmaLaunch {
   static constexpr size_t smem = sizeof(SmemT<BK, STAGES>);
@@ -186,7 +152,7 @@ struct TmaLaunch {
       }
     }
     CUtensorMap map;
-    if (!make_map_v(&map, V, BK)) return cudaErrorInvalidValue;
+    if (!sy::make_map_f32(&map, V.p, V.nv, V.nf, V.ld, C::BM, BK)) return cudaErrorInvalidValue;
     const unsigned grid = (unsigned)std::min<int64_t>(ntiles, (int64_t)h->num_sms);
     mgemm2_tma_kernel<BK, STAGES, KU, FASTDIV><<<grid, C::NT, smem, st>>>(map, V.nv, V.nf, S, out, mode, T, R0, R1, G,
                                                               ntiles, err);

@@ -101,5 +101,43 @@ __device__ __forceinline__ void drain_after_abort() {
   }
 }
 
+// ---- host: 2-D FP32 tensor maps through the driver entry point ----
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                   const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                   const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+inline EncodeTiledFn encode_tiled_fn() {
+  static EncodeTiledFn fn = [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    EncodeTiledFn f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      f = reinterpret_cast<EncodeTiledFn>(p);
+    cudaGetLastError();
+    return f;
+  }();
+  return fn;
+}
+
+// Field-major FP32 matrix (element (i, q) at p[i + q ld]) as a 2-D tensor:
+// x = vector index (nv, contiguous), y = field (nf rows, ld floats apart);
+// box box_x vectors x box_y fields, zero fill outside the matrix.  Needs p
+// 16-byte aligned and ld % 4 == 0; box_x * 4 bytes a multiple of 16.
+inline bool make_map_f32(CUtensorMap* m, const float* p, int64_t nv, int64_t nf, int64_t ld, int box_x,
+                         int box_y) {
+  EncodeTiledFn enc = encode_tiled_fn();
+  if (!enc || nv < 1) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)nv, (cuuint64_t)(nf > 0 ? nf : 1)};
+  const cuuint64_t strides[1] = {(cuuint64_t)ld * sizeof(float)};
+  const cuuint32_t box[2] = {(cuuint32_t)box_x, (cuuint32_t)box_y};
+  const cuuint32_t estr[2] = {1, 1};
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(p), dims, strides, box, estr,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 }  // namespace sy
 }  // namespace ps

@@ -60,3 +60,28 @@ def test_config3_full_size_sampled(ps, handle):
     print(f"config3 sampled max rel err {err:.3e}")
     del got_all
     torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("nv,nf", [(129, 16), (300, 70), (517, 200)])
+def test_operand_feeds_bit_identical(ps, handle, monkeypatch, nv, nf):
+    # the TMA-fed kernel (pivot min applied per slice in shared memory, warps
+    # skipping blocks outside the pivot's rectangle) and the cp.async kernels
+    # (8 and 16 warps) sum every triple in the same order: bit-identical
+    # slabs, whole and by pivot ranges
+    V = synth.zero_inflated(nv, nf, synth.seed_for(3, 81 + nv + nf))
+    res = {}
+    for feed, warps in (("cpasync", "8"), ("cpasync", "16"), ("tma", "0")):
+        monkeypatch.setenv("PS_MGEMM3_FEED", feed)
+        monkeypatch.setenv("PS_MGEMM_WARPS", warps)
+        h = ps.Handle(0)
+        try:
+            res[feed + warps] = [metrics_3way(ps, h, V),
+                                 np.concatenate([metrics_3way(ps, h, V, a, b)
+                                                 for a, b in [(0, 5), (5, min(130, nv)), (min(130, nv), nv)]])]
+        finally:
+            h.close()
+    ref = oracle.c3_slab(oracle.to_vector_major(V), 0, nv)
+    assert_rel(res["tma0"][0], ref, RTOL32, f"tma nv={nv} nf={nf}")
+    for key, r in res.items():
+        np.testing.assert_array_equal(r[0], res["cpasync8"][0], err_msg=key)
+        np.testing.assert_array_equal(r[1], res["cpasync8"][0], err_msg=key + " pivot ranges")
