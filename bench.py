@@ -123,8 +123,8 @@ class ClockSampler:
 # kernel's sources hash to the value recorded with the capture.
 TRAFFIC = {
     "mgemm2": ("profiles/mgemm2_2way_32768x8192_dram.md",
-               ["paper_1705_08210_gb300/csrc/ps_mgemm_impl.cuh", "paper_1705_08210_gb300/csrc/ps_mgemm_t128.cu",
-                "paper_1705_08210_gb300/csrc/ps_mgemm.cu"]),
+               ["paper_1705_08210_gb300/csrc/ps_mgemm_impl.cuh", "paper_1705_08210_gb300/csrc/ps_mgemm_tma.cu",
+                "paper_1705_08210_gb300/csrc/ps_sync.cuh"]),
     "thermo_gemm": ("profiles/thermo_gemm_2way_32768x8192_dram.md", ["paper_1705_08210_gb300/csrc/ps_thermo.cu"]),
 }
 

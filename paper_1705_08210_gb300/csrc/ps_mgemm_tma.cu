@@ -58,7 +58,7 @@ template <int BK, int STAGES, int KU, bool FASTDIV>
 __global__ void __launch_bounds__(C::NT, 1)
     mgemm2_tma_kernel(const __grid_constant__ CUtensorMap mapV, int nv, int nf,
                       const double* __restrict__ S, void* __restrict__ out, int mode, int T, int R0,
-                      int R1, int G, int64_t ntiles, int* err) {
+                      int R1, int G, int64_t ntiles, int* err, unsigned* __restrict__ sync, int sync_sl) {
   static_assert(mg::FOLD * mg::BK % BK == 0, "a fold boundary ends a slice");
   constexpr int FOLD_SLICES = mg::FOLD * mg::BK / BK;  // 64 fields per compensated fold
   constexpr uint32_t SLICE_BYTES = 2u * BK * C::BM * sizeof(float);
@@ -86,16 +86,32 @@ __global__ void __launch_bounds__(C::NT, 1)
   uint64_t g_next = 0;
   int pI = 0, pJ = 0;
   // loads slice g_next (waiting until its ring stage is free); false on abort
+  // With sync_sl > 0 the producers of all CTAs (co-resident: cooperative
+  // launch) meet at the grid-wide counter every sync_sl slices: a producer
+  // does not load chunk c of its round-r tile before every CTA has loaded all
+  // earlier chunks.  Without it the CTAs drift apart over the ~200 rounds of
+  // tiles at nv = 32768, the tiles that share a row or column panel stop
+  // meeting in L2, and the panels are re-read from DRAM.
+  const int cpt = sync_sl > 0 ? (nkb + sync_sl - 1) / sync_sl : 0;  // chunks per tile
   auto issue_one = [&]() -> bool {
+    SmemT<BK, STAGES>& sm = *reinterpret_cast<SmemT<BK, STAGES>*>(smem_raw);
     if (g_next >= n_slices) return true;
     const int s = (int)(g_next % STAGES);
     const uint32_t ph = (uint32_t)(g_next / STAGES) & 1u;
     const int kb = (int)(g_next % (uint64_t)nkb);
-    if (kb == 0) mg::band_tile(blockIdx.x + (int64_t)(g_next / nkb) * gridDim.x, T, R0, R1, G, pI, pJ);
+    const int64_t r = (int64_t)(g_next / nkb);  // round: this CTA's r-th tile
+    if (kb == 0) mg::band_tile(blockIdx.x + r * gridDim.x, T, R0, R1, G, pI, pJ);
+    if (cpt && kb % sync_sl == 0 && (r | kb) != 0) {
+      // CTAs holding a tile in round r, and the chunks issued before this one
+      const int64_t P = min((int64_t)gridDim.x, ntiles - r * (int64_t)gridDim.x);
+      const unsigned need = (unsigned)(r * cpt * gridDim.x + (int64_t)(kb / sync_sl) * P);
+      if (!sy::counter_wait(sync, need, &sm.abort, err)) return false;
+    }
     if (!sy::bar_wait(&sm.empty[s], ph ^ 1u, &sm.abort, err)) return false;
     sy::bar_arrive_tx(&sm.full[s], SLICE_BYTES);
     sy::tma_load_2d(&sm.A[s][0][0], &mapV, pI * C::BM, kb * BK, &sm.full[s]);
     sy::tma_load_2d(&sm.B[s][0][0], &mapV, pJ * C::BN, kb * BK, &sm.full[s]);
+    if (cpt && ((kb + 1) % sync_sl == 0 || kb + 1 == nkb)) atomicAdd(sync, 1u);
     ++g_next;
     return true;
   };
@@ -138,7 +154,7 @@ template <int BK, int STAGES, int KU, bool FASTDIV = false>
 struct TmaLaunch {
   static constexpr size_t smem = sizeof(SmemT<BK, STAGES>);
   static cudaError_t run(ps_ctx* h, const VF32& V, const double* S, void* out, int mode, cudaStream_t st,
-                         int T, int R0, int R1, int G, int64_t ntiles, int* err) {
+                         int T, int R0, int R1, int G, int64_t ntiles, int* err, unsigned* sync) {
     static std::mutex mu;
     static uint64_t attr_done = 0;
     {
@@ -154,9 +170,24 @@ struct TmaLaunch {
     CUtensorMap map;
     if (!sy::make_map_f32(&map, V.p, V.nv, V.nf, V.ld, C::BM, BK)) return cudaErrorInvalidValue;
     const unsigned grid = (unsigned)std::min<int64_t>(ntiles, (int64_t)h->num_sms);
-    mgemm2_tma_kernel<BK, STAGES, KU, FASTDIV><<<grid, C::NT, smem, st>>>(map, V.nv, V.nf, S, out, mode, T, R0, R1, G,
-                                                              ntiles, err);
-    return cudaGetLastError();
+    // producers meet only when there is more than one round of tiles
+    const int sync_sl = (ntiles > (int64_t)grid && h->mgemm_tma_sync > 0) ? h->mgemm_tma_sync : 0;
+    if (sync_sl) {
+      const cudaError_t e = cudaMemsetAsync(sync, 0, sizeof(unsigned), st);
+      if (e != cudaSuccess) return e;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(C::NT);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;  // all CTAs resident: the meetings always end
+    attr[0].val.cooperative = sync_sl ? 1 : 0;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, mgemm2_tma_kernel<BK, STAGES, KU, FASTDIV>, map, (int)V.nv, (int)V.nf, S, out,
+                              mode, T, R0, R1, G, ntiles, err, sync, sync_sl);
   }
 };
 
@@ -166,6 +197,8 @@ cudaError_t launch_mgemm2_tma(ps_ctx* h, const VF32& V, const double* S, void* o
                               int T, int R0, int R1, int G, int64_t ntiles, int* err) {
   // TMA: 16-byte aligned base and row pitch; the tile walk assumes 128-wide tiles
   if ((uintptr_t)V.p % 16 != 0 || V.ld % 4 != 0 || V.nv < 1) return cudaErrorInvalidValue;
+  unsigned* sync = static_cast<unsigned*>(ws_get(h, WS_SYNC, 256));
+  if (!sync) return cudaErrorMemoryAllocation;
   // slice width: 16 fields up to n_f = 32 (wider slices would be mostly zero
   // fill), else the configured width (32 by default: fewer waits and
   // releases per comparison)
@@ -177,7 +210,7 @@ cudaError_t launch_mgemm2_tma(ps_ctx* h, const VF32& V, const double* S, void* o
   // (n_f <= 256: 2.59 -> 2.33 ms at n_f = 16, nv = 32768); at large n_f its
   // extra registers cost more than it saves (271.1 -> 275.8 ms at 8192)
   const bool fastdiv = V.nf <= 256;
-#define PS_TMA_RUN(...) TmaLaunch<__VA_ARGS__>::run(h, V, S, out, mode, st, T, R0, R1, G, ntiles, err)
+#define PS_TMA_RUN(...) TmaLaunch<__VA_ARGS__>::run(h, V, S, out, mode, st, T, R0, R1, G, ntiles, err, sync)
   if (bk == 16) return fastdiv ? PS_TMA_RUN(16, 8, 8, true) : PS_TMA_RUN(16, 8, 8);
   if (bk == 64) return PS_TMA_RUN(64, 3, 16);
   if (fastdiv) return PS_TMA_RUN(32, 4, 16, true);

@@ -81,6 +81,33 @@ __device__ __forceinline__ bool bar_wait(unsigned long long* b, uint32_t parity,
   }
 }
 
+// Wait until the grid-wide counter *c reaches `need` (relaxed loads: the
+// counter only paces the producers, it guards no data).  False when the CTA
+// is aborting or the time limit passed (then it sets the abort word and
+// *err).
+__device__ __forceinline__ bool counter_wait(const unsigned* c, unsigned need, int* abort_word, int* err) {
+  auto load = [c]() {
+    unsigned v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(c) : "memory");
+    return v;
+  };
+  if (load() >= need) return true;
+  const unsigned long long t0 = now_ns();
+  for (;;) {
+    __nanosleep(64);
+    if (load() >= need) return true;
+    if (*(volatile int*)abort_word) return false;
+    if (now_ns() - t0 > PS_SYNC_WAIT_NS) {
+      *(volatile int*)abort_word = 1;
+      if (err) {
+        atomicExch(err, 1);
+        __threadfence_system();
+      }
+      return false;
+    }
+  }
+}
+
 // 2-D tiled TMA load of the box at element coordinates (x, y) (x innermost)
 // into shared memory; completion is signalled on barrier `b` as transaction
 // bytes.  x times the element size must be a multiple of 16 bytes.
@@ -135,7 +162,8 @@ inline bool make_map_f32(CUtensorMap* m, const float* p, int64_t nv, int64_t nf,
   const cuuint32_t box[2] = {(cuuint32_t)box_x, (cuuint32_t)box_y};
   const cuuint32_t estr[2] = {1, 1};
   return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(p), dims, strides, box, estr,
-             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 

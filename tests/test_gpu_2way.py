@@ -258,3 +258,28 @@ def test_operand_feeds_bit_identical(ps, handle, monkeypatch, nv, nf):
     for key, r in results.items():
         for a, b in zip(r, base):
             np.testing.assert_array_equal(a, b, err_msg=str(key))
+
+
+def test_tma_producer_meetings(ps, handle, monkeypatch):
+    # the TMA producers' grid-wide meetings (cooperative launch; off by
+    # default) change no value: 210 tiles over 152 CTAs (two rounds, the
+    # second partial), meetings every 2 slices, whole matrix and row bands
+    import torch
+    nv, nf = 2560, 200
+    V = synth.zero_inflated(nv, nf, synth.seed_for(1, 91))
+    base = metrics_2way(ps, handle, V)
+    monkeypatch.setenv("PS_MGEMM_TMA_SYNC", "2")
+    h = ps.Handle(0)
+    try:
+        np.testing.assert_array_equal(metrics_2way(ps, h, V), base)
+        np.testing.assert_array_equal(metrics_2way(ps, h, V, on_host=True), base)
+        X = torch.from_numpy(V).cuda()
+        m = ps.matrix(X)
+        out = torch.full((nv * (nv - 1) // 2,), float("nan"), device="cuda")
+        for p in range(3):
+            ps.check(ps.ps_metrics_2way_part(h.h, ctypes.byref(m), 3, p, out.data_ptr(), 0,
+                                             torch.cuda.current_stream().cuda_stream), h.h)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(out.cpu().numpy(), base)
+    finally:
+        h.close()
