@@ -44,7 +44,13 @@
  * Errors.  Every entry point returns a ps_status.  Argument errors are
  *   detected before any launch and leave outputs untouched.  CUDA errors are
  *   reported as PS_ERR_CUDA; ps_last_error() gives the message.  No
- *   exception, abort or exit crosses this boundary.
+ *   exception, abort or exit crosses this boundary.  Every wait inside a
+ *   kernel is bounded (2 s); a TMA-fed min-product kernel whose pipeline
+ *   wait timed out raises a word in the handle's mapped host memory and
+ *   returns, leaving that call's output incomplete: the call reports
+ *   PS_ERR_TIMEOUT itself when it synchronises (host buffers), otherwise the
+ *   next ps_metrics_2way / ps_metrics_2way_part / ps_metrics_3way /
+ *   ps_threshold_3way call on the handle does, once.
  *
  * Threads.  A handle may be used by one host thread at a time.  Calls that
  *   overlap on the GPU (different streams, same handle) race on the handle's
