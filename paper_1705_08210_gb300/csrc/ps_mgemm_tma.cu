@@ -36,6 +36,11 @@ struct __align__(128) SmemT {
   float B[STAGES][BK][C::BN];
   unsigned long long full[STAGES];
   unsigned long long empty[STAGES];
+  int tile_of[STAGES];  // dynamic schedule: tile of local tile lt at [lt % STAGES], -1 = none
+  // producer state (thread 0 only; kept here to leave registers to the
+  // micro-kernel): next slice to load, schedule exhausted, its tile
+  uint32_t p_next;
+  int p_done, pI, pJ;
   int abort;
 };
 
@@ -54,11 +59,12 @@ __device__ __forceinline__ void compute_slice_tma(const float* As, const float* 
   }
 }
 
-template <int BK, int STAGES, int KU, bool FASTDIV>
+template <int BK, int STAGES, int KU, bool FASTDIV, bool DYN>
 __global__ void __launch_bounds__(C::NT, 1)
     mgemm2_tma_kernel(const __grid_constant__ CUtensorMap mapV, int nv, int nf,
                       const double* __restrict__ S, void* __restrict__ out, int mode, int T, int R0,
-                      int R1, int G, int64_t ntiles, int* err, unsigned* __restrict__ sync, int sync_sl) {
+                      int R1, int G, int64_t ntiles, int* err, unsigned* __restrict__ sync, int sync_sl,
+                      unsigned long long* __restrict__ tile_ctr) {
   static_assert(mg::FOLD * mg::BK % BK == 0, "a fold boundary ends a slice");
   constexpr int FOLD_SLICES = mg::FOLD * mg::BK / BK;  // 64 fields per compensated fold
   constexpr uint32_t SLICE_BYTES = 2u * BK * C::BM * sizeof(float);
@@ -73,46 +79,75 @@ __global__ void __launch_bounds__(C::NT, 1)
       sy::bar_init(&sm.empty[s], NW);
     }
     sm.abort = 0;
+    sm.p_next = 0;
+    sm.p_done = 0;
     sy::bar_init_fence();
   }
   __syncthreads();
   const int nkb = (nf + BK - 1) / BK;
-  // this CTA's tiles: blockIdx.x, blockIdx.x + gridDim.x, ...
-  const int64_t my_tiles = ntiles > blockIdx.x ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
-  const uint64_t n_slices = (uint64_t)my_tiles * (uint64_t)nkb;
-
-  // producer state (lane 0 of warp 0): next slice to load and its tile
+  // Tile schedule.  Static (tile_ctr null): this CTA's tiles are blockIdx.x,
+  // blockIdx.x + gridDim.x, ...  Dynamic: the producer claims the next tile
+  // of the walk from the grid-wide counter when it loads the tile's first
+  // slice and hands its index to the warps through tile_of; the tiles in
+  // flight then always stay a window of about gridDim.x consecutive tiles
+  // (which share their panels in L2), and a faster CTA simply takes more
+  // tiles.  (Statically scheduled CTAs drift apart over the ~200 rounds at
+  // nv = 32768 and re-read the panels from DRAM; making them meet fixes the
+  // traffic but paces the grid at its slowest CTA.)
+  constexpr bool dyn = DYN;  // (tile_ctr is used only when DYN)
+  const int my_tiles = ntiles > blockIdx.x ? (int)((ntiles - 1 - blockIdx.x) / gridDim.x) + 1 : 0;
+  // slices of this CTA (< 2^32, checked by the launcher); unbounded when dynamic
+  const uint32_t n_slices = dyn ? 0xffffffffu : (uint32_t)my_tiles * (uint32_t)nkb;
   const bool producer = threadIdx.x == 0;
-  uint64_t g_next = 0;
-  int pI = 0, pJ = 0;
-  // loads slice g_next (waiting until its ring stage is free); false on abort
-  // With sync_sl > 0 the producers of all CTAs (co-resident: cooperative
-  // launch) meet at the grid-wide counter every sync_sl slices: a producer
-  // does not load chunk c of its round-r tile before every CTA has loaded all
-  // earlier chunks.  Without it the CTAs drift apart over the ~200 rounds of
-  // tiles at nv = 32768, the tiles that share a row or column panel stop
-  // meeting in L2, and the panels are re-read from DRAM.
-  const int cpt = sync_sl > 0 ? (nkb + sync_sl - 1) / sync_sl : 0;  // chunks per tile
+  // With sync_sl > 0 (static schedule only) the producers of all CTAs
+  // (co-resident: cooperative launch) meet at the grid-wide counter every
+  // sync_sl slices: a producer does not load chunk c of its round-r tile
+  // before every CTA has loaded all earlier chunks.
+  const int cpt = (!DYN && sync_sl > 0) ? (nkb + sync_sl - 1) / sync_sl : 0;  // chunks per tile
+  // producer: loads its next slice (waiting until the ring stage is free);
+  // false on abort
   auto issue_one = [&]() -> bool {
     SmemT<BK, STAGES>& sm = *reinterpret_cast<SmemT<BK, STAGES>*>(smem_raw);
-    if (g_next >= n_slices) return true;
-    const int s = (int)(g_next % STAGES);
-    const uint32_t ph = (uint32_t)(g_next / STAGES) & 1u;
-    const int kb = (int)(g_next % (uint64_t)nkb);
-    const int64_t r = (int64_t)(g_next / nkb);  // round: this CTA's r-th tile
-    if (kb == 0) mg::band_tile(blockIdx.x + r * gridDim.x, T, R0, R1, G, pI, pJ);
+    const uint32_t g = sm.p_next;
+    if (sm.p_done || g >= n_slices) return true;
+    const int s = (int)(g % STAGES);
+    const uint32_t ph = (g / STAGES) & 1u;
+    const int kb = (int)(g % (uint32_t)nkb);
+    const int r = (int)(g / (uint32_t)nkb);  // this CTA's r-th tile
+    int pI, pJ;
+    if (!dyn && kb == 0) {
+      mg::band_tile(blockIdx.x + (int64_t)r * gridDim.x, T, R0, R1, G, pI, pJ);
+      sm.pI = pI;
+      sm.pJ = pJ;
+    }
     if (cpt && kb % sync_sl == 0 && (r | kb) != 0) {
       // CTAs holding a tile in round r, and the chunks issued before this one
-      const int64_t P = min((int64_t)gridDim.x, ntiles - r * (int64_t)gridDim.x);
-      const unsigned need = (unsigned)(r * cpt * gridDim.x + (int64_t)(kb / sync_sl) * P);
+      const int64_t P = min((int64_t)gridDim.x, ntiles - (int64_t)r * gridDim.x);
+      const unsigned need = (unsigned)((int64_t)r * cpt * gridDim.x + (int64_t)(kb / sync_sl) * P);
       if (!sy::counter_wait(sync, need, &sm.abort, err)) return false;
     }
     if (!sy::bar_wait(&sm.empty[s], ph ^ 1u, &sm.abort, err)) return false;
+    if (dyn && kb == 0) {
+      // (the stage being free means every warp has read tile_of of tile r - STAGES)
+      const unsigned long long t = atomicAdd(tile_ctr, 1ull);
+      if (t >= (unsigned long long)ntiles) {
+        sm.tile_of[r % STAGES] = -1;
+        sy::bar_arrive(&sm.full[s]);  // completes the phase with no copies: the warps see -1 and stop
+        sm.p_done = 1;
+        return true;
+      }
+      sm.tile_of[r % STAGES] = (int)t;  // published by the arrival below
+      mg::band_tile((int64_t)t, T, R0, R1, G, pI, pJ);
+      sm.pI = pI;
+      sm.pJ = pJ;
+    }
+    pI = sm.pI;
+    pJ = sm.pJ;
     sy::bar_arrive_tx(&sm.full[s], SLICE_BYTES);
     sy::tma_load_2d(&sm.A[s][0][0], &mapV, pI * C::BM, kb * BK, &sm.full[s]);
     sy::tma_load_2d(&sm.B[s][0][0], &mapV, pJ * C::BN, kb * BK, &sm.full[s]);
     if (cpt && ((kb + 1) % sync_sl == 0 || kb + 1 == nkb)) atomicAdd(sync, 1u);
-    ++g_next;
+    sm.p_next = g + 1;
     return true;
   };
   if (producer)
@@ -121,36 +156,40 @@ __global__ void __launch_bounds__(C::NT, 1)
 
   const mg::Lanes<C> L;
   mg::Acc<true, C::NJ> acc;
-  uint64_t it = 0;
-  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    int I, J;
-    mg::band_tile(t, T, R0, R1, G, I, J);
-    const int row0 = I * C::BM, col0 = J * C::BN;
+  uint32_t it = 0;
+  bool ok = true;
+  for (int lt = 0; ok && (dyn || lt < my_tiles); ++lt) {
+    int t = blockIdx.x + lt * gridDim.x;  // static schedule
     acc.zero();
-    bool ok = true;
     for (int kb = 0; kb < nkb; ++kb, ++it) {
       if (producer) ok = issue_one();  // slice it + STAGES - 1
       const int s = (int)(it % STAGES);
-      const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
+      const uint32_t ph = (it / STAGES) & 1u;
       // every lane waits (each gets the barrier's acquire); the warp follows
       // the common verdict so that it never diverges here
       const bool mine = ok && sy::bar_wait(&sm.full[s], ph, &sm.abort, err);
       if (!__all_sync(0xffffffffu, mine)) { ok = false; break; }
+      if (dyn && kb == 0) {
+        t = sm.tile_of[lt % STAGES];
+        if (t < 0) break;  // no tile left
+      }
       compute_slice_tma<BK, KU>(&sm.A[s][0][L.am], &sm.B[s][0][L.bn], acc);
       __syncwarp();
       if (lane == 0) sy::bar_arrive(&sm.empty[s]);
       if ((kb + 1) % FOLD_SLICES == 0) acc.fold();
     }
-    if (!ok) break;
+    if (!ok || t < 0) break;
     acc.fold();
-    mg::store_tile2<C, true, FASTDIV>(acc, L, row0, col0, nv, S, out, mode);
+    int I, J;
+    mg::band_tile(t, T, R0, R1, G, I, J);
+    mg::store_tile2<C, true, FASTDIV>(acc, L, I * C::BM, J * C::BN, nv, S, out, mode);
   }
   __syncthreads();
   if (*(volatile int*)&sm.abort) sy::drain_after_abort();
 }
 
 // ---- host side ----
-template <int BK, int STAGES, int KU, bool FASTDIV = false>
+template <int BK, int STAGES, int KU, bool FASTDIV = false, bool DYN = false>
 struct TmaLaunch {
   static constexpr size_t smem = sizeof(SmemT<BK, STAGES>);
   static cudaError_t run(ps_ctx* h, const VF32& V, const double* S, void* out, int mode, cudaStream_t st,
@@ -161,7 +200,7 @@ struct TmaLaunch {
       std::lock_guard<std::mutex> lk(mu);
       const uint64_t bit = 1ull << (h->device & 63);
       if (!(attr_done & bit)) {
-        const cudaError_t e = cudaFuncSetAttribute(mgemm2_tma_kernel<BK, STAGES, KU, FASTDIV>,
+        const cudaError_t e = cudaFuncSetAttribute(mgemm2_tma_kernel<BK, STAGES, KU, FASTDIV, DYN>,
                                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         attr_done |= bit;
@@ -172,8 +211,10 @@ struct TmaLaunch {
     const unsigned grid = (unsigned)std::min<int64_t>(ntiles, (int64_t)h->num_sms);
     // producers meet only when there is more than one round of tiles
     const int sync_sl = (ntiles > (int64_t)grid && h->mgemm_tma_sync > 0) ? h->mgemm_tma_sync : 0;
-    if (sync_sl) {
-      const cudaError_t e = cudaMemsetAsync(sync, 0, sizeof(unsigned), st);
+    // dynamic schedule: tile counter 8 bytes past the meeting counter
+    unsigned long long* tile_ctr = DYN ? reinterpret_cast<unsigned long long*>(sync + 2) : nullptr;
+    if (sync_sl || tile_ctr) {
+      const cudaError_t e = cudaMemsetAsync(sync, 0, 16, st);
       if (e != cudaSuccess) return e;
     }
     cudaLaunchConfig_t cfg = {};
@@ -186,8 +227,8 @@ struct TmaLaunch {
     attr[0].val.cooperative = sync_sl ? 1 : 0;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, mgemm2_tma_kernel<BK, STAGES, KU, FASTDIV>, map, (int)V.nv, (int)V.nf, S, out,
-                              mode, T, R0, R1, G, ntiles, err, sync, sync_sl);
+    return cudaLaunchKernelEx(&cfg, mgemm2_tma_kernel<BK, STAGES, KU, FASTDIV, DYN>, map, (int)V.nv, (int)V.nf, S, out,
+                              mode, T, R0, R1, G, ntiles, err, sync, sync_sl, tile_ctr);
   }
 };
 
@@ -197,6 +238,10 @@ cudaError_t launch_mgemm2_tma(ps_ctx* h, const VF32& V, const double* S, void* o
                               int T, int R0, int R1, int G, int64_t ntiles, int* err) {
   // TMA: 16-byte aligned base and row pitch; the tile walk assumes 128-wide tiles
   if ((uintptr_t)V.p % 16 != 0 || V.ld % 4 != 0 || V.nv < 1) return cudaErrorInvalidValue;
+  // tile indices and per-CTA slice counts in 32 bits
+  if (ntiles >= ((int64_t)1 << 31) ||
+      (double)ceil_div(ntiles, h->num_sms) * (double)ceil_div(V.nf, 16) >= 4294967295.0)
+    return cudaErrorInvalidValue;
   unsigned* sync = static_cast<unsigned*>(ws_get(h, WS_SYNC, 256));
   if (!sync) return cudaErrorMemoryAllocation;
   // slice width: 16 fields up to n_f = 32 (wider slices would be mostly zero
@@ -210,14 +255,20 @@ cudaError_t launch_mgemm2_tma(ps_ctx* h, const VF32& V, const double* S, void* o
   // (n_f <= 256: 2.59 -> 2.33 ms at n_f = 16, nv = 32768); at large n_f its
   // extra registers cost more than it saves (271.1 -> 275.8 ms at 8192)
   const bool fastdiv = V.nf <= 256;
+  // dynamic tile schedule (the default) unless the producers are to meet,
+  // which needs the static rounds; the other slice shapes are static only
+  const bool dyn = h->mgemm_tma_dynamic && h->mgemm_tma_sync <= 0;
 #define PS_TMA_RUN(...) TmaLaunch<__VA_ARGS__>::run(h, V, S, out, mode, st, T, R0, R1, G, ntiles, err, sync)
-  if (bk == 16) return fastdiv ? PS_TMA_RUN(16, 8, 8, true) : PS_TMA_RUN(16, 8, 8);
+  if (bk == 16) {
+    if (fastdiv) return dyn ? PS_TMA_RUN(16, 8, 8, true, true) : PS_TMA_RUN(16, 8, 8, true);
+    return dyn ? PS_TMA_RUN(16, 8, 8, false, true) : PS_TMA_RUN(16, 8, 8);
+  }
   if (bk == 64) return PS_TMA_RUN(64, 3, 16);
-  if (fastdiv) return PS_TMA_RUN(32, 4, 16, true);
+  if (fastdiv) return dyn ? PS_TMA_RUN(32, 4, 16, true, true) : PS_TMA_RUN(32, 4, 16, true);
   if (stages == 6) return PS_TMA_RUN(32, 6, 16);
   if (ku == 8) return PS_TMA_RUN(32, 4, 8);
   if (ku == 32) return PS_TMA_RUN(32, 4, 32);
-  return PS_TMA_RUN(32, 4, 16);
+  return dyn ? PS_TMA_RUN(32, 4, 16, false, true) : PS_TMA_RUN(32, 4, 16);
 #undef PS_TMA_RUN
 }
 

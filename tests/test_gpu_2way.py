@@ -225,16 +225,19 @@ def test_u8_rejected_on_other_paths(ps, handle):
 
 @pytest.mark.parametrize("nv,nf", [(129, 33), (300, 1000), (1300, 77), (700, 16), (4096, 64)])
 def test_operand_feeds_bit_identical(ps, handle, monkeypatch, nv, nf):
-    # the TMA-fed kernel (16- and 32-field slices) and the cp.async kernel
+    # the TMA-fed kernel (16-, 32- and 64-field slices; tiles claimed from a
+    # counter or assigned round-robin) and the cp.async kernel
     # run the same micro-kernel in the same order: every output bit-identical,
     # for FP32, FP64 and one-byte outputs, by parts, and in the 3-way n2 table
     import torch
     V = synth.zero_inflated(nv, nf, synth.seed_for(1, 71 + nv + nf))
     ref = oracle.c2_packed(oracle.to_vector_major(V))
     results = {}
-    for feed, bk in (("cpasync", "16"), ("tma", "16"), ("tma", "32"), ("tma", "64")):
+    for feed, bk, dyn in (("cpasync", "16", "1"), ("tma", "16", "1"), ("tma", "32", "1"), ("tma", "64", "1"),
+                          ("tma", "32", "0")):
         monkeypatch.setenv("PS_MGEMM_FEED", feed)
         monkeypatch.setenv("PS_MGEMM_TMA_BK", bk)
+        monkeypatch.setenv("PS_MGEMM_TMA_DYNAMIC", dyn)  # 0: static round-robin tiles
         h = ps.Handle(0)
         try:
             r = [metrics_2way(ps, h, V), metrics_2way(ps, h, V, out_dtype=np.float64),
@@ -250,11 +253,11 @@ def test_operand_feeds_bit_identical(ps, handle, monkeypatch, nv, nf):
             if nv <= 300:
                 from gpu_run import metrics_3way
                 r.append(metrics_3way(ps, h, V))
-            results[(feed, bk)] = r
+            results[(feed, bk, dyn)] = r
         finally:
             h.close()
-    assert_rel(results[("tma", "16")][0], ref, RTOL32, f"tma nv={nv} nf={nf}")
-    base = results[("cpasync", "16")]
+    assert_rel(results[("tma", "16", "1")][0], ref, RTOL32, f"tma nv={nv} nf={nf}")
+    base = results[("cpasync", "16", "1")]
     for key, r in results.items():
         for a, b in zip(r, base):
             np.testing.assert_array_equal(a, b, err_msg=str(key))
