@@ -286,3 +286,21 @@ def test_tma_producer_meetings(ps, handle, monkeypatch):
         np.testing.assert_array_equal(out.cpu().numpy(), base)
     finally:
         h.close()
+
+
+@pytest.mark.parametrize("scale", [1e-37, 1e36])
+def test_fast_division_fallback_range(ps, handle, monkeypatch, scale):
+    # n_f <= 256 takes the branch-free division; denominators below 2^-120
+    # or above 2^120 are outside its range, so the warps rewrite their
+    # outputs with __fdiv_rn: same values as the oracle and, bit for bit, as
+    # the cp.async kernel (which always divides with __fdiv_rn)
+    V = (synth.zero_inflated(300, 40, synth.seed_for(1, 95)).astype(np.float64) * scale).astype(np.float32)
+    ref = oracle.c2_packed(oracle.to_vector_major(V))
+    got = metrics_2way(ps, handle, V)
+    assert_rel(got, ref, RTOL32, f"scale {scale}")
+    monkeypatch.setenv("PS_MGEMM_FEED", "cpasync")
+    h = ps.Handle(0)
+    try:
+        np.testing.assert_array_equal(metrics_2way(ps, h, V), got)
+    finally:
+        h.close()
