@@ -504,7 +504,7 @@ ps_status ps_create(ps_handle* out, int device) {
   if (const char* v = getenv("PS_MGEMM_TMA_SYNC")) h->mgemm_tma_sync = std::max(0, atoi(v));
   if (const char* v = getenv("PS_MGEMM_TMA_DYNAMIC")) h->mgemm_tma_dynamic = atoi(v) != 0;
   if (const char* v = getenv("PS_MGEMM3_FEED")) h->mgemm3_feed_tma = strcmp(v, "cpasync") != 0;
-  if (const char* v = getenv("PS_MGEMM_TMA_STAGES")) h->mgemm_tma_stages = atoi(v) == 6 ? 6 : 4;
+  if (const char* v = getenv("PS_MGEMM_TMA_STAGES")) h->mgemm_tma_stages = atoi(v) == 6 ? 6 : (atoi(v) == 3 ? 3 : 4);
   if (const char* v = getenv("PS_THERMO_TILE_M")) h->thermo_tile_m = atoi(v) == 128 ? 128 : (atoi(v) == 256 ? 256 : 0);
   if (const char* v = getenv("PS_THERMO_SYNC_KB")) h->thermo_sync_kb = std::max(0, atoi(v));
   if (prop.major < 10) {

@@ -270,9 +270,16 @@ cudaError_t launch_mgemm3_tma(ps_ctx* h, const VF32& V, const double* S, const f
   // slices per CTA counted in 32 bits
   if ((double)ceil_div(ntiles, h->num_sms) * (double)ceil_div(V.nf, 16) >= 4294967295.0)
     return cudaErrorInvalidValue;
-  if (V.nf <= 16) return Tma3Launch<16, 8, 8>::run(h, V, S, n2sq, items, jb, out, ntiles, err, st);
-  // 16 k-steps per unrolled iteration: 457.8 ms vs 463.5 with 8 at 2048 x 4096
+  // slice width by n_f (a wider slice than n_f is mostly zero fill): 64
+  // fields in 3 stages above 32 (2048 x 4096: 433.0 ms; 32 fields in 4
+  // stages 457.2 ms, in 3 stages 450.7 ms: the per-slice pivot min, waits
+  // and releases are what a wider slice saves), 16 k-steps per unrolled
+  // iteration (457.8 vs 463.5 ms with 8 at 32-field slices)
+  const int bk = V.nf <= 16 ? 16 : (V.nf <= 32 ? 32 : (h->mgemm_tma_bk ? h->mgemm_tma_bk : 64));
+  if (bk == 16) return Tma3Launch<16, 8, 8>::run(h, V, S, n2sq, items, jb, out, ntiles, err, st);
+  if (bk == 64) return Tma3Launch<64, 3, 16>::run(h, V, S, n2sq, items, jb, out, ntiles, err, st);
   if (h->mgemm_tma_ku == 8) return Tma3Launch<32, 4, 8>::run(h, V, S, n2sq, items, jb, out, ntiles, err, st);
+  if (h->mgemm_tma_stages == 3) return Tma3Launch<32, 3, 16>::run(h, V, S, n2sq, items, jb, out, ntiles, err, st);
   return Tma3Launch<32, 4, 16>::run(h, V, S, n2sq, items, jb, out, ntiles, err, st);
 }
 
