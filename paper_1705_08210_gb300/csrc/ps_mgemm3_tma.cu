@@ -8,11 +8,12 @@
 // slice, lane 0 of warp 0 issues three TMA loads into an mbarrier-guarded
 // ring: the 128-vector row panel, the 128-vector column panel, and a
 // 4-vector box holding the pivot column v_j.  X_j = min(V, v_j) is never
-// stored: when a slice lands each warp min-s two of its field rows of the
-// row panel with the pivot value, arrives on the slice's `ready` barrier and
-// waits for the other warps' rows (a bounded mbarrier wait, not a CTA
-// barrier), then runs the 2-way micro-kernel (8 x 4 outputs per lane, FP32
-// min + packed FP32 add, TwoSum fold every 64 fields) on it.
+// stored: one slice ahead of the compute each warp min-s its BK/16 field
+// rows of the row panel with the pivot value in place and arrives on the
+// slice's `ready` barrier; before computing a slice a warp waits there for
+// the other warps' rows (a bounded mbarrier wait, not a CTA barrier), then
+// runs the 2-way micro-kernel (8 x 4 outputs per lane, FP32 min + packed
+// FP32 add, TwoSum fold every 64 fields) on it.
 //
 // Warp placement.  A warp owns a 64-row x 16-column block.  The tile that
 // straddles the pivot has rows i >= j (past the pivot's rectangle) and
