@@ -45,7 +45,8 @@
  *   detected before any launch and leave outputs untouched.  CUDA errors are
  *   reported as PS_ERR_CUDA; ps_last_error() gives the message.  No
  *   exception, abort or exit crosses this boundary.  Every wait inside a
- *   kernel is bounded (2 s); a TMA-fed min-product kernel whose pipeline
+ *   kernel is bounded (ps_config.wait_limit_ns, 2 s by default); a TMA-fed
+ *   min-product kernel whose pipeline
  *   wait timed out raises a word in the handle's mapped host memory and
  *   returns, leaving that call's output incomplete: the call reports
  *   PS_ERR_TIMEOUT itself when it synchronises (host buffers), otherwise the
@@ -145,10 +146,109 @@ typedef struct {
 } ps_triple;
 
 /* ---------------------------------------------------------------------------
+ * Handle configuration.  The paper fixes its precision (SP or DP) and its
+ * decomposition sizes at build or job-launch time (Sections 5 and 6.5); here
+ * they are per-handle run-time settings.  Every field has a default (what
+ * ps_config_init writes; 0 means "automatic" in every kernel-choice field),
+ * and no kernel choice depends on anything outside this struct.  Results are
+ * the same, bit for bit, under every kernel choice (only speed differs).
+ *
+ *   precision      : arithmetic of the calls that take no path argument
+ *                    (ps_metrics_2way_part, ps_metrics_batched and the 3-way
+ *                    calls): PS_PATH_FP32 (default).  PS_PATH_FP64 is the
+ *                    paper's DP build: ps_metrics_2way_part then computes on
+ *                    the FP64 path, and the calls with no FP64 kernel (3-way,
+ *                    thresholded, batched) return PS_ERR_UNSUPPORTED.
+ *   debug_checks   : 1 = every call first checks that the input values are
+ *                    finite and >= 0 (one extra pass over V, synchronising)
+ *                    and returns PS_ERR_INVALID_ARG otherwise; 0 (default) =
+ *                    such input is undefined, as the paper assumes v >= 0.
+ *   wait_limit_ns  : bound of every wait inside a kernel (pipeline barriers,
+ *                    grid-wide meetings, the batched launch's dependency
+ *                    waits).  A wait that runs out makes the call return
+ *                    PS_ERR_TIMEOUT (see "Errors" above).  Default 2e9 (2 s);
+ *                    must be in [1e3, 6e10].
+ *   autotune_cache : path of the JSON-lines file of ps_autotune_batched,
+ *                    used when that call's cache_path is NULL, and read by
+ *                    ps_metrics_batched for batch shapes the handle has not
+ *                    tuned itself.  NULL = none.  The string is copied.
+ *   Kernel choices of the FP32 min-product (0 = automatic):
+ *   mgemm_feed     : 2-way operand feed: 1 = TMA ring (automatic),
+ *                    2 = per-thread cp.async.
+ *   mgemm3_feed    : 3-way operand feed: 1 = TMA ring (automatic), 2 = cp.async.
+ *   mgemm_tile     : 64 or 128 (automatic) vectors per tile side of the
+ *                    cp.async kernels (the TMA kernels use 128).
+ *   mgemm_warps    : 8 or 16 warps per 128 x 128 tile of the cp.async
+ *                    kernels (automatic: 16 for 2-way, 8 for 3-way).
+ *   mgemm_unroll   : 4, 8 (automatic) or 16 k-steps per loop iteration of
+ *                    the cp.async kernels.
+ *   mgemm_add      : 1 = packed add.rn.f32x2 (automatic), 2 = scalar adds
+ *                    (8-warp 128 x 128 cp.async kernels).
+ *   mgemm_band     : tile rows per band of the 2-way tile walk, 1..64
+ *                    (automatic 16).
+ *   tma_slice      : fields per TMA slice, 16, 32 or 64 (automatic: by n_f).
+ *   tma_unroll     : k-steps per loop iteration of the TMA kernels, 8, 16
+ *                    (automatic) or 32.
+ *   tma_stages     : ring depth of 32-field TMA slices, 3, 4 (automatic) or 6.
+ *   tma_schedule   : tiles of the TMA 2-way kernel: 1 = claimed from a
+ *                    grid-wide counter (automatic), 2 = static round-robin.
+ *   tma_meet       : with the static schedule, slices between grid-wide
+ *                    meetings of the TMA producers (0 = never, automatic).
+ *   mgemm3_schedule: work items of the TMA 3-way kernel: 1 = claimed from a
+ *                    grid-wide counter (automatic), 2 = static round-robin.
+ *   thermo_tile_m  : rows of the thermometer tensor-core tile, 128 or 256
+ *                    (automatic: by the operand width).
+ *   thermo_meet_kb : k-blocks between grid-wide meetings of the thermometer
+ *                    GEMM's producers; 0 = automatic (960), -1 = never.
+ *   test_batched_stall : testing aid for the timeout path, 0 by default.
+ *                    1 = the next ps_metrics_batched call (persistent mode)
+ *                    raises its first dependency target by one item that
+ *                    does not exist, so that the launch's dependency wait
+ *                    runs out after wait_limit_ns and the call returns
+ *                    PS_ERR_TIMEOUT; the setting then clears itself.  No
+ *                    kernel is altered: the wait is an ordinary bounded
+ *                    wait on a count that nothing completes. */
+typedef struct {
+  int32_t precision;
+  int32_t debug_checks;
+  int64_t wait_limit_ns;
+  const char* autotune_cache;
+  int32_t mgemm_feed;
+  int32_t mgemm3_feed;
+  int32_t mgemm_tile;
+  int32_t mgemm_warps;
+  int32_t mgemm_unroll;
+  int32_t mgemm_add;
+  int32_t mgemm_band;
+  int32_t tma_slice;
+  int32_t tma_unroll;
+  int32_t tma_stages;
+  int32_t tma_schedule;
+  int32_t tma_meet;
+  int32_t mgemm3_schedule;
+  int32_t thermo_tile_m;
+  int32_t thermo_meet_kb;
+  int32_t test_batched_stall;
+} ps_config;
+
+/* Defaults: precision PS_PATH_FP32, no debug checks, 2 s wait limit, no
+ * autotune cache, every kernel choice automatic (0). */
+void ps_config_init(ps_config* cfg);
+
+/* ---------------------------------------------------------------------------
  * Handle.  ps_create binds a handle to CUDA device `device` (the device is
- * made current inside each call).  Returns PS_ERR_INVALID_ARG for a null
- * `out` or an invalid device, PS_ERR_CUDA if the device cannot be used. */
-ps_status ps_create(ps_handle* out, int device);
+ * made current inside each call) with configuration `cfg` (copied; NULL =
+ * ps_config_init's defaults).  Returns PS_ERR_INVALID_ARG for a null `out`,
+ * an invalid device or a configuration field outside the ranges above,
+ * PS_ERR_CUDA if the device cannot be used. */
+ps_status ps_create(ps_handle* out, int device, const ps_config* cfg);
+/* Current configuration of `h` (autotune_cache points at the handle's copy,
+ * valid until the next ps_set_config or ps_destroy). */
+ps_status ps_get_config(ps_handle h, ps_config* cfg);
+/* Replaces the configuration of `h` (validated as in ps_create); applies to
+ * later calls.  Synchronises the device first, so no queued call of the
+ * handle runs under the old settings. */
+ps_status ps_set_config(ps_handle h, const ps_config* cfg);
 /* Frees the handle and its workspace (synchronises the device first).
  * NULL is accepted. */
 ps_status ps_destroy(ps_handle h);
@@ -270,7 +370,8 @@ ps_status ps_threshold_2way(ps_handle h, const ps_matrix* V, float tau,
  *   be NULL.  Parts are disjoint and cover everything.
  * ps_metrics_2way_part: the pairs of rows [begin, end) of part `part`,
  *   written at their packed positions of the full nv*(nv-1)/2 DEVICE array
- *   `out` (other entries untouched); FP32 path.
+ *   `out` (other entries untouched); FP32 path, or the FP64 path under a
+ *   handle whose ps_config.precision is PS_PATH_FP64.
  * Errors: PS_ERR_INVALID_ARG for bad sizes or part indices. */
 ps_status ps_partition(int64_t nv, int32_t way, int32_t nparts, int32_t part,
                        int64_t* begin, int64_t* end, int64_t* out_begin,
@@ -308,16 +409,19 @@ typedef struct {
  * The kernel variant is the one ps_autotune_batched chose for these shapes,
  * else the default.  Synchronises `stream` (it reads the launch's error flag).
  * Errors: PS_ERR_INVALID_ARG for a problem outside the limits above;
- *   PS_ERR_TIMEOUT if a dependency wait inside the launch ran out (2 s). */
+ *   PS_ERR_TIMEOUT if a dependency wait inside the launch ran out
+ *   (ps_config.wait_limit_ns; the handle stays usable);
+ *   PS_ERR_UNSUPPORTED under FP64 precision. */
 ps_status ps_metrics_batched(ps_handle h, const ps_problem* probs, int32_t n,
                              int32_t mode, ps_stream stream);
 
-/* Autotuner of the batched launch: times every kernel configuration
- * (accumulate form: packed f32x2 or scalar adds; k-unroll depth 16, 8 or 4)
- * on these problems, keeps the fastest for this batch shape in the handle
- * and appends {"shape_signature", "variant", "ms"} as one JSON line to
- * cache_path (if not NULL).  If cache_path already holds this shape
- * signature, its variant is used without measuring.  choice (if not NULL)
+/* Autotuner of the batched launch: times every kernel configuration (tile
+ * 128 x 128 with 8 or 16 warps or 64 x 64 with 2 warps; k-unroll depth 16, 8
+ * or 4) on these problems, keeps the fastest for this batch shape in the
+ * handle and appends {"shape_signature", "variant", "ms"} as one JSON line to
+ * cache_path (NULL: the handle's ps_config.autotune_cache, if any).  If that
+ * file already holds this shape signature, its variant is used without
+ * measuring.  choice (if not NULL)
  * receives a readable description of the chosen configuration.
  * Errors: as ps_metrics_batched. */
 ps_status ps_autotune_batched(ps_handle h, const ps_problem* probs, int32_t n,
@@ -432,9 +536,14 @@ ps_status ps_probe_minadd_peak(ps_handle h, int32_t variant,
  *     ps_metrics_2way.
  * Its only scratch (nv FP64 sums) lives in a 512 KiB array inside the
  * library's device image, held on every GPU that loads the library until the
- * process exits.  No handle is used and nothing is allocated.  The first call
- * on a device looks up that array's device address (cudaGetSymbolAddress) and
- * sets kernel attributes; make that first call before any stream capture.
+ * process exits.  No handle is used and nothing is allocated.  Every call
+ * looks up that array's device address (cudaGetSymbolAddress, a host-side
+ * query); the first call on a device also loads the library's kernels there
+ * and sets kernel attributes, so make that first call before any stream
+ * capture.  The call always runs the 16-warp 128 x 128 cp.async min-product
+ * kernel under the default configuration (no handle, so no ps_config
+ * applies); its values equal those of ps_metrics_2way's default TMA-fed
+ * kernel bit for bit.
  * All calls share the array and it keeps the last call's contents; every call
  * rewrites the entries it reads, so nothing needs clearing.  Calls that
  * overlap on the GPU (other streams or host threads) race on the array:

@@ -8,6 +8,7 @@
 #include <cstdarg>
 #include <cstdlib>
 #include <cstring>
+#include <initializer_list>
 #include <mutex>
 #include <new>
 #include <vector>
@@ -107,6 +108,60 @@ static void timing_clear(ps_ctx* h) {
     cudaEventDestroy(r.b);
   }
   h->trecs.clear();
+}
+
+ps_status apply_config(ps_ctx* h, const ps_config* user) {
+  ps_config c;
+  ps_config_init(&c);
+  if (user) c = *user;
+  auto bad = [h](const char* field, long long v) {
+    return fail(h, PS_ERR_INVALID_ARG, "ps_config.%s = %lld is outside its range", field, v);
+  };
+  auto one_of = [](int v, std::initializer_list<int> ok) {
+    for (int x : ok)
+      if (v == x) return true;
+    return false;
+  };
+  if (!one_of(c.precision, {PS_PATH_FP32, PS_PATH_FP64})) return bad("precision", c.precision);
+  if (!one_of(c.debug_checks, {0, 1})) return bad("debug_checks", c.debug_checks);
+  if (c.wait_limit_ns < 1000 || c.wait_limit_ns > 60000000000LL) return bad("wait_limit_ns", c.wait_limit_ns);
+  if (!one_of(c.mgemm_feed, {0, 1, 2})) return bad("mgemm_feed", c.mgemm_feed);
+  if (!one_of(c.mgemm3_feed, {0, 1, 2})) return bad("mgemm3_feed", c.mgemm3_feed);
+  if (!one_of(c.mgemm_tile, {0, 64, 128})) return bad("mgemm_tile", c.mgemm_tile);
+  if (!one_of(c.mgemm_warps, {0, 8, 16})) return bad("mgemm_warps", c.mgemm_warps);
+  if (!one_of(c.mgemm_unroll, {0, 4, 8, 16})) return bad("mgemm_unroll", c.mgemm_unroll);
+  if (!one_of(c.mgemm_add, {0, 1, 2})) return bad("mgemm_add", c.mgemm_add);
+  if (c.mgemm_band < 0 || c.mgemm_band > 64) return bad("mgemm_band", c.mgemm_band);
+  if (!one_of(c.tma_slice, {0, 16, 32, 64})) return bad("tma_slice", c.tma_slice);
+  if (!one_of(c.tma_unroll, {0, 8, 16, 32})) return bad("tma_unroll", c.tma_unroll);
+  if (!one_of(c.tma_stages, {0, 3, 4, 6})) return bad("tma_stages", c.tma_stages);
+  if (!one_of(c.tma_schedule, {0, 1, 2})) return bad("tma_schedule", c.tma_schedule);
+  if (c.tma_meet < 0 || c.tma_meet > 1 << 20) return bad("tma_meet", c.tma_meet);
+  if (!one_of(c.mgemm3_schedule, {0, 1, 2})) return bad("mgemm3_schedule", c.mgemm3_schedule);
+  if (!one_of(c.thermo_tile_m, {0, 128, 256})) return bad("thermo_tile_m", c.thermo_tile_m);
+  if (c.thermo_meet_kb < -1 || c.thermo_meet_kb > 1 << 20) return bad("thermo_meet_kb", c.thermo_meet_kb);
+  if (!one_of(c.test_batched_stall, {0, 1})) return bad("test_batched_stall", c.test_batched_stall);
+  h->cache_path = c.autotune_cache ? c.autotune_cache : "";
+  c.autotune_cache = c.autotune_cache ? h->cache_path.c_str() : nullptr;
+  h->cfg = c;
+  h->wait_ns = (unsigned long long)c.wait_limit_ns;
+  h->mgemm_feed_tma = c.mgemm_feed != 2;
+  h->mgemm3_feed_tma = c.mgemm3_feed != 2;
+  h->mgemm_tile = c.mgemm_tile == 64 ? 64 : 128;
+  h->mgemm_warps = c.mgemm_warps;
+  h->mgemm_ku = c.mgemm_unroll ? c.mgemm_unroll : 8;
+  h->mgemm_packed_add = c.mgemm_add != 2;
+  h->mgemm_band = c.mgemm_band ? c.mgemm_band : 16;
+  h->mgemm_tma_bk = c.tma_slice;
+  h->mgemm_tma_ku = c.tma_unroll;
+  h->mgemm_tma_stages = c.tma_stages ? c.tma_stages : 4;
+  h->mgemm_tma_dynamic = c.tma_schedule != 2;
+  h->mgemm_tma_sync = c.tma_schedule == 2 ? c.tma_meet : 0;
+  h->mgemm3_dynamic = c.mgemm3_schedule != 2;
+  h->thermo_tile_m = c.thermo_tile_m;
+  h->thermo_sync_kb = c.thermo_meet_kb == 0 ? 960 : (c.thermo_meet_kb < 0 ? 0 : c.thermo_meet_kb);
+  h->batched_stall = c.test_batched_stall;
+  return PS_OK;
 }
 
 namespace {
@@ -211,6 +266,17 @@ ps_status prepare(ps_ctx* h, const ps_matrix& V, cudaStream_t st, bool need_f32,
     P->dev.data = d;
     P->host_input = true;
   }
+  if (h->cfg.debug_checks) {
+    // the paper's precondition v >= 0 (Section 2.1), and finite values
+    auto* bad = static_cast<unsigned long long*>(ws_get(h, WS_AUX2, 256));
+    if (!bad) return PS_ERR_OOM;
+    PS_CUDA_TRY(h, launch_count_invalid(P->dev, bad, st));
+    unsigned long long nbad = 0;
+    PS_CUDA_TRY(h, cudaMemcpyAsync(&nbad, bad, sizeof(nbad), cudaMemcpyDeviceToHost, st));
+    PS_CUDA_TRY(h, cudaStreamSynchronize(st));
+    if (nbad)
+      return fail(h, PS_ERR_INVALID_ARG, "debug check: %llu input values are negative, NaN or infinite", nbad);
+  }
   if (need_sums) {
     P->S = static_cast<double*>(ws_get(h, WS_SUMS, (size_t)std::max<int64_t>(V.nv, 1) * 8));
     if (!P->S) return PS_ERR_OOM;
@@ -232,6 +298,24 @@ ps_status prepare(ps_ctx* h, const ps_matrix& V, cudaStream_t st, bool need_f32,
     }
     P->f32 = VF32{d, ldp, (int)V.nv, (int)V.nf};
   }
+  return PS_OK;
+}
+
+// FP64 field-major operand of the FP64 kernel: the caller's matrix when it
+// already is one, else an exact widening / transpose into the workspace.
+ps_status fp64_operand(ps_ctx* h, const ps_matrix* V, const Prepared& P, cudaStream_t st, const double** X,
+                       int64_t* ld) {
+  if (V->dtype == PS_F64 && V->layout == PS_LAYOUT_FIELD_MAJOR) {
+    *X = static_cast<const double*>(P.dev.data);
+    *ld = V->ld;
+    return PS_OK;
+  }
+  const int64_t ldp = round_up(V->nv, 4);
+  double* d = static_cast<double*>(ws_get(h, WS_PACKED, (size_t)std::max<int64_t>(V->nf * ldp, 1) * 8));
+  if (!d) return PS_ERR_OOM;
+  PS_CUDA_TRY(h, launch_pack_f64(P.dev, d, ldp, st));
+  *X = d;
+  *ld = ldp;
   return PS_OK;
 }
 
@@ -459,7 +543,14 @@ const char* ps_last_error(ps_handle h) {
   return g_last_error.c_str();
 }
 
-ps_status ps_create(ps_handle* out, int device) {
+void ps_config_init(ps_config* cfg) {
+  if (!cfg) return;
+  memset(cfg, 0, sizeof(*cfg));
+  cfg->precision = PS_PATH_FP32;
+  cfg->wait_limit_ns = 2000000000LL;
+}
+
+ps_status ps_create(ps_handle* out, int device, const ps_config* cfg) {
   if (!out) return fail(nullptr, PS_ERR_INVALID_ARG, "ps_create: null out");
   *out = nullptr;
   int n = 0;
@@ -473,6 +564,12 @@ ps_status ps_create(ps_handle* out, int device) {
   ps_ctx* h = new (std::nothrow) ps_ctx();
   if (!h) return fail(nullptr, PS_ERR_OOM, "ps_create: out of host memory");
   h->device = device;
+  const ps_status cs = apply_config(h, cfg);
+  if (cs != PS_OK) {
+    const std::string msg = h->last_error;
+    delete h;
+    return fail(nullptr, cs, "%s", msg.c_str());
+  }
   Guard g(device);
   cudaDeviceProp prop;
   e = cudaGetDeviceProperties(&prop, device);
@@ -484,29 +581,6 @@ ps_status ps_create(ps_handle* out, int device) {
   h->cc_major = prop.major;
   h->cc_minor = prop.minor;
   h->smem_optin = prop.sharedMemPerBlockOptin;
-  if (const char* v = getenv("PS_MGEMM_ADD")) h->mgemm_packed_add = strcmp(v, "scalar") != 0;
-  if (const char* v = getenv("PS_MGEMM_KU")) {
-    const int ku = atoi(v);
-    if (ku == 4 || ku == 8 || ku == 16) h->mgemm_ku = ku;
-  }
-  if (const char* v = getenv("PS_MGEMM_TILE")) h->mgemm_tile = atoi(v) == 64 ? 64 : 128;
-  if (const char* v = getenv("PS_MGEMM_WARPS")) h->mgemm_warps = atoi(v) == 16 ? 16 : (atoi(v) == 8 ? 8 : 0);
-  if (const char* v = getenv("PS_MGEMM_BAND")) h->mgemm_band = std::max(1, std::min(atoi(v), 64));
-  if (const char* v = getenv("PS_MGEMM_FEED")) h->mgemm_feed_tma = strcmp(v, "cpasync") != 0;
-  if (const char* v = getenv("PS_MGEMM_TMA_BK")) {
-    const int bk = atoi(v);
-    h->mgemm_tma_bk = (bk == 16 || bk == 32 || bk == 64) ? bk : 0;
-  }
-  if (const char* v = getenv("PS_MGEMM_TMA_KU")) {
-    const int ku = atoi(v);
-    h->mgemm_tma_ku = (ku == 8 || ku == 16 || ku == 32) ? ku : 0;
-  }
-  if (const char* v = getenv("PS_MGEMM_TMA_SYNC")) h->mgemm_tma_sync = std::max(0, atoi(v));
-  if (const char* v = getenv("PS_MGEMM_TMA_DYNAMIC")) h->mgemm_tma_dynamic = atoi(v) != 0;
-  if (const char* v = getenv("PS_MGEMM3_FEED")) h->mgemm3_feed_tma = strcmp(v, "cpasync") != 0;
-  if (const char* v = getenv("PS_MGEMM_TMA_STAGES")) h->mgemm_tma_stages = atoi(v) == 6 ? 6 : (atoi(v) == 3 ? 3 : 4);
-  if (const char* v = getenv("PS_THERMO_TILE_M")) h->thermo_tile_m = atoi(v) == 128 ? 128 : (atoi(v) == 256 ? 256 : 0);
-  if (const char* v = getenv("PS_THERMO_SYNC_KB")) h->thermo_sync_kb = std::max(0, atoi(v));
   if (prop.major < 10) {
     delete h;
     return fail(nullptr, PS_ERR_UNSUPPORTED, "device %d is sm_%d%d; this library is built for sm_103a",
@@ -514,6 +588,21 @@ ps_status ps_create(ps_handle* out, int device) {
   }
   *out = h;
   return PS_OK;
+}
+
+ps_status ps_get_config(ps_handle h, ps_config* cfg) {
+  if (!h || !cfg) return fail(h, PS_ERR_INVALID_ARG, "ps_get_config: null argument");
+  *cfg = h->cfg;
+  return PS_OK;
+}
+
+ps_status ps_set_config(ps_handle h, const ps_config* cfg) {
+  if (!h) return fail(nullptr, PS_ERR_INVALID_ARG, "null handle");
+  {
+    Guard g(h->device);
+    cudaDeviceSynchronize();
+  }
+  return apply_config(h, cfg);
 }
 
 ps_status ps_destroy(ps_handle h) {
@@ -651,17 +740,8 @@ ps_status ps_metrics_2way(ps_handle h, const ps_matrix* V, int32_t path, int32_t
     if (s != PS_OK) return s;
     const double* X;
     int64_t ld;
-    if (V->dtype == PS_F64 && V->layout == PS_LAYOUT_FIELD_MAJOR) {
-      X = static_cast<const double*>(P.dev.data);
-      ld = V->ld;
-    } else {  // exact widening / transpose into an FP64 field-major copy
-      const int64_t ldp = round_up(V->nv, 4);
-      double* d = static_cast<double*>(ws_get(h, WS_PACKED, (size_t)std::max<int64_t>(V->nf * ldp, 1) * 8));
-      if (!d) return PS_ERR_OOM;
-      PS_CUDA_TRY(h, launch_pack_f64(P.dev, d, ldp, st));
-      X = d;
-      ld = ldp;
-    }
+    s = fp64_operand(h, V, P, st, &X, &ld);
+    if (s != PS_OK) return s;
     ScopedTimer tm(h, "mgemm2_f64", st);
     PS_CUDA_TRY(h, launch_mgemm2_f64(h, X, ld, (int)V->nv, (int)V->nf, P.S, o.dev,
                                      out_dtype == PS_F64, st));
@@ -705,6 +785,21 @@ ps_status ps_metrics_2way_part(ps_handle h, const ps_matrix* V, int32_t nparts, 
   s = resolve_out(h, out, (size_t)npairs * dtype_size(out_dtype), WS_OUTPUT, &o);
   if (s != PS_OK) return s;
   if (o.host) return fail(h, PS_ERR_INVALID_ARG, "ps_metrics_2way_part needs a device output");
+  if (wants_fp64(h)) {
+    // the paper's DP arithmetic: the FP64 kernel over the same rows
+    if (out_dtype == PS_U8) return fail(h, PS_ERR_UNSUPPORTED, "PS_U8 output under FP64 precision");
+    Prepared P;
+    s = prepare(h, *V, st, false, &P);
+    if (s != PS_OK) return s;
+    const double* X;
+    int64_t ld;
+    s = fp64_operand(h, V, P, st, &X, &ld);
+    if (s != PS_OK) return s;
+    ScopedTimer tm(h, "mgemm2_f64", st);
+    PS_CUDA_TRY(h, launch_mgemm2_f64(h, X, ld, (int)V->nv, (int)V->nf, P.S, o.dev, out_dtype == PS_F64, st, rb,
+                                     re));
+    return finish(h, o, P.host_input, st);
+  }
   Prepared P;
   s = prepare(h, *V, st, true, &P);
   if (s != PS_OK) return s;
@@ -727,6 +822,8 @@ ps_status ps_metrics_3way(ps_handle h, const ps_matrix* V, int64_t j_begin, int6
   if (const ps_status ae = take_async_error(h); ae != PS_OK) return ae;
   ps_status s = check_matrix(h, V, 3);
   if (s != PS_OK) return s;
+  if (wants_fp64(h))
+    return fail(h, PS_ERR_UNSUPPORTED, "%s has no FP64 kernel (handle precision is PS_PATH_FP64)", "ps_metrics_3way");
   if (j_begin < 0 || j_end < j_begin || j_end > V->nv)
     return fail(h, PS_ERR_INVALID_ARG, "pivot range [%lld,%lld) not inside [0,%lld]",
                 (long long)j_begin, (long long)j_end, (long long)V->nv);
@@ -760,6 +857,8 @@ ps_status ps_threshold_3way(ps_handle h, const ps_matrix* V, float tau, int32_t 
   if (const ps_status ae = take_async_error(h); ae != PS_OK) return ae;
   ps_status s = check_matrix(h, V, 3);
   if (s != PS_OK) return s;
+  if (wants_fp64(h))
+    return fail(h, PS_ERR_UNSUPPORTED, "%s has no FP64 kernel (handle precision is PS_PATH_FP64)", "ps_threshold_3way");
   if (V->nv > (1 << 21)) return fail(h, PS_ERR_INVALID_ARG, "nv=%lld above 2^21", (long long)V->nv);
   if (capacity < 0) return fail(h, PS_ERR_INVALID_ARG, "capacity < 0");
   if (!count) return fail(h, PS_ERR_INVALID_ARG, "null count");
@@ -824,6 +923,8 @@ ps_status ps_threshold_2way(ps_handle h, const ps_matrix* V, float tau, ps_pair*
   if (!h) return fail(nullptr, PS_ERR_INVALID_ARG, "null handle");
   ps_status s = check_matrix(h, V, 2);
   if (s != PS_OK) return s;
+  if (wants_fp64(h))
+    return fail(h, PS_ERR_UNSUPPORTED, "%s has no FP64 kernel (handle precision is PS_PATH_FP64)", "ps_threshold_2way");
   if (V->nv > 2147483647LL) return fail(h, PS_ERR_INVALID_ARG, "nv=%lld above 2^31-1", (long long)V->nv);
   if (capacity < 0) return fail(h, PS_ERR_INVALID_ARG, "capacity < 0");
   if (!count) return fail(h, PS_ERR_INVALID_ARG, "null count");

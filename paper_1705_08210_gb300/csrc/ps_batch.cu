@@ -50,19 +50,45 @@ uint64_t shape_signature(const ps_problem* probs, int n) {
   return h;
 }
 
-uint64_t full_signature(const ps_problem* probs, int n, int variant) {
+// Everything a captured launch depends on: shapes, pointers, kernel variant
+// and the wait limit (a kernel argument baked into the graph).
+uint64_t full_signature(const ps_problem* probs, int n, int variant, unsigned long long wait_ns) {
   uint64_t h = shape_signature(probs, n);
   for (int t = 0; t < n; ++t) {
     const uintptr_t f[3] = {(uintptr_t)probs[t].V.data, (uintptr_t)probs[t].out,
                             (uintptr_t)probs[t].V.ld};
     h = fnv(h, f, sizeof(f));
   }
+  h = fnv(h, &wait_ns, sizeof(wait_ns));
   return fnv(h, &variant, sizeof(variant));
+}
+
+// Variant stored for shape signature `sigs` in a JSON-lines autotune cache
+// (the last matching line wins), or -1.
+int cached_variant(const char* path, const char* sigs) {
+  int best = -1;
+  if (!path || !*path) return best;
+  if (FILE* f = fopen(path, "r")) {
+    char line[1024];
+    while (fgets(line, sizeof(line), f)) {
+      const char* p = strstr(line, sigs);
+      const char* v = strstr(line, "\"variant\": ");
+      if (p && v) best = atoi(v + 11);
+    }
+    fclose(f);
+  }
+  return best;
 }
 
 // candidate configurations of the autotuner (see mgemm_variant_code):
 // tile 128 (8 or 16 warps) or 64 x unroll depth 16, 8, 4, all packed adds
 const int kVariants[9] = {108, 116, 104, 1108, 1116, 1104, 2108, 2116, 2104};
+
+bool known_variant(int v) {
+  for (int k : kVariants)
+    if (k == v) return true;
+  return false;
+}
 
 bool is_device(const void* p) {
   cudaPointerAttributes a;
@@ -105,7 +131,11 @@ int64_t tiles3_of_pivot(int nv, int j, int B) {
 }
 
 // Build the work list and device state of one batch and capture its graph.
-ps_status build_batch(ps_ctx* h, const ps_problem* probs, int n, int variant, CachedBatch* cb) {
+// stall: testing aid (ps_config.test_batched_stall): problem 0's per-vector
+// sums target is raised by one block that does not exist, so the first
+// dependency wait on it runs out after the handle's wait limit.
+ps_status build_batch(ps_ctx* h, const ps_problem* probs, int n, int variant, CachedBatch* cb,
+                      bool stall = false) {
   const int B = mgemm_variant_of(variant)->tile;
   std::vector<BatchProb> bp(n);
   size_t off_S = 0, off_n2 = 0;
@@ -166,7 +196,7 @@ ps_status build_batch(ps_ctx* h, const ps_problem* probs, int n, int variant, Ca
     q.out = p.out;
     q.way = p.way;
     q.out_f64 = p.out_dtype == PS_F64;
-    q.nsum_blocks = (int)ceil_div(p.V.nv, 32);
+    q.nsum_blocks = (int)ceil_div(p.V.nv, 32) + ((stall && t == 0) ? 1 : 0);
     const int64_t T = ceil_div(p.V.nv, B);
     q.n2_tiles = p.way == 3 ? (int)(T * (T + 1) / 2) : 0;
   }
@@ -195,9 +225,33 @@ ps_status build_batch(ps_ctx* h, const ps_problem* probs, int n, int variant, Ca
   return PS_OK;
 }
 
+// Reads the launch's error flag; PS_ERR_TIMEOUT if a dependency wait ran out.
+ps_status graph_status(ps_ctx* h, const CachedBatch& cb, cudaStream_t st) {
+  int herr = 0;
+  PS_CUDA_TRY(h, cudaMemcpyAsync(&herr, cb.counters + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
+  PS_CUDA_TRY(h, cudaStreamSynchronize(st));
+  if (herr) return fail(h, PS_ERR_TIMEOUT, "batched launch: a dependency wait timed out");
+  return PS_OK;
+}
+
 ps_status run_graph(ps_ctx* h, const ps_problem* probs, int n, int variant, cudaStream_t st) {
   if (!h->batch) h->batch = new BatchState();
-  const uint64_t key = full_signature(probs, n, variant);
+  if (h->batched_stall) {
+    // one-off launch with the stalled dependency; not cached
+    h->batched_stall = 0;
+    h->cfg.test_batched_stall = 0;
+    CachedBatch cb;
+    ps_status s = build_batch(h, probs, n, variant, &cb, true);
+    if (s == PS_OK) {
+      const cudaError_t e = cudaGraphLaunch(cb.exec, st);
+      s = e == cudaSuccess ? graph_status(h, cb, st) : cuda_fail(h, e, "cudaGraphLaunch");
+    }
+    cudaStreamSynchronize(st);
+    if (cb.exec) cudaGraphExecDestroy(cb.exec);
+    if (cb.mem) cudaFree(cb.mem);
+    return s;
+  }
+  const uint64_t key = full_signature(probs, n, variant, h->wait_ns);
   auto it = h->batch->graphs.find(key);
   if (it == h->batch->graphs.end()) {
     CachedBatch cb;
@@ -213,11 +267,7 @@ ps_status run_graph(ps_ctx* h, const ps_problem* probs, int n, int variant, cuda
     ScopedTimer tm(h, "batched", st);
     PS_CUDA_TRY(h, cudaGraphLaunch(it->second.exec, st));
   }
-  int herr = 0;
-  PS_CUDA_TRY(h, cudaMemcpyAsync(&herr, it->second.counters + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
-  PS_CUDA_TRY(h, cudaStreamSynchronize(st));
-  if (herr) return fail(h, PS_ERR_TIMEOUT, "batched launch: a dependency wait timed out");
-  return PS_OK;
+  return graph_status(h, it->second, st);
 }
 
 int default_variant(ps_ctx* h) { return mgemm_variant_code(h); }
@@ -247,6 +297,8 @@ extern "C" ps_status ps_metrics_batched(ps_handle h, const ps_problem* probs, in
   cudaGetDevice(&prev);
   if (prev != h->device) cudaSetDevice(h->device);
   ps_status s = check_problems(h, probs, n);
+  if (s == PS_OK && wants_fp64(h))
+    s = fail(h, PS_ERR_UNSUPPORTED, "ps_metrics_batched has no FP64 kernel (handle precision is PS_PATH_FP64)");
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   if (s == PS_OK) {
     if (mode == PS_BATCH_PER_INSTANCE) {
@@ -258,10 +310,23 @@ extern "C" ps_status ps_metrics_batched(ps_handle h, const ps_problem* probs, in
                               stream);
       }
     } else {
+      // the handle's own tuning, else the configured autotune cache, else
+      // the default variant
       int variant = default_variant(h);
+      const uint64_t sig = shape_signature(probs, n);
+      bool tuned = false;
       if (h->batch) {
-        auto it = h->batch->tuned.find(shape_signature(probs, n));
-        if (it != h->batch->tuned.end()) variant = it->second;
+        auto it = h->batch->tuned.find(sig);
+        if (it != h->batch->tuned.end()) {
+          variant = it->second;
+          tuned = true;
+        }
+      }
+      if (!tuned && !h->cache_path.empty()) {
+        char sigs[32];
+        snprintf(sigs, sizeof(sigs), "%016llx", (unsigned long long)sig);
+        const int v = cached_variant(h->cache_path.c_str(), sigs);
+        if (known_variant(v)) variant = v;
       }
       s = run_graph(h, probs, n, variant, st);
     }
@@ -280,19 +345,11 @@ extern "C" ps_status ps_autotune_batched(ps_handle h, const ps_problem* probs, i
   const uint64_t sig = shape_signature(probs, n);
   char sigs[32];
   snprintf(sigs, sizeof(sigs), "%016llx", (unsigned long long)sig);
-  int best = -1;
-  // a cache hit skips the measurement
-  if (cache_path) {
-    if (FILE* f = fopen(cache_path, "r")) {
-      char line[1024];
-      while (fgets(line, sizeof(line), f)) {
-        const char* p = strstr(line, sigs);
-        const char* v = strstr(line, "\"variant\": ");
-        if (p && v) best = atoi(v + 11);
-      }
-      fclose(f);
-    }
-  }
+  // the call's cache path, else the handle's configured one; a cache hit
+  // skips the measurement
+  if (!cache_path && !h->cache_path.empty()) cache_path = h->cache_path.c_str();
+  int best = cached_variant(cache_path, sigs);
+  if (!known_variant(best)) best = -1;
   std::string detail;
   if (best < 0) {
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
@@ -322,7 +379,7 @@ extern "C" ps_status ps_autotune_batched(ps_handle h, const ps_problem* probs, i
       }
       // keep only the graph of the winner so far
       for (auto it = h->batch->graphs.begin(); it != h->batch->graphs.end();) {
-        if (it->first == full_signature(probs, n, vc) && vc != best) {
+        if (it->first == full_signature(probs, n, vc, h->wait_ns) && vc != best) {
           cudaGraphExecDestroy(it->second.exec);
           cudaFree(it->second.mem);
           it = h->batch->graphs.erase(it);

@@ -17,13 +17,13 @@ constexpr int DBM = 64, DBK = 16;
 __global__ void __launch_bounds__(256)
     mgemm2_f64_kernel(const double* __restrict__ X, int64_t ld, int nv, int nf,
                       const double* __restrict__ S, void* __restrict__ out, int out_f64, int T,
-                      int64_t ntiles) {
+                      int64_t tbase, int64_t ntiles) {
   __shared__ double As[DBK][DBM];
   __shared__ double Bs[DBK][DBM];
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
     int I, J;
-    mg::tri_tile(t, T, I, J);
+    mg::tri_tile(tbase + t, T, I, J);
     const int row0 = I * DBM, col0 = J * DBM;
     double acc[4][4] = {};
     for (int k0 = 0; k0 < nf; k0 += DBK) {
@@ -282,7 +282,7 @@ cudaError_t launch_batched(ps_ctx* h, int code, const BatchProb* probs, int npro
   if (e != cudaSuccess) return e;
   if (nitems == 0) return cudaSuccess;
   const unsigned grid = (unsigned)std::min<int64_t>(nitems, (int64_t)h->num_sms * v->minb);
-  v->batched(grid, st, probs, nprob, items, nitems, counters);
+  v->batched(grid, st, probs, nprob, items, nitems, counters, h->wait_ns);
   return cudaGetLastError();
 }
 
@@ -293,12 +293,17 @@ cudaError_t launch_mgemm3_thresh(ps_ctx* h, const VF32& V, const double* S, cons
 }
 
 cudaError_t launch_mgemm2_f64(ps_ctx* h, const double* X, int64_t ld, int nv, int nf,
-                              const double* S, void* out, int out_f64, cudaStream_t st) {
+                              const double* S, void* out, int out_f64, cudaStream_t st, int64_t row_begin,
+                              int64_t row_end) {
   const int T = (int)ceil_div(nv, DBM);
-  const int64_t ntiles = (int64_t)T * (T + 1) / 2;
-  if (ntiles == 0) return cudaSuccess;
+  // tile rows [I0, I1) of the 64-wide triangle; tiles in rows [0, I): I*T - I(I-1)/2
+  const int64_t I0 = std::max<int64_t>(0, row_begin) / DBM;
+  const int64_t I1 = row_end < 0 ? T : std::min<int64_t>(T, ceil_div(row_end, DBM));
+  if (I1 <= I0) return cudaSuccess;
+  const int64_t tbase = I0 * T - I0 * (I0 - 1) / 2;
+  const int64_t ntiles = (I1 * T - I1 * (I1 - 1) / 2) - tbase;
   const int64_t grid = std::min<int64_t>(ntiles, (int64_t)h->num_sms * 4);
-  mgemm2_f64_kernel<<<(unsigned)grid, 256, 0, st>>>(X, ld, nv, nf, S, out, out_f64, T, ntiles);
+  mgemm2_f64_kernel<<<(unsigned)grid, 256, 0, st>>>(X, ld, nv, nf, S, out, out_f64, T, tbase, ntiles);
   return cudaGetLastError();
 }
 

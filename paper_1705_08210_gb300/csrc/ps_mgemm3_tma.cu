@@ -62,7 +62,9 @@ struct __align__(128) Smem3 {
   float B[STAGES][BK][C::BN];  // column panel
   float P[STAGES][BK][PBOX];   // pivot column: v_j at [kk][j % 4]
   int pcol[STAGES];            // j % 4 of the slice's pivot (written by the producer)
+  int tile_of[STAGES];         // counter schedule: work item of local item lt at [lt % STAGES], -1 = none
   int2 pitem;                  // the producer's current work item
+  int p_done;                  // counter schedule: the producer has issued the end marker
   unsigned long long full[STAGES];
   unsigned long long ready[STAGES];
   unsigned long long empty[STAGES];
@@ -90,12 +92,12 @@ __device__ __forceinline__ void item3(int2 w, int& j, int& row0, int& col0) {
   col0 = (w.y & 0xffff) * C::BN;
 }
 
-template <int BK, int STAGES, int KU>
+template <int BK, int STAGES, int KU, bool DYN>
 __global__ void __launch_bounds__(C::NT, 1)
     mgemm3_tma_kernel(const __grid_constant__ CUtensorMap mapV, const __grid_constant__ CUtensorMap mapP,
                       int nv, int nf, const double* __restrict__ S, const float* __restrict__ n2sq,
                       const int2* __restrict__ items, int jb, float* __restrict__ out, int64_t ntiles,
-                      int* err) {
+                      int* err, unsigned long long* __restrict__ item_ctr, unsigned long long wait_ns) {
   static_assert(mg::FOLD * mg::BK % BK == 0 && BK % NW == 0, "slice shape");
   constexpr int FOLD_SLICES = mg::FOLD * mg::BK / BK;
   constexpr int ROWS_PER_WARP = BK / NW;  // field rows of a slice each warp min-s with the pivot
@@ -110,12 +112,25 @@ __global__ void __launch_bounds__(C::NT, 1)
       sy::bar_init(&sm.empty[s], NW);
     }
     sm.abort = 0;
+    sm.p_done = 0;
     sy::bar_init_fence();
   }
   __syncthreads();
   const int nkb = (nf + BK - 1) / BK;
+  // Work schedule.  Static (DYN false): this CTA's items are blockIdx.x,
+  // blockIdx.x + gridDim.x, ...  Counter (DYN true): the producer claims the
+  // next item from the grid-wide counter when it loads the item's first
+  // slice, after that slice's ring stage is free, and hands the item index
+  // to the warps in tile_of[lt % STAGES], published by the stage's full
+  // barrier; a claim past the end publishes -1 with a plain arrival (no
+  // copies), which stops the warps.  Entry lt % STAGES is rewritten only
+  // when item lt + STAGES is claimed, which waits for every warp to release
+  // slice (lt + STAGES) nkb - STAGES >= lt nkb, so every warp has read the
+  // entry of item lt by then.  The warps read nothing else the producer
+  // rewrites per item: the epilogue reads its item from the global table.
   const int64_t my_tiles = ntiles > blockIdx.x ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
-  const uint32_t n_slices = (uint32_t)(my_tiles * nkb);  // < 2^32 (checked by the launcher)
+  // slices of this CTA (< 2^32, checked by the launcher); unbounded with DYN
+  const uint32_t n_slices = DYN ? 0xffffffffu : (uint32_t)(my_tiles * nkb);
 
   // producer (lane 0 of warp 0): loads slice g (waiting until its ring
   // stage is free); false on abort.  Its work item is kept in shared memory
@@ -123,14 +138,26 @@ __global__ void __launch_bounds__(C::NT, 1)
   const bool producer = threadIdx.x == 0;
   auto issue_one = [&](uint32_t g) -> bool {
     Smem3<BK, STAGES>& sm = *reinterpret_cast<Smem3<BK, STAGES>*>(smem_raw);
-    if (g >= n_slices) return true;
+    if (g >= n_slices || (DYN && sm.p_done)) return true;
     const int s = (int)(g % STAGES);
     const uint32_t ph = (g / STAGES) & 1u;
     const int kb = (int)(g % (uint32_t)nkb);
-    if (kb == 0) sm.pitem = items[blockIdx.x + (int64_t)(g / nkb) * gridDim.x];
+    const uint32_t r = g / (uint32_t)nkb;  // this CTA's r-th item
+    if (!DYN && kb == 0) sm.pitem = items[blockIdx.x + (int64_t)r * gridDim.x];
+    if (!sy::bar_wait(&sm.empty[s], ph ^ 1u, &sm.abort, err, wait_ns)) return false;
+    if (DYN && kb == 0) {
+      const unsigned long long t = atomicAdd(item_ctr, 1ull);
+      if (t >= (unsigned long long)ntiles) {
+        sm.tile_of[r % STAGES] = -1;
+        sy::bar_arrive(&sm.full[s]);  // completes the phase with no copies
+        sm.p_done = 1;
+        return true;
+      }
+      sm.tile_of[r % STAGES] = (int)t;  // published by the arrival below
+      sm.pitem = items[t];
+    }
     int pj, prow0, pcol0;
     item3(sm.pitem, pj, prow0, pcol0);
-    if (!sy::bar_wait(&sm.empty[s], ph ^ 1u, &sm.abort, err)) return false;
     sm.pcol[s] = pj & (PBOX - 1);  // published by the arrival below
     sy::bar_arrive_tx(&sm.full[s], SLICE_BYTES);
     sy::tma_load_2d(&sm.A[s][0][0], &mapV, prow0, kb * BK, &sm.full[s]);
@@ -143,15 +170,17 @@ __global__ void __launch_bounds__(C::NT, 1)
       if (!issue_one(g)) break;
 
   // X_j = min(V, v_j) on this warp's field rows of slice g's row panel,
-  // then one arrival on the slice's `ready` barrier; false on abort
+  // then one arrival on the slice's `ready` barrier; false on abort.  (With
+  // DYN, the first slice of the end marker has nothing to prepare.)
   auto prepare = [&](uint32_t g) -> bool {
     // (the shared array itself, not the captured reference: through the
     // capture the compiler would emit generic loads and stores)
     Smem3<BK, STAGES>& sm = *reinterpret_cast<Smem3<BK, STAGES>*>(smem_raw);
     const int s = (int)(g % STAGES);
     const uint32_t ph = (g / STAGES) & 1u;
-    const bool landed = sy::bar_wait(&sm.full[s], ph, &sm.abort, err);
+    const bool landed = sy::bar_wait(&sm.full[s], ph, &sm.abort, err, wait_ns);
     if (!__all_sync(0xffffffffu, landed)) return false;
+    if (DYN && g % (uint32_t)nkb == 0 && sm.tile_of[(g / (uint32_t)nkb) % STAGES] < 0) return true;
     const int pc = sm.pcol[s];
 #pragma unroll
     for (int rr = 0; rr < ROWS_PER_WARP; ++rr) {
@@ -178,7 +207,15 @@ __global__ void __launch_bounds__(C::NT, 1)
   // slices are prepared one ahead of the compute, so that a warp waiting for
   // the other warps' rows of slice it waited a whole slice earlier
   bool ok = n_slices == 0 || prepare(0);
-  for (int64_t t = blockIdx.x; ok && t < ntiles; t += gridDim.x) {
+  for (int64_t lt = 0; ok; ++lt) {
+    int64_t t;
+    if (DYN) {
+      t = sm.tile_of[lt % STAGES];  // published by the full barrier prepare() waited on
+      if (t < 0) break;
+    } else {
+      t = blockIdx.x + lt * gridDim.x;
+      if (t >= ntiles) break;
+    }
     int j, row0, col0;
     item3(items[t], j, row0, col0);
     // a warp whose 64 x 16 block has no row i < j, no column k > j, or no
@@ -194,7 +231,7 @@ __global__ void __launch_bounds__(C::NT, 1)
       if (!ok) break;
       const int s = (int)(it % STAGES);
       const uint32_t ph = (it / STAGES) & 1u;
-      const bool prepared = sy::bar_wait(&sm.ready[s], ph, &sm.abort, err);
+      const bool prepared = sy::bar_wait(&sm.ready[s], ph, &sm.abort, err, wait_ns);
       if (!__all_sync(0xffffffffu, prepared)) { ok = false; break; }
       if (active) compute_slice3<BK, KU>(&sm.A[s][0][L.am], &sm.B[s][0][L.bn], acc);
       __syncwarp();
@@ -234,18 +271,18 @@ __global__ void __launch_bounds__(C::NT, 1)
 }
 
 // ---- host side ----
-template <int BK, int STAGES, int KU>
+template <int BK, int STAGES, int KU, bool DYN>
 struct Tma3Launch {
   static constexpr size_t smem = sizeof(Smem3<BK, STAGES>);
   static cudaError_t run(ps_ctx* h, const VF32& V, const double* S, const float* n2sq, const int2* items, int jb,
-                         float* out, int64_t ntiles, int* err, cudaStream_t st) {
+                         float* out, int64_t ntiles, int* err, unsigned long long* item_ctr, cudaStream_t st) {
     static std::mutex mu;
     static uint64_t attr_done = 0;
     {
       std::lock_guard<std::mutex> lk(mu);
       const uint64_t bit = 1ull << (h->device & 63);
       if (!(attr_done & bit)) {
-        const cudaError_t e = cudaFuncSetAttribute(mgemm3_tma_kernel<BK, STAGES, KU>,
+        const cudaError_t e = cudaFuncSetAttribute(mgemm3_tma_kernel<BK, STAGES, KU, DYN>,
                                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         attr_done |= bit;
@@ -255,9 +292,13 @@ struct Tma3Launch {
     if (!sy::make_map_f32(&mapV, V.p, V.nv, V.nf, V.ld, C::BM, BK) ||
         !sy::make_map_f32(&mapP, V.p, V.nv, V.nf, V.ld, PBOX, BK))
       return cudaErrorInvalidValue;
+    if (DYN) {
+      const cudaError_t e = cudaMemsetAsync(item_ctr, 0, sizeof(unsigned long long), st);
+      if (e != cudaSuccess) return e;
+    }
     const unsigned grid = (unsigned)std::min<int64_t>(ntiles, (int64_t)h->num_sms);
-    mgemm3_tma_kernel<BK, STAGES, KU><<<grid, C::NT, smem, st>>>(mapV, mapP, V.nv, V.nf, S, n2sq, items, jb,
-                                                                 out, ntiles, err);
+    mgemm3_tma_kernel<BK, STAGES, KU, DYN><<<grid, C::NT, smem, st>>>(mapV, mapP, V.nv, V.nf, S, n2sq, items, jb,
+                                                                      out, ntiles, err, item_ctr, h->wait_ns);
     return cudaGetLastError();
   }
 };
@@ -268,8 +309,9 @@ cudaError_t launch_mgemm3_tma(ps_ctx* h, const VF32& V, const double* S, const f
                               int jb, float* out, int64_t ntiles, int* err, cudaStream_t st) {
   // TMA: 16-byte aligned base and row pitch; 128-wide tiles
   if ((uintptr_t)V.p % 16 != 0 || V.ld % 4 != 0 || V.nv < 1) return cudaErrorInvalidValue;
-  // slices per CTA counted in 32 bits
-  if ((double)ceil_div(ntiles, h->num_sms) * (double)ceil_div(V.nf, 16) >= 4294967295.0)
+  // item indices in 31 bits, slices per CTA counted in 32 bits
+  if (ntiles >= ((int64_t)1 << 31) ||
+      (double)ceil_div(ntiles, h->num_sms) * (double)ceil_div(V.nf, 16) >= 4294967295.0)
     return cudaErrorInvalidValue;
   // slice width by n_f (a wider slice than n_f is mostly zero fill): 64
   // fields in 3 stages above 32 (2048 x 4096: 433.0 ms; 32 fields in 4
@@ -277,11 +319,21 @@ cudaError_t launch_mgemm3_tma(ps_ctx* h, const VF32& V, const double* S, const f
   // and releases are what a wider slice saves), 16 k-steps per unrolled
   // iteration (457.8 vs 463.5 ms with 8 at 32-field slices)
   const int bk = V.nf <= 16 ? 16 : (V.nf <= 32 ? 32 : (h->mgemm_tma_bk ? h->mgemm_tma_bk : 64));
-  if (bk == 16) return Tma3Launch<16, 8, 8>::run(h, V, S, n2sq, items, jb, out, ntiles, err, st);
-  if (bk == 64) return Tma3Launch<64, 3, 16>::run(h, V, S, n2sq, items, jb, out, ntiles, err, st);
-  if (h->mgemm_tma_ku == 8) return Tma3Launch<32, 4, 8>::run(h, V, S, n2sq, items, jb, out, ntiles, err, st);
-  if (h->mgemm_tma_stages == 3) return Tma3Launch<32, 3, 16>::run(h, V, S, n2sq, items, jb, out, ntiles, err, st);
-  return Tma3Launch<32, 4, 16>::run(h, V, S, n2sq, items, jb, out, ntiles, err, st);
+  // work items claimed from a grid-wide counter (default) or round-robin;
+  // the counter is its own word of the handle's counter slot (bytes 16..23;
+  // the 2-way kernel uses bytes 0..15) and is zeroed before each launch
+  unsigned* sync = static_cast<unsigned*>(ws_get(h, WS_SYNC, 256));
+  if (!sync) return cudaErrorMemoryAllocation;
+  unsigned long long* ctr = reinterpret_cast<unsigned long long*>(sync + 4);
+#define PS_TMA3_RUN(...)                                                                                 \
+  (h->mgemm3_dynamic ? Tma3Launch<__VA_ARGS__, true>::run(h, V, S, n2sq, items, jb, out, ntiles, err, ctr, st) \
+                     : Tma3Launch<__VA_ARGS__, false>::run(h, V, S, n2sq, items, jb, out, ntiles, err, ctr, st))
+  if (bk == 16) return PS_TMA3_RUN(16, 8, 8);
+  if (bk == 64) return PS_TMA3_RUN(64, 3, 16);
+  if (h->mgemm_tma_ku == 8) return PS_TMA3_RUN(32, 4, 8);
+  if (h->mgemm_tma_stages == 3) return PS_TMA3_RUN(32, 3, 16);
+  return PS_TMA3_RUN(32, 4, 16);
+#undef PS_TMA3_RUN
 }
 
 }  // namespace ps

@@ -834,8 +834,10 @@ __device__ __forceinline__ int ld_acquire(const int* p) {
   return v;
 }
 
-// Thread 0 waits until *ctr >= target (2 s limit); the CTA follows its verdict.
-__device__ __forceinline__ bool cta_wait_count(const int* ctr, int target, int* err, int* s_flag) {
+// Thread 0 waits until *ctr >= target (at most wait_ns of %globaltimer time,
+// or until another CTA's wait ran out); the CTA follows its verdict.
+__device__ __forceinline__ bool cta_wait_count(const int* ctr, int target, int* err, int* s_flag,
+                                               unsigned long long wait_ns) {
   if (threadIdx.x == 0) {
     int ok = 1;
     if (ld_acquire(ctr) < target) {
@@ -844,7 +846,7 @@ __device__ __forceinline__ bool cta_wait_count(const int* ctr, int target, int* 
       while (ld_acquire(ctr) < target) {
         unsigned long long t1;
         asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t1));
-        if (t1 - t0 > 2000000000ull || *(volatile int*)err) {
+        if (t1 - t0 > wait_ns || *(volatile int*)err) {
           atomicExch(err, 1);
           ok = 0;
           break;
@@ -871,7 +873,7 @@ __device__ __forceinline__ void cta_signal(int* ctr) {
 template <class C, bool PACKED, int KU>
 __global__ void __launch_bounds__(C::NT, C::MINB)
     batched_kernel(const BatchProb* __restrict__ probs, int nprob, const BatchItem* __restrict__ items,
-                   int nitems, int* __restrict__ counters) {
+                   int nitems, int* __restrict__ counters, unsigned long long wait_ns) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Smem<C>& sm = *reinterpret_cast<Smem<C>*>(smem_raw);
   __shared__ int s_item, s_flag;
@@ -917,7 +919,7 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
     if (w.kind == BK_TILE2 || w.kind == BK_N2) {
       const int row0 = w.a * C::BM, col0 = w.b * C::BN;
       tile_minsum<C, false, PACKED, KU>(sm, V, row0, col0, 0, L.am, L.bn, acc);
-      if (!cta_wait_count(&sums_done[w.prob], p.nsum_blocks, err, &s_flag)) continue;
+      if (!cta_wait_count(&sums_done[w.prob], p.nsum_blocks, err, &s_flag, wait_ns)) continue;
 #pragma unroll
       for (int r = 0; r < 8; ++r) {
         const int i = row0 + L.row(r);
@@ -959,7 +961,7 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
     // its sub-partition for the other warp (the pivot's partial row tile)
     tile_minsum<C, true, PACKED, KU>(sm, V, row0, col0, j, L.am, L.bn, acc,
                                      row0 + (int)(threadIdx.x >> 5) / C::WN * 64 < j);
-    if (!cta_wait_count(&n2_done[w.prob], p.n2_tiles, err, &s_flag)) continue;
+    if (!cta_wait_count(&n2_done[w.prob], p.n2_tiles, err, &s_flag, wait_ns)) continue;
     const int64_t wdt = nv - 1 - j;
     const int64_t base = slab_offset(nv, 0, j);
     const float Sj = (float)__ldcg(p.S + j);
@@ -1009,8 +1011,8 @@ struct Launch {
                                                             ntiles);
   }
   static void batched(unsigned grid, cudaStream_t st, const BatchProb* probs, int nprob,
-                      const BatchItem* items, int nitems, int* counters) {
-    batched_kernel<C, PACKED, KU><<<grid, C::NT, smem, st>>>(probs, nprob, items, nitems, counters);
+                      const BatchItem* items, int nitems, int* counters, unsigned long long wait_ns) {
+    batched_kernel<C, PACKED, KU><<<grid, C::NT, smem, st>>>(probs, nprob, items, nitems, counters, wait_ns);
   }
 };
 

@@ -64,7 +64,7 @@ __global__ void __launch_bounds__(C::NT, 1)
     mgemm2_tma_kernel(const __grid_constant__ CUtensorMap mapV, int nv, int nf,
                       const double* __restrict__ S, void* __restrict__ out, int mode, int T, int R0,
                       int R1, int G, int64_t ntiles, int* err, unsigned* __restrict__ sync, int sync_sl,
-                      unsigned long long* __restrict__ tile_ctr) {
+                      unsigned long long* __restrict__ tile_ctr, unsigned long long wait_ns) {
   static_assert(mg::FOLD * mg::BK % BK == 0, "a fold boundary ends a slice");
   constexpr int FOLD_SLICES = mg::FOLD * mg::BK / BK;  // 64 fields per compensated fold
   constexpr uint32_t SLICE_BYTES = 2u * BK * C::BM * sizeof(float);
@@ -124,9 +124,9 @@ __global__ void __launch_bounds__(C::NT, 1)
       // CTAs holding a tile in round r, and the chunks issued before this one
       const int64_t P = min((int64_t)gridDim.x, ntiles - (int64_t)r * gridDim.x);
       const unsigned need = (unsigned)((int64_t)r * cpt * gridDim.x + (int64_t)(kb / sync_sl) * P);
-      if (!sy::counter_wait(sync, need, &sm.abort, err)) return false;
+      if (!sy::counter_wait(sync, need, &sm.abort, err, wait_ns)) return false;
     }
-    if (!sy::bar_wait(&sm.empty[s], ph ^ 1u, &sm.abort, err)) return false;
+    if (!sy::bar_wait(&sm.empty[s], ph ^ 1u, &sm.abort, err, wait_ns)) return false;
     if (dyn && kb == 0) {
       // (the stage being free means every warp has read tile_of of tile r - STAGES)
       const unsigned long long t = atomicAdd(tile_ctr, 1ull);
@@ -167,7 +167,7 @@ __global__ void __launch_bounds__(C::NT, 1)
       const uint32_t ph = (it / STAGES) & 1u;
       // every lane waits (each gets the barrier's acquire); the warp follows
       // the common verdict so that it never diverges here
-      const bool mine = ok && sy::bar_wait(&sm.full[s], ph, &sm.abort, err);
+      const bool mine = ok && sy::bar_wait(&sm.full[s], ph, &sm.abort, err, wait_ns);
       if (!__all_sync(0xffffffffu, mine)) { ok = false; break; }
       if (dyn && kb == 0) {
         t = sm.tile_of[lt % STAGES];
@@ -228,7 +228,7 @@ struct TmaLaunch {
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, mgemm2_tma_kernel<BK, STAGES, KU, FASTDIV, DYN>, map, (int)V.nv, (int)V.nf, S, out,
-                              mode, T, R0, R1, G, ntiles, err, sync, sync_sl, tile_ctr);
+                              mode, T, R0, R1, G, ntiles, err, sync, sync_sl, tile_ctr, h->wait_ns);
   }
 };
 

@@ -164,6 +164,26 @@ __global__ void pack_half2_kernel(VF32 V, const unsigned* __restrict__ mx, uint3
   }
 }
 
+
+// Entries that break the paper's precondition v >= 0 (Section 2.1) or are not
+// finite: negative, NaN or infinite.  Logical index t = q * nv + i walks the
+// matrix in either layout; one atomic per warp.
+template <typename T>
+__global__ void __launch_bounds__(256) count_invalid(const T* __restrict__ X, int64_t ld, int64_t nv,
+                                                     int64_t nf, int field_major,
+                                                     unsigned long long* __restrict__ bad) {
+  const int64_t total = nv * nf;
+  unsigned long long c = 0;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t q = t / nv, i = t - q * nv;
+    const double x = (double)__ldg(X + (field_major ? i + q * ld : q + i * ld));
+    c += !(x >= 0.0 && x <= 1.7976931348623157e308);  // false for NaN, -0.0 passes
+  }
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+  if ((threadIdx.x & 31) == 0 && c) atomicAdd(bad, c);
+}
+
 }  // namespace
 
 cudaError_t launch_pack_half2(const VF32& V, uint32_t* out, int64_t ldo, unsigned* mx, float* inv_scale,
@@ -175,6 +195,18 @@ cudaError_t launch_pack_half2(const VF32& V, uint32_t* out, int64_t ldo, unsigne
   const int64_t total = (int64_t)np * ldo;
   pack_half2_kernel<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(total, 256), 152 * 32)), 256,
                       0, st>>>(V, mx, out, ldo, np, inv_scale);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_count_invalid(const ps_matrix& V, unsigned long long* bad, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(bad, 0, sizeof(unsigned long long), st);
+  if (e != cudaSuccess || V.nv <= 0 || V.nf <= 0 || V.dtype == PS_B1) return e;
+  const unsigned grid = (unsigned)std::min<int64_t>(ceil_div(V.nv * V.nf, 256), 152 * 32);
+  const int fm = V.layout == PS_LAYOUT_FIELD_MAJOR;
+  if (V.dtype == PS_F32)
+    count_invalid<float><<<grid, 256, 0, st>>>((const float*)V.data, V.ld, V.nv, V.nf, fm, bad);
+  else
+    count_invalid<double><<<grid, 256, 0, st>>>((const double*)V.data, V.ld, V.nv, V.nf, fm, bad);
   return cudaGetLastError();
 }
 

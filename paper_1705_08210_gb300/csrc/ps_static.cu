@@ -19,8 +19,6 @@
 // different host threads) race on the array: serialise them.
 #include "ps_internal.cuh"
 
-#include <mutex>
-
 namespace ps {
 namespace {
 
@@ -29,23 +27,18 @@ constexpr int64_t kStaticMaxNv = 65536;  // = PS_STATIC_MAX_NV in ps.h
 // Scratch of the no-allocation entry point: per-vector FP64 sums.
 static __device__ __align__(256) double g_static_sums[kStaticMaxNv];
 
-std::mutex g_static_mu;
-constexpr int kMaxDevices = 64;
-double* g_static_addr[kMaxDevices] = {};  // device address of g_static_sums, per device
-
-// Set-up, once per device, with that device current: in host code the name
-// g_static_sums is only a host-side stand-in, so the kernels get the device
-// address returned by cudaGetSymbolAddress.
-cudaError_t static_sums_address(int dev, double** out) {
-  std::lock_guard<std::mutex> lk(g_static_mu);
-  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-  if (!g_static_addr[dev]) {
-    void* p = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&p, g_static_sums);
-    if (e != cudaSuccess) return e;
-    g_static_addr[dev] = static_cast<double*>(p);
-  }
-  *out = g_static_addr[dev];
+// Device address of g_static_sums on the current device.  In host code the
+// name g_static_sums is only a host-side stand-in, so the kernels get the
+// address cudaGetSymbolAddress returns.  It is looked up on every call (a
+// host-side query that allocates nothing), so a context that was torn down
+// and created again, which may load the module at another address, never
+// receives a stale pointer.  The first lookup on a device loads the module
+// there; make that first call before any stream capture.
+cudaError_t static_sums_address(double** out) {
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_static_sums);
+  if (e != cudaSuccess) return e;
+  *out = static_cast<double*>(p);
   return cudaSuccess;
 }
 
@@ -92,11 +85,14 @@ extern "C" ps_status ps_metrics_2way_static(const ps_matrix* V, void* out, int32
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cuda_fail(nullptr, e, "cudaGetDevice");
   double* S = nullptr;
-  e = static_sums_address(dev, &S);
+  e = static_sums_address(&S);
   if (e != cudaSuccess) return cuda_fail(nullptr, e, "cudaGetSymbolAddress(g_static_sums)");
-  ps_ctx ctx;  // stack context: no workspace is touched by the calls below
+  // stack context with the default configuration: no workspace is touched by
+  // the calls below; the 16-warp 128 x 128 cp.async kernel (it needs no
+  // error word) gives the same values as the default TMA-fed kernel
+  ps_ctx ctx;
   ctx.device = dev;
-  ctx.mgemm_feed_tma = 0;  // the cp.async kernel: it needs no error word
+  ctx.mgemm_feed_tma = 0;
   e = cudaDeviceGetAttribute(&ctx.num_sms, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return cuda_fail(nullptr, e, "cudaDeviceGetAttribute");
 

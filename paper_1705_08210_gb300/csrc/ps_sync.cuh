@@ -1,9 +1,10 @@
 // ps_sync.cuh -- shared-memory mbarriers, tensor-memory-accelerator (TMA)
 // tile loads and bounded waits for the warp-specialised kernels.
 //
-// Every wait here is bounded: after PS_SYNC_WAIT_NS of %globaltimer time the
-// waiter raises the CTA's abort word and a device error flag and gives up,
-// so a lost copy cannot hang the GPU.
+// Every wait here is bounded: after `limit_ns` of %globaltimer time (the
+// handle's wait_limit_ns, 2 s by default) the waiter raises the CTA's abort
+// word and a device error flag and gives up, so a lost copy cannot hang the
+// GPU.
 #pragma once
 
 #include <cuda.h>
@@ -12,8 +13,6 @@
 
 namespace ps {
 namespace sy {
-
-constexpr unsigned long long PS_SYNC_WAIT_NS = 2000000000ull;  // 2 s per wait
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -60,16 +59,16 @@ __device__ __forceinline__ bool bar_test(unsigned long long* b, uint32_t parity)
 
 // Wait for the completion of the barrier phase with `parity`.  Returns false
 // when the CTA is aborting (abort word set by another waiter) or when this
-// wait passed the time limit (then it sets the abort word and *err).
+// wait passed `limit_ns` (then it sets the abort word and *err).
 __device__ __forceinline__ bool bar_wait(unsigned long long* b, uint32_t parity, int* abort_word,
-                                         int* err) {
+                                         int* err, unsigned long long limit_ns) {
   if (bar_test(b, parity)) return true;
   const unsigned long long t0 = now_ns();
   for (uint32_t it = 1;; ++it) {
     if (bar_test(b, parity)) return true;
     if ((it & 31) == 0) {
       if (*(volatile int*)abort_word) return false;
-      if (now_ns() - t0 > PS_SYNC_WAIT_NS) {
+      if (now_ns() - t0 > limit_ns) {
         *(volatile int*)abort_word = 1;
         if (err) {
           atomicExch(err, 1);
@@ -83,9 +82,9 @@ __device__ __forceinline__ bool bar_wait(unsigned long long* b, uint32_t parity,
 
 // Wait until the grid-wide counter *c reaches `need` (relaxed loads: the
 // counter only paces the producers, it guards no data).  False when the CTA
-// is aborting or the time limit passed (then it sets the abort word and
-// *err).
-__device__ __forceinline__ bool counter_wait(const unsigned* c, unsigned need, int* abort_word, int* err) {
+// is aborting or `limit_ns` passed (then it sets the abort word and *err).
+__device__ __forceinline__ bool counter_wait(const unsigned* c, unsigned need, int* abort_word, int* err,
+                                             unsigned long long limit_ns) {
   auto load = [c]() {
     unsigned v;
     asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(c) : "memory");
@@ -97,7 +96,7 @@ __device__ __forceinline__ bool counter_wait(const unsigned* c, unsigned need, i
     __nanosleep(64);
     if (load() >= need) return true;
     if (*(volatile int*)abort_word) return false;
-    if (now_ns() - t0 > PS_SYNC_WAIT_NS) {
+    if (now_ns() - t0 > limit_ns) {
       *(volatile int*)abort_word = 1;
       if (err) {
         atomicExch(err, 1);
@@ -121,7 +120,8 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
 }
 
 // After an abort: keep the CTA (and its shared memory) alive for 1 ms so
-// that copies already issued land before the memory is released.
+// that copies (and tensor-core operations) already issued land before the
+// memory is released.
 __device__ __forceinline__ void drain_after_abort() {
   const unsigned long long t0 = now_ns();
   while (now_ns() - t0 < 1000000ull) {
@@ -147,6 +147,22 @@ inline EncodeTiledFn encode_tiled_fn() {
     return f;
   }();
   return fn;
+}
+
+// 2-D byte matrix (rows of `pitch` bytes, `cols` valid bytes per row) as a
+// tensor with boxes of box_cols x box_rows bytes and the 128-byte swizzle
+// (the K-major tensor-core operand layout); zero fill outside.
+inline bool make_map_u8_sw128(CUtensorMap* m, const void* p, int64_t cols, int64_t rows, int64_t pitch,
+                              int box_cols, int box_rows) {
+  EncodeTiledFn enc = encode_tiled_fn();
+  if (!enc) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)pitch};
+  const cuuint32_t box[2] = {(cuuint32_t)box_cols, (cuuint32_t)box_rows};
+  const cuuint32_t estr[2] = {1, 1};
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<void*>(p), dims, strides, box, estr,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 // Field-major FP32 matrix (element (i, q) at p[i + q ld]) as a 2-D tensor:

@@ -34,9 +34,11 @@
 // `sync_kb` k-blocks (cooperative launch: all CTAs are resident): a producer
 // does not issue chunk m of its round-r tile before every CTA has issued all
 // earlier chunks.
-// Every mbarrier and counter wait is bounded (PS_WAIT_NS); on timeout the CTA
-// raises `err`, lets in-flight copies drain, frees its TMEM and returns.
+// Every mbarrier and counter wait is bounded (the handle's wait limit,
+// ps_sync.cuh); on timeout the CTA raises `err`, lets in-flight copies drain,
+// frees its TMEM and returns.
 #include "ps_internal.cuh"
+#include "ps_sync.cuh"
 
 #include <cuda.h>
 
@@ -50,7 +52,6 @@ namespace {
 constexpr int TN = 256, TKB = 128;  // tile columns, K bytes per stage
 constexpr int NTHREADS = 192;
 constexpr uint32_t TMEM_COLS = 512;
-constexpr unsigned long long PS_WAIT_NS = 2000000000ull;  // 2 s per wait
 
 // MH M=128 halves per CTA tile: MH = 1 -> 128 x 256 tile, 4 stages of 48 KB,
 // two 256-column accumulators (epilogue overlaps the next tile); MH = 2 ->
@@ -77,65 +78,7 @@ struct __align__(1024) SmemTC {
   int abort;
 };
 
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ unsigned long long globaltimer() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
-  return t;
-}
-
-__device__ __forceinline__ void mbar_init(unsigned long long* b, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(unsigned long long* b) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b)) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long* b, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)),
-               "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(unsigned long long* b, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(smem_u32(b)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-// Bounded wait: true when the phase with `parity` completed; false when the
-// CTA is aborting or the time limit passed (then the abort flag is raised).
-template <class SM>
-__device__ __forceinline__ bool mbar_wait(SM& sm, unsigned long long* b, uint32_t parity,
-                                          int* err) {
-  if (mbar_try_wait(b, parity)) return true;
-  const unsigned long long t0 = globaltimer();
-  for (uint32_t it = 0;; ++it) {
-    if (mbar_try_wait(b, parity)) return true;
-    if ((it & 63) == 0) {
-      if (*(volatile int*)&sm.abort) return false;
-      if (globaltimer() - t0 > PS_WAIT_NS) {
-        *(volatile int*)&sm.abort = 1;
-        atomicExch(err, 1);
-        return false;
-      }
-    }
-  }
-}
-
-__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y,
-                                            unsigned long long* bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, "
-      "%3}], [%4];" ::"r"(smem_u32(dst)),
-      "l"(map), "r"(x), "r"(y), "r"(smem_u32(bar))
-      : "memory");
-}
+using sy::smem_addr;
 
 // UMMA shared-memory descriptor, K-major operand written by TMA with the
 // 128-byte swizzle: 8-row x 128-byte atoms, 1024 bytes apart (SBO).
@@ -164,7 +107,7 @@ __device__ __forceinline__ void umma_f8(uint32_t tmem_d, uint64_t ad, uint64_t b
 }
 __device__ __forceinline__ void umma_commit(unsigned long long* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                   smem_u32(bar))
+                   smem_addr(bar))
                : "memory");
 }
 __device__ __forceinline__ void tc_fence_before() {
@@ -190,28 +133,6 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
   for (int t = 0; t < 32; ++t) v[t] = __uint_as_float(r[t]);
-}
-
-// Bounded wait until the grid-wide chunk counter reaches `need`.
-template <class SM>
-__device__ __forceinline__ bool counter_wait(SM& sm, const unsigned* c, unsigned need, int* err) {
-  auto load = [c]() {
-    unsigned v;
-    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(c) : "memory");
-    return v;
-  };
-  if (load() >= need) return true;
-  const unsigned long long t0 = globaltimer();
-  for (;;) {
-    __nanosleep(32);
-    if (load() >= need) return true;
-    if (*(volatile int*)&sm.abort) return false;
-    if (globaltimer() - t0 > PS_WAIT_NS) {
-      *(volatile int*)&sm.abort = 1;
-      atomicExch(err, 1);
-      return false;
-    }
-  }
 }
 
 // Tile walk: every (I, J) with I*TM < (J+1)*TN (some i < j in the tile),
@@ -240,7 +161,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                        const __grid_constant__ CUtensorMap mapB, int nkb, int nv,
                        const int2* __restrict__ tiles, int64_t ntiles, const int* __restrict__ SQ,
                        void* __restrict__ out, int out_mode, int* __restrict__ err,
-                       unsigned* __restrict__ sync, int sync_kb) {
+                       unsigned* __restrict__ sync, int sync_kb, unsigned long long wait_ns) {
   extern __shared__ unsigned char smem_raw[];
   using CF = TCfg<MH>;
   constexpr int TM = CF::TM, TSTAGES = CF::STAGES, A_BYTES = CF::A_BYTES, B_BYTES = CF::B_BYTES;
@@ -250,20 +171,19 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < TSTAGES; ++s) {
-      mbar_init(&sm.full[s], 1);
-      mbar_init(&sm.empty[s], 1);
+      sy::bar_init(&sm.full[s], 1);
+      sy::bar_init(&sm.empty[s], 1);
     }
     for (int a = 0; a < 2; ++a) {
-      mbar_init(&sm.tfull[a], 1);
-      mbar_init(&sm.tempty[a], 128);
+      sy::bar_init(&sm.tfull[a], 1);
+      sy::bar_init(&sm.tempty[a], 128);
     }
     sm.abort = 0;
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    sy::bar_init_fence();
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                     smem_u32(&sm.tmem_base)),
+                     smem_addr(&sm.tmem_base)),
                  "r"(TMEM_COLS)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
@@ -288,12 +208,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           if (cpt && kb % sync_kb == 0 && (r | kb) != 0) {
             // chunks issued before chunk kb/sync_kb of round r, over all CTAs
             const unsigned need = (unsigned)r * cpt * gridDim.x + (unsigned)(kb / sync_kb) * P;
-            if (!counter_wait(sm, sync, need, err)) { ok = false; break; }
+            if (!sy::counter_wait(sync, need, &sm.abort, err, wait_ns)) { ok = false; break; }
           }
-          if (!mbar_wait(sm, &sm.empty[stage], phase ^ 1, err)) { ok = false; break; }
-          mbar_arrive_expect_tx(&sm.full[stage], A_BYTES + B_BYTES);
-          tma_load_2d(sm.A[stage], &mapA, kb * TKB, I * TM, &sm.full[stage]);
-          tma_load_2d(sm.B[stage], &mapB, kb * TKB, J * TN, &sm.full[stage]);
+          if (!sy::bar_wait(&sm.empty[stage], phase ^ 1, &sm.abort, err, wait_ns)) { ok = false; break; }
+          sy::bar_arrive_tx(&sm.full[stage], A_BYTES + B_BYTES);
+          sy::tma_load_2d(sm.A[stage], &mapA, kb * TKB, I * TM, &sm.full[stage]);
+          sy::tma_load_2d(sm.B[stage], &mapB, kb * TKB, J * TN, &sm.full[stage]);
           if (++stage == TSTAGES) { stage = 0; phase ^= 1; }
           if (cpt && ((kb + 1) % sync_kb == 0 || kb + 1 == nkb)) atomicAdd(sync, 1u);
         }
@@ -308,13 +228,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       uint32_t aphase = 0;
       bool ok = true;
       for (int64_t t = blockIdx.x; ok && t < ntiles; t += gridDim.x) {
-        if (!mbar_wait(sm, &sm.tempty[acc], aphase ^ 1, err)) break;
+        if (!sy::bar_wait(&sm.tempty[acc], aphase ^ 1, &sm.abort, err, wait_ns)) break;
         tc_fence_after();
         const uint32_t dcol = tmem + (uint32_t)(acc * MH * TN);
         for (int kb = 0; kb < nkb; ++kb) {
-          if (!mbar_wait(sm, &sm.full[stage], phase, err)) { ok = false; break; }
+          if (!sy::bar_wait(&sm.full[stage], phase, &sm.abort, err, wait_ns)) { ok = false; break; }
           tc_fence_after();
-          const uint32_t a0 = smem_u32(sm.A[stage]), b0 = smem_u32(sm.B[stage]);
+          const uint32_t a0 = smem_addr(sm.A[stage]), b0 = smem_addr(sm.B[stage]);
 #pragma unroll
           for (int kk = 0; kk < TKB / 32; ++kk)
 #pragma unroll
@@ -339,7 +259,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       const int I = tiles[t].x, J = tiles[t].y;
       // warp-uniform wait: lane 0 polls, the warp follows its verdict
       int ok = 0;
-      if (lane == 0) ok = mbar_wait(sm, &sm.tfull[acc], aphase, err) ? 1 : 0;
+      if (lane == 0) ok = sy::bar_wait(&sm.tfull[acc], aphase, &sm.abort, err, wait_ns) ? 1 : 0;
       ok = __shfl_sync(0xffffffffu, ok, 0);
       if (!ok) break;
       tc_fence_after();
@@ -379,17 +299,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         }
       }
       tc_fence_before();
-      mbar_arrive(&sm.tempty[acc]);
+      sy::bar_arrive(&sm.tempty[acc]);
       if (++acc == CF::ACC_SETS) { acc = 0; aphase ^= 1; }
     }
   }
   __syncthreads();
-  if (*(volatile int*)&sm.abort) {
-    // let copies and MMAs already issued finish before the memory goes away
-    const unsigned long long t0 = globaltimer();
-    while (globaltimer() - t0 < 1000000ull) {
-    }
-  }
+  // let copies and MMAs already issued finish before the memory goes away
+  if (*(volatile int*)&sm.abort) sy::drain_after_abort();
   tc_fence_after();
   if (warp == 1)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
@@ -397,37 +313,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                  : "memory");
 }
 
-// ---- host: tensor maps through the driver entry point ----
-using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
-                                   const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
-                                   const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
-                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-EncodeTiledFn get_encode_fn() {
-  static EncodeTiledFn fn = nullptr;
-  static std::once_flag once;
-  std::call_once(once, [] {
-    void* p = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
-                                         &q) == cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<EncodeTiledFn>(p);
-    cudaGetLastError();
-  });
-  return fn;
-}
-
+// ---- host ----
+// T (rows x Kpad bytes) as a tensor with TKB x box_rows boxes, 128-byte swizzle
 bool make_map(CUtensorMap* m, const uint8_t* T, int64_t Kpad, int rows, int box_rows) {
-  EncodeTiledFn enc = get_encode_fn();
-  if (!enc) return false;
-  const cuuint64_t dims[2] = {(cuuint64_t)Kpad, (cuuint64_t)rows};
-  const cuuint64_t strides[1] = {(cuuint64_t)Kpad};
-  const cuuint32_t box[2] = {(cuuint32_t)TKB, (cuuint32_t)box_rows};
-  const cuuint32_t estr[2] = {1, 1};
-  return enc(m, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<uint8_t*>(T), dims, strides, box, estr,
-             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+  return sy::make_map_u8_sw128(m, T, Kpad, rows, Kpad, TKB, box_rows);
 }
 
 uint64_t g_thermo_attr_devices[3] = {};
@@ -476,7 +365,7 @@ cudaError_t launch_mh(ps_ctx* h, const uint8_t* T, int64_t Kpad, int nv, int nv_
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   return cudaLaunchKernelEx(&cfg, thermo_gemm_kernel<MH>, mA, mB, nkb, nv, (const int2*)dtl, ntiles, SQ,
-                            out, out_mode, err, sync, sync_kb);
+                            out, out_mode, err, sync, sync_kb, h->wait_ns);
 }
 
 }  // namespace

@@ -33,6 +33,20 @@ class ps_matrix(ctypes.Structure):
                 ("ld", ctypes.c_int64), ("dtype", ctypes.c_int32), ("layout", ctypes.c_int32)]
 
 
+class ps_config(ctypes.Structure):
+    """Handle configuration (include/ps.h); 0 = automatic in every kernel-choice field."""
+    _fields_ = [("precision", ctypes.c_int32), ("debug_checks", ctypes.c_int32),
+                ("wait_limit_ns", ctypes.c_int64), ("autotune_cache", ctypes.c_char_p),
+                ("mgemm_feed", ctypes.c_int32), ("mgemm3_feed", ctypes.c_int32),
+                ("mgemm_tile", ctypes.c_int32), ("mgemm_warps", ctypes.c_int32),
+                ("mgemm_unroll", ctypes.c_int32), ("mgemm_add", ctypes.c_int32),
+                ("mgemm_band", ctypes.c_int32), ("tma_slice", ctypes.c_int32),
+                ("tma_unroll", ctypes.c_int32), ("tma_stages", ctypes.c_int32),
+                ("tma_schedule", ctypes.c_int32), ("tma_meet", ctypes.c_int32),
+                ("mgemm3_schedule", ctypes.c_int32), ("thermo_tile_m", ctypes.c_int32),
+                ("thermo_meet_kb", ctypes.c_int32), ("test_batched_stall", ctypes.c_int32)]
+
+
 class ps_problem(ctypes.Structure):
     _fields_ = [("V", ps_matrix), ("way", ctypes.c_int32), ("out_dtype", ctypes.c_int32),
                 ("out", ctypes.c_void_p)]
@@ -63,7 +77,10 @@ def _sig(name, res, args):
     return f
 
 
-ps_create = _sig("ps_create", ctypes.c_int, [ctypes.POINTER(_h), ctypes.c_int])
+ps_config_init = _sig("ps_config_init", None, [ctypes.POINTER(ps_config)])
+ps_create = _sig("ps_create", ctypes.c_int, [ctypes.POINTER(_h), ctypes.c_int, ctypes.POINTER(ps_config)])
+ps_get_config = _sig("ps_get_config", ctypes.c_int, [_h, ctypes.POINTER(ps_config)])
+ps_set_config = _sig("ps_set_config", ctypes.c_int, [_h, ctypes.POINTER(ps_config)])
 ps_destroy = _sig("ps_destroy", ctypes.c_int, [_h])
 ps_status_string = _sig("ps_status_string", ctypes.c_char_p, [ctypes.c_int])
 ps_last_error = _sig("ps_last_error", ctypes.c_char_p, [_h])
@@ -101,7 +118,7 @@ ps_probe_minadd_peak = _sig("ps_probe_minadd_peak", ctypes.c_int,
                             [_h, _i32, ctypes.POINTER(ctypes.c_double)])
 
 EXPORTED = [n for n in globals() if n.startswith("ps_") and callable(globals()[n])
-            and n not in ("ps_matrix", "ps_pair", "ps_triple", "ps_problem")]
+            and n not in ("ps_matrix", "ps_pair", "ps_triple", "ps_problem", "ps_config")]
 
 
 class PSError(RuntimeError):
@@ -116,12 +133,43 @@ def check(status: int, handle=None) -> int:
     return status
 
 
-class Handle:
-    """Owns a ps_handle for one CUDA device."""
+def config(**fields) -> ps_config:
+    """ps_config with the library defaults, then the given fields set
+    (autotune_cache may be a str)."""
+    c = ps_config()
+    ps_config_init(ctypes.byref(c))
+    for k, v in fields.items():
+        if k == "autotune_cache" and isinstance(v, str):
+            v = v.encode()
+        setattr(c, k, v)
+    return c
 
-    def __init__(self, device: int = 0):
+
+class Handle:
+    """Owns a ps_handle for one CUDA device; keyword arguments are ps_config
+    fields (the rest keep their defaults)."""
+
+    def __init__(self, device: int = 0, cfg: ps_config | None = None, **fields):
         self.h = _h()
-        check(ps_create(ctypes.byref(self.h), int(device)))
+        if cfg is None:
+            cfg = config(**fields)
+        self._cfg = cfg  # keeps autotune_cache's bytes alive for the call
+        check(ps_create(ctypes.byref(self.h), int(device), ctypes.byref(cfg)))
+
+    def get_config(self) -> ps_config:
+        c = ps_config()
+        check(ps_get_config(self.h, ctypes.byref(c)), self.h)
+        return c
+
+    def set_config(self, **fields) -> None:
+        """Change the given ps_config fields of this handle."""
+        c = self.get_config()
+        for k, v in fields.items():
+            if k == "autotune_cache" and isinstance(v, str):
+                v = v.encode()
+            setattr(c, k, v)
+        self._cfg = c
+        check(ps_set_config(self.h, ctypes.byref(c)), self.h)
 
     def close(self):
         if self.h:

@@ -158,14 +158,13 @@ def test_host_output_banded_path_matches_device(ps, handle):
 
 
 @pytest.mark.parametrize("band", [1, 2, 3])
-def test_tile_walk_bands(ps, handle, band, monkeypatch):
+def test_tile_walk_bands(ps, handle, band):
     # the 2-way tile walk in bands of `band` tile rows (the default band is
     # wider than these small cases, so narrow bands exercise the diagonal
     # triangles, the column chunks and the ragged last band): every pair is
     # computed once, whole-matrix, by parts and through the host-output bands
     import torch
-    monkeypatch.setenv("PS_MGEMM_BAND", str(band))
-    h = ps.Handle(0)
+    h = ps.Handle(0, mgemm_band=band)
     try:
         nv, nf = 1300, 77
         V = synth.zero_inflated(nv, nf, synth.seed_for(1, 51 + band))
@@ -224,7 +223,7 @@ def test_u8_rejected_on_other_paths(ps, handle):
 
 
 @pytest.mark.parametrize("nv,nf", [(129, 33), (300, 1000), (1300, 77), (700, 16), (4096, 64)])
-def test_operand_feeds_bit_identical(ps, handle, monkeypatch, nv, nf):
+def test_operand_feeds_bit_identical(ps, handle, nv, nf):
     # the TMA-fed kernel (16-, 32- and 64-field slices; tiles claimed from a
     # counter or assigned round-robin) and the cp.async kernel
     # run the same micro-kernel in the same order: every output bit-identical,
@@ -235,10 +234,9 @@ def test_operand_feeds_bit_identical(ps, handle, monkeypatch, nv, nf):
     results = {}
     for feed, bk, dyn in (("cpasync", "16", "1"), ("tma", "16", "1"), ("tma", "32", "1"), ("tma", "64", "1"),
                           ("tma", "32", "0")):
-        monkeypatch.setenv("PS_MGEMM_FEED", feed)
-        monkeypatch.setenv("PS_MGEMM_TMA_BK", bk)
-        monkeypatch.setenv("PS_MGEMM_TMA_DYNAMIC", dyn)  # 0: static round-robin tiles
-        h = ps.Handle(0)
+        # dyn 0: static round-robin tiles
+        h = ps.Handle(0, mgemm_feed=2 if feed == "cpasync" else 1, tma_slice=int(bk),
+                      tma_schedule=1 if dyn == "1" else 2)
         try:
             r = [metrics_2way(ps, h, V), metrics_2way(ps, h, V, out_dtype=np.float64),
                  metrics_2way(ps, h, V, out_dtype=np.uint8)]
@@ -263,7 +261,7 @@ def test_operand_feeds_bit_identical(ps, handle, monkeypatch, nv, nf):
             np.testing.assert_array_equal(a, b, err_msg=str(key))
 
 
-def test_tma_producer_meetings(ps, handle, monkeypatch):
+def test_tma_producer_meetings(ps, handle):
     # the TMA producers' grid-wide meetings (cooperative launch; off by
     # default) change no value: 210 tiles over 152 CTAs (two rounds, the
     # second partial), meetings every 2 slices, whole matrix and row bands
@@ -271,8 +269,7 @@ def test_tma_producer_meetings(ps, handle, monkeypatch):
     nv, nf = 2560, 200
     V = synth.zero_inflated(nv, nf, synth.seed_for(1, 91))
     base = metrics_2way(ps, handle, V)
-    monkeypatch.setenv("PS_MGEMM_TMA_SYNC", "2")
-    h = ps.Handle(0)
+    h = ps.Handle(0, tma_schedule=2, tma_meet=2)
     try:
         np.testing.assert_array_equal(metrics_2way(ps, h, V), base)
         np.testing.assert_array_equal(metrics_2way(ps, h, V, on_host=True), base)
@@ -289,7 +286,7 @@ def test_tma_producer_meetings(ps, handle, monkeypatch):
 
 
 @pytest.mark.parametrize("scale", [1e-37, 1e36])
-def test_fast_division_fallback_range(ps, handle, monkeypatch, scale):
+def test_fast_division_fallback_range(ps, handle, scale):
     # n_f <= 256 takes the branch-free division; denominators below 2^-120
     # or above 2^120 are outside its range, so the warps rewrite their
     # outputs with __fdiv_rn: same values as the oracle and, bit for bit, as
@@ -298,8 +295,7 @@ def test_fast_division_fallback_range(ps, handle, monkeypatch, scale):
     ref = oracle.c2_packed(oracle.to_vector_major(V))
     got = metrics_2way(ps, handle, V)
     assert_rel(got, ref, RTOL32, f"scale {scale}")
-    monkeypatch.setenv("PS_MGEMM_FEED", "cpasync")
-    h = ps.Handle(0)
+    h = ps.Handle(0, mgemm_feed=2)
     try:
         np.testing.assert_array_equal(metrics_2way(ps, h, V), got)
     finally:

@@ -63,25 +63,25 @@ def test_config3_full_size_sampled(ps, handle):
 
 
 @pytest.mark.parametrize("nv,nf", [(129, 16), (300, 70), (517, 200)])
-def test_operand_feeds_bit_identical(ps, handle, monkeypatch, nv, nf):
+def test_operand_feeds_bit_identical(ps, handle, nv, nf):
     # the TMA-fed kernel (pivot min applied per slice in shared memory, warps
-    # skipping blocks outside the pivot's rectangle) and the cp.async kernels
-    # (8 and 16 warps) sum every triple in the same order: bit-identical
-    # slabs, whole and by pivot ranges
+    # skipping blocks outside the pivot's rectangle; work items claimed from
+    # a counter or assigned round-robin) and the cp.async kernels (8 and 16
+    # warps) sum every triple in the same order: bit-identical slabs, whole
+    # and by pivot ranges
     V = synth.zero_inflated(nv, nf, synth.seed_for(3, 81 + nv + nf))
     res = {}
-    for feed, warps in (("cpasync", "8"), ("cpasync", "16"), ("tma", "0")):
-        monkeypatch.setenv("PS_MGEMM3_FEED", feed)
-        monkeypatch.setenv("PS_MGEMM_WARPS", warps)
-        h = ps.Handle(0)
+    for feed, warps, sched in (("cpasync", "8", 0), ("cpasync", "16", 0), ("tma", "0", 1), ("tma", "0", 2)):
+        h = ps.Handle(0, mgemm3_feed=2 if feed == "cpasync" else 1, mgemm_warps=int(warps),
+                      mgemm3_schedule=sched)
         try:
-            res[feed + warps] = [metrics_3way(ps, h, V),
+            res[feed + warps + str(sched)] = [metrics_3way(ps, h, V),
                                  np.concatenate([metrics_3way(ps, h, V, a, b)
                                                  for a, b in [(0, 5), (5, min(130, nv)), (min(130, nv), nv)]])]
         finally:
             h.close()
     ref = oracle.c3_slab(oracle.to_vector_major(V), 0, nv)
-    assert_rel(res["tma0"][0], ref, RTOL32, f"tma nv={nv} nf={nf}")
+    assert_rel(res["tma01"][0], ref, RTOL32, f"tma nv={nv} nf={nf}")
     for key, r in res.items():
-        np.testing.assert_array_equal(r[0], res["cpasync8"][0], err_msg=key)
-        np.testing.assert_array_equal(r[1], res["cpasync8"][0], err_msg=key + " pivot ranges")
+        np.testing.assert_array_equal(r[0], res["cpasync80"][0], err_msg=key)
+        np.testing.assert_array_equal(r[1], res["cpasync80"][0], err_msg=key + " pivot ranges")

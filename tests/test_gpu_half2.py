@@ -31,11 +31,10 @@ def test_half2_integer_data_bit_exact(ps, handle):
 
 
 @pytest.mark.parametrize("warps", [8, 16])
-def test_half2_tile_warps(ps, monkeypatch, warps):
+def test_half2_tile_warps(ps, warps):
     # both tile configurations of the half2 kernel (8 x 8 or 8 x 4 outputs
     # per lane) give the same values
-    monkeypatch.setenv("PS_MGEMM_WARPS", str(warps))
-    h = ps.Handle(0)
+    h = ps.Handle(0, mgemm_warps=warps)
     try:
         V = synth.zero_inflated(700, 333, synth.seed_for(2, 70))
         ref = oracle.c2_packed(oracle.to_vector_major(V))

@@ -103,14 +103,12 @@ def test_thermo_config2_full_size_sampled(ps, handle):
 
 @pytest.mark.parametrize("tile_m", [128, 256])
 @pytest.mark.parametrize("sync_kb", [0, 1, 7])
-def test_thermo_multi_round_producer_sync(ps, handle, sync_kb, tile_m, monkeypatch):
+def test_thermo_multi_round_producer_sync(ps, handle, sync_kb, tile_m):
     # 20 x 20 tile blocks of 256 -> 210 tiles over 152 persistent CTAs (two
     # rounds); 30 k-blocks per tile; the producers meet every sync_kb
     # k-blocks (0: never, 7: a ragged last chunk).  Results stay bit-exact.
     # (tile_m: the 128 x 256 tile with two accumulators, or the 256 x 256 tile)
-    monkeypatch.setenv("PS_THERMO_SYNC_KB", str(sync_kb))
-    monkeypatch.setenv("PS_THERMO_TILE_M", str(tile_m))
-    h = ps.Handle(0)
+    h = ps.Handle(0, thermo_meet_kb=sync_kb if sync_kb else -1, thermo_tile_m=tile_m)
     try:
         nv, nf, L = 5000, 200, 16
         V = synth.zero_inflated(nv, nf, synth.seed_for(2, 90))
