@@ -553,23 +553,27 @@ void ps_config_init(ps_config* cfg) {
 ps_status ps_create(ps_handle* out, int device, const ps_config* cfg) {
   if (!out) return fail(nullptr, PS_ERR_INVALID_ARG, "ps_create: null out");
   *out = nullptr;
-  int n = 0;
-  cudaError_t e = cudaGetDeviceCount(&n);
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    return fail(nullptr, PS_ERR_CUDA, "cudaGetDeviceCount: %s", cudaGetErrorString(e));
-  }
-  if (device < 0 || device >= n)
-    return fail(nullptr, PS_ERR_INVALID_ARG, "device %d not in [0,%d)", device, n);
   ps_ctx* h = new (std::nothrow) ps_ctx();
   if (!h) return fail(nullptr, PS_ERR_OOM, "ps_create: out of host memory");
-  h->device = device;
+  // the configuration is checked first (host only, no device needed)
   const ps_status cs = apply_config(h, cfg);
   if (cs != PS_OK) {
     const std::string msg = h->last_error;
     delete h;
     return fail(nullptr, cs, "%s", msg.c_str());
   }
+  int n = 0;
+  cudaError_t e = cudaGetDeviceCount(&n);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    delete h;
+    return fail(nullptr, PS_ERR_CUDA, "cudaGetDeviceCount: %s", cudaGetErrorString(e));
+  }
+  if (device < 0 || device >= n) {
+    delete h;
+    return fail(nullptr, PS_ERR_INVALID_ARG, "device %d not in [0,%d)", device, n);
+  }
+  h->device = device;
   Guard g(device);
   cudaDeviceProp prop;
   e = cudaGetDeviceProperties(&prop, device);

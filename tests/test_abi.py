@@ -67,3 +67,25 @@ def test_null_handle_is_rejected_without_gpu(ps):
 
 def test_version_string(ps):
     assert b"sm_103a" in ps.ps_version()
+
+
+def test_config_defaults_and_validation_without_gpu(ps):
+    # ps_config_init's defaults; ps_create checks the configuration before it
+    # looks for a device, so every out-of-range field is rejected here
+    c = ps.config()
+    assert c.precision == ps.PS_PATH_FP32 and c.debug_checks == 0
+    assert c.wait_limit_ns == 2_000_000_000 and c.autotune_cache is None
+    for name, _ in ps.ps_config._fields_:
+        if name not in ("precision", "wait_limit_ns", "autotune_cache"):
+            assert getattr(c, name) == 0, name
+    h = ps._h()
+    for field, value in [("precision", ps.PS_PATH_THERMO), ("debug_checks", 2), ("wait_limit_ns", 10),
+                         ("wait_limit_ns", 10**12), ("mgemm_feed", 3), ("mgemm3_feed", -1), ("mgemm_tile", 96),
+                         ("mgemm_warps", 4), ("mgemm_unroll", 5), ("mgemm_add", 7), ("mgemm_band", 65),
+                         ("tma_slice", 48), ("tma_unroll", 12), ("tma_stages", 5), ("tma_schedule", 3),
+                         ("tma_meet", -1), ("mgemm3_schedule", 9), ("thermo_tile_m", 64),
+                         ("thermo_meet_kb", -2), ("test_batched_stall", 2)]:
+        bad = ps.config(**{field: value})
+        assert ps.ps_create(ctypes.byref(h), 0, ctypes.byref(bad)) == ps.PS_ERR_INVALID_ARG, field
+        assert field.encode() in ps.ps_last_error(None)
+    assert ps.ps_create(None, 0, None) == ps.PS_ERR_INVALID_ARG

@@ -112,3 +112,76 @@ def test_batched_rejects_bad_problems(ps, handle):
     probs[1].V.dtype = ps.PS_F64
     assert ps.ps_metrics_batched(handle.h, probs, 2, 0, 0) == ps.PS_ERR_INVALID_ARG
     assert ps.ps_metrics_batched(handle.h, probs, 0, 0, 0) == ps.PS_ERR_INVALID_ARG
+
+
+def test_dependency_wait_timeout_reports_and_handle_recovers(ps):
+    # The timeout path of the persistent launch, in the allowed form: a
+    # dependency count that nothing completes.  test_batched_stall raises
+    # problem 0's per-vector-sums target by one block that does not exist;
+    # with a 1 ms wait limit the first tile epilogue that waits on it gives
+    # up, raises the launch's error flag, every later wait sees the flag, and
+    # the call returns PS_ERR_TIMEOUT.  No kernel is altered and no GPU wait
+    # is unbounded.  The next call on the same handle is normal and correct.
+    import time
+    import torch
+    h = ps.Handle(0, wait_limit_ns=1_000_000)
+    try:
+        probs, keep = _make_batch(ps, SHAPES[:4], 9300)
+        st = torch.cuda.current_stream().cuda_stream
+        h.set_config(test_batched_stall=1)
+        t0 = time.perf_counter()
+        s = ps.ps_metrics_batched(h.h, probs, 4, ps.PS_BATCH_PERSISTENT, st)
+        dt = time.perf_counter() - t0
+        assert s == ps.PS_ERR_TIMEOUT, ps.ps_last_error(h.h)
+        assert b"timed out" in ps.ps_last_error(h.h)
+        assert dt < 30.0
+        assert h.get_config().test_batched_stall == 0  # one-shot
+        for (V, X, o) in keep:
+            o.fill_(float("nan"))
+        ps.check(ps.ps_metrics_batched(h.h, probs, 4, ps.PS_BATCH_PERSISTENT, st), h.h)
+        torch.cuda.synchronize()
+        for t, ((way, nv, nf), (V, X, o)) in enumerate(zip(SHAPES[:4], keep)):
+            Vv = oracle.to_vector_major(V)
+            ref = oracle.c2_packed(Vv) if way == 2 else oracle.c3_slab(Vv, 0, nv)
+            assert_rel(o.cpu().numpy(), ref, 1e-5, f"after timeout, problem {t}")
+        # the other entry points of the handle work too
+        from gpu_run import metrics_2way
+        V = synth.zero_inflated(300, 40, synth.seed_for(4, 9301))
+        assert_rel(metrics_2way(ps, h, V), oracle.c2_packed(oracle.to_vector_major(V)), 1e-5, "2-way after")
+    finally:
+        h.close()
+
+
+def test_config4_shapes_sampled(ps, handle):
+    # the 64 uneven instances of the batched workload (48 2-way with nv in
+    # [256, 4096], 16 3-way with nv in [256, 1024], nf in [512, 8192]) in one
+    # persistent launch: sampled pairs and triples of every instance against
+    # the oracle, and bit-identity with one call per instance
+    import torch
+    shapes = synth.batched_shapes(synth.seed_for(4))
+    assert len(shapes) == 64 and sum(w == 3 for w, _, _ in shapes) == 16
+    probs, keep = _make_batch(ps, shapes, synth.seed_for(4, 1))
+    st = torch.cuda.current_stream().cuda_stream
+    ps.check(ps.ps_metrics_batched(handle.h, probs, 64, ps.PS_BATCH_PERSISTENT, st), handle.h)
+    torch.cuda.synchronize()
+    got = [o.cpu().numpy().copy() for _, _, o in keep]
+    for t, ((way, nv, nf), (V, X, o)) in enumerate(zip(shapes, keep)):
+        Vv = oracle.to_vector_major(V)
+        if way == 2:
+            pairs = synth.sample_pairs(nv, 300, seed=t)
+            pairs = np.concatenate([pairs, [[0, 1], [0, nv - 1], [nv - 2, nv - 1], [127, 128]]])
+            idx = pairs[:, 0] * (2 * nv - pairs[:, 0] - 1) // 2 + (pairs[:, 1] - pairs[:, 0] - 1)
+            assert_rel(got[t][idx], oracle.c2_pairs(Vv, pairs), 1e-5, f"instance {t} pairs")
+        else:
+            from gpu_run import slab_index
+            tr = synth.sample_triples(nv, 300, seed=t)
+            tr = np.concatenate([tr, [[0, 1, 2], [0, 1, nv - 1], [nv - 3, nv - 2, nv - 1], [126, 127, 128]]])
+            idx = slab_index(nv, 0, tr[:, 0], tr[:, 1], tr[:, 2])
+            assert_rel(got[t][idx], oracle.c3_triples(Vv, tr), 1e-5, f"instance {t} triples")
+        assert np.all(np.isfinite(got[t])) and got[t].min() >= 0.0 and got[t].max() <= 1.0
+    for (V, X, o) in keep:
+        o.fill_(float("nan"))
+    ps.check(ps.ps_metrics_batched(handle.h, probs, 64, ps.PS_BATCH_PER_INSTANCE, st), handle.h)
+    torch.cuda.synchronize()
+    for t, (V, X, o) in enumerate(keep):
+        np.testing.assert_array_equal(got[t], o.cpu().numpy(), err_msg=f"instance {t}")
