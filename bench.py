@@ -11,9 +11,12 @@ add per element pair, the paper's count).  Prints ONE JSON line on rank 0.
 
   python bench.py [--gpus N --steps K --warmup W] [--impl reference]
 
-Multi-GPU (torchrun): every rank computes its own instance of the workload
-(seed + rank), no collective on the data path; value = all ranks'
-comparisons / max-over-ranks time ("scaling": "weak").
+Multi-GPU (torchrun): by default the ranks share ONE instance, each
+computing the equal-work part ps_partition gives it (the paper's split of
+the vector axis, Section 4.1; V replicated, outputs sharded, no collective
+on the data path); value = the instance's comparisons / max-over-ranks time
+("scaling": "strong").  --scaling weak runs one independent instance per
+rank (seed + rank) instead.
 """
 from __future__ import annotations
 
@@ -232,11 +235,71 @@ def run_reference(args, w, ws, rank):
     print(json.dumps(line), flush=True)
 
 
+def batched_section(ps, synth, h, torch, sptr, peak_cmp, steps=3):
+    """The 64 uneven instances (48 2-way with nv ~ U[256, 4096], 16 3-way with
+    nv ~ U[256, 1024], nf ~ U[512, 8192], FP32) in one persistent launch
+    replayed from a CUDA graph, against one call per instance; the kernel
+    variant is the autotuner's choice for this batch shape."""
+    shapes = synth.batched_shapes(synth.seed_for(4))
+    keep, probs = [], (ps.ps_problem * len(shapes))()
+    cmp_total = 0
+    for t, (way, nv, nf) in enumerate(shapes):
+        V = synth.zero_inflated(nv, nf, synth.seed_for(4, 1 + t))
+        ld = (nv + 3) // 4 * 4
+        Xp = torch.zeros((nf, ld), dtype=torch.float32, device="cuda")
+        Xp[:, :nv] = torch.from_numpy(V).cuda()
+        n = nv * (nv - 1) // 2 if way == 2 else ps.ps_slab_size(nv, 0, nv)
+        out = torch.empty(n, dtype=torch.float32, device="cuda")
+        probs[t].V = ps.matrix(Xp[:, :nv])
+        probs[t].way = way
+        probs[t].out_dtype = ps.PS_F32
+        probs[t].out = out.data_ptr()
+        keep.append((Xp, out))
+        cmp_total += nf * (nv * (nv - 1) // 2 if way == 2 else nv * (nv - 1) * (nv - 2) // 6)
+    choice = ctypes.create_string_buffer(256)
+    t0 = time.perf_counter()
+    ps.check(ps.ps_autotune_batched(h.h, probs, len(shapes), None, choice, 256, sptr), h.h)
+    t_tune = time.perf_counter() - t0
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    res = {}
+    for name, mode in (("persistent_graph", ps.PS_BATCH_PERSISTENT), ("per_instance", ps.PS_BATCH_PER_INSTANCE)):
+        for _ in range(2):
+            ps.check(ps.ps_metrics_batched(h.h, probs, len(shapes), mode, sptr), h.h)
+        torch.cuda.synchronize()
+        e0.record(torch.cuda.current_stream())
+        for _ in range(steps):
+            ps.check(ps.ps_metrics_batched(h.h, probs, len(shapes), mode, sptr), h.h)
+        e1.record(torch.cuda.current_stream())
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        res[name] = {"ms_per_batch": ms, "value": cmp_total / (ms / 1e3), "unit": UNIT,
+                     "frac_of_alu_peak": cmp_total / (ms / 1e3) / peak_cmp}
+    del keep, probs
+    torch.cuda.empty_cache()
+    n2 = sum(1 for w, _, _ in shapes if w == 2)
+    return {"workload": f"64 uneven instances ({n2} 2-way nv~U[256,4096], {64 - n2} 3-way nv~U[256,1024], "
+                        "nf~U[512,8192], FP32)",
+            "comparisons_per_batch": cmp_total, **res,
+            "speedup_persistent_vs_per_instance": res["per_instance"]["ms_per_batch"]
+            / res["persistent_graph"]["ms_per_batch"],
+            "autotuner_choice": choice.value.decode(), "autotune_seconds": t_tune,
+            "timing": "CUDA events on the launching stream around each whole batched call (the persistent "
+                      "call includes its error-flag read back)"}
+
+
 def threshold_section(ps, synth, h, torch, sptr):
     """Exhaustive vs learned vs bound-filtered thresholded 3-way search on
-    8192 x 2048 vectors from 64 latent profiles (sigma 0.4), tau = 0.7."""
+    8192 x 2048 vectors from 64 latent profiles (sigma 0.4), tau = 0.7.
+
+    The encoder is trained on 8 fresh 1024-vector matrices drawn from the
+    same latent-profile population (the same 64 profiles, new profile
+    assignments, scales and noise: none of the searched vectors), labelled by
+    the exact thresholded search, 1500 Adam steps.  A second line trains on 8
+    random 1024-vector subsets of the searched matrix itself."""
     nv, nf, tau = 8192, 2048, 0.7
-    V, _ = synth.latent_profiles(nv, nf, synth.seed_for(5), n_profiles=64, sigma=0.4)
+    pseed = synth.seed_for(5)
+    V, _ = synth.latent_profiles(nv, nf, pseed, n_profiles=64, sigma=0.4)
     X = torch.from_numpy(V).cuda()
     m = ps.matrix(X)
     cap = 20_000_000
@@ -256,33 +319,50 @@ def threshold_section(ps, synth, h, torch, sptr):
         keys = out[:n, :3].to(torch.int64)
         return dt, n, (keys[:, 0] << 42) | (keys[:, 1] << 21) | keys[:, 2], out[:n, 3].clone(), kept.value
 
+    def train(mats_np, label):
+        subs = [torch.from_numpy(np.ascontiguousarray(x)).cuda() for x in mats_np]
+        mats = (ps.ps_matrix * len(subs))(*[ps.matrix(x) for x in subs])
+        loss = ctypes.c_double()
+        ps.check(ps.ps_proposal_init(h.h, nf, 99), h.h)
+        ps.check(ps.ps_timing_enable(h.h, 1), h.h)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ps.check(ps.ps_proposal_train(h.h, mats, len(subs), tau, 1500, 1e-3, 0.995, 99, ctypes.addressof(loss),
+                                      sptr), h.h)
+        t_train = time.perf_counter() - t0
+        n_l, ms_l, n_s, ms_s = ctypes.c_int64(), ctypes.c_double(), ctypes.c_int64(), ctypes.c_double()
+        ps.check(ps.ps_timing_read(h.h, b"proposal_labels", ctypes.byref(n_l), ctypes.byref(ms_l)), h.h)
+        ps.check(ps.ps_timing_read(h.h, b"proposal_steps", ctypes.byref(n_s), ctypes.byref(ms_s)), h.h)
+        ps.check(ps.ps_timing_enable(h.h, 0), h.h)
+        t_l, n_found, k_l, v_l, kept_l = run(1)
+        found = torch.isin(k_l, k_ex)
+        exact_vals = bool(torch.equal(v_l, v_ex[torch.isin(k_ex, k_l)]))
+        recall = float(found.sum().item()) / max(n_ex, 1)
+        del subs
+        return {"training_data": label, "train_seconds": t_train, "train_loss": loss.value,
+                "train_breakdown": {"exact_label_search_s": ms_l.value / 1e3, "label_searches": n_l.value,
+                                    "adam_steps_s": ms_s.value / 1e3, "steps": 1500,
+                                    "other_s": t_train - (ms_l.value + ms_s.value) / 1e3},
+                "search_seconds": t_l, "triples": n_found, "recall": recall,
+                "values_bit_identical": exact_vals, "blocks_searched": kept_l,
+                "speedup_search": t_ex / t_l, "speedup_incl_training": t_ex / (t_l + t_train)}
+
     t_ex, n_ex, k_ex, v_ex, _ = run(0)
-    # encoder trained on the exact results of 8 random 1024-vector subsets
-    # (1500 Adam steps, theta at the 0.5% quantile of positive pair scores)
+    fresh = [synth.latent_profiles(1024, nf, synth.seed_for(5, 100 + t), n_profiles=64, sigma=0.4,
+                                   profile_seed=pseed)[0] for t in range(8)]
+    held_out = train(fresh, "8 fresh 1024-vector matrices from the same 64 latent profiles (new assignments, "
+                            "scales and noise; no searched vector)")
     rng = np.random.default_rng(170508210)
-    nsub = 8
-    subs = [torch.from_numpy(np.ascontiguousarray(V[:, np.sort(rng.choice(nv, 1024, replace=False))])).cuda()
-            for _ in range(nsub)]
-    mats = (ps.ps_matrix * nsub)(*[ps.matrix(x) for x in subs])
-    loss = ctypes.c_double()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    ps.check(ps.ps_proposal_train(h.h, mats, nsub, tau, 1500, 1e-3, 0.995, 99, ctypes.addressof(loss), sptr),
-             h.h)
-    t_train = time.perf_counter() - t0
-    t_l, n_l, k_l, v_l, kept_l = run(1)
-    found = torch.isin(k_l, k_ex)
-    recall = float(found.sum().item()) / max(n_ex, 1)
+    subsets = [V[:, np.sort(rng.choice(nv, 1024, replace=False))] for _ in range(8)]
+    subset = train(subsets, "8 random 1024-vector subsets of the searched matrix")
     t_b, n_b, k_b, v_b, kept_b = run(2)
     exact_b = n_b == n_ex and bool(torch.equal(k_b, k_ex)) and bool(torch.equal(v_b, v_ex))
-    del out, X, subs
+    del out, X
     torch.cuda.empty_cache()
     return {"workload": "3way threshold 8192x2048 f32, 64 latent profiles, sigma 0.4, tau 0.7",
             "comparisons_exhaustive": nf * nv * (nv - 1) * (nv - 2) // 6,
             "exhaustive": {"seconds": t_ex, "triples": n_ex},
-            "learned": {"train_seconds": t_train, "train_loss": loss.value, "search_seconds": t_l,
-                        "triples": n_l, "recall": recall, "blocks_searched": kept_l,
-                        "speedup_search": t_ex / t_l, "speedup_incl_training": t_ex / (t_l + t_train)},
+            "learned": held_out, "learned_subset_training": subset,
             "bound_lossless": {"search_seconds": t_b, "triples": n_b, "identical_to_exhaustive": exact_b,
                                "blocks_searched": kept_b, "speedup": t_ex / t_b}}
 
@@ -299,6 +379,10 @@ def main():
     ap.add_argument("--no-secondary", action="store_true")
     ap.add_argument("--no-thermo", action="store_true")
     ap.add_argument("--no-threshold", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--scaling", default="strong", choices=["strong", "weak"],
+                    help="with N > 1 ranks: strong = the ranks share one instance (ps_partition's equal-work "
+                         "parts, no collective on the data path); weak = one independent instance per rank")
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
     ws, rank, local = dist_env()
@@ -316,29 +400,49 @@ def main():
     h = ps.Handle(local)
     nv, nf = w["nv"], w["nf"]
     dtype = np.float64 if args.workload.endswith("f64") else np.float32
-    V = synth.zero_inflated(nv, nf, synth.seed_for(w["number"], rank), dtype=dtype)
+    strong = ws > 1 and args.scaling == "strong"
+    # strong scaling: every rank holds the same instance and computes its
+    # part; weak scaling: rank r computes its own instance (seed + r)
+    V = synth.zero_inflated(nv, nf, synth.seed_for(w["number"], 0 if strong else rank), dtype=dtype)
     X = torch.from_numpy(V).cuda()
     m = ps.matrix(X)
     stream = torch.cuda.current_stream()
     sptr = stream.cuda_stream
+    # this rank's share of the unique outputs (the whole instance unless strong)
+    pb, pe, ob, oe = (ctypes.c_int64() for _ in range(4))
+    ps.check(ps.ps_partition(nv, w["way"], ws if strong else 1, rank if strong else 0, ctypes.byref(pb),
+                             ctypes.byref(pe), ctypes.byref(ob), ctypes.byref(oe)))
     if w["way"] == 2:
         out_dtype = 1 if dtype == np.float64 else 0
         out = torch.empty(nv * (nv - 1) // 2, dtype=torch.float64 if out_dtype else torch.float32, device="cuda")
         main_kernel = "mgemm2"
-        launches_per_step = 2
+        # vector sums, (the small-n_f epilogue's sums and range words,) min-product
+        launches_per_step = 2 + (1 if nf <= 256 and dtype == np.float32 else 0)
+        rows = range(pb.value, pe.value)
+        cmp_mine = nf * sum(nv - 1 - i for i in rows) if strong else None
 
-        def step():
-            ps.check(ps.ps_metrics_2way(h.h, ctypes.byref(m), ps.PS_PATH_FP32, 0, out.data_ptr(), out_dtype, sptr), h.h)
+        if strong:
+            def step():
+                ps.check(ps.ps_metrics_2way_part(h.h, ctypes.byref(m), ws, rank, out.data_ptr(), out_dtype, sptr),
+                         h.h)
+        else:
+            def step():
+                ps.check(ps.ps_metrics_2way(h.h, ctypes.byref(m), ps.PS_PATH_FP32, 0, out.data_ptr(), out_dtype,
+                                            sptr), h.h)
     else:
-        out = torch.empty(ps.ps_slab_size(nv, 0, nv), dtype=torch.float32, device="cuda")
+        jb, je = pb.value, pe.value
+        out = torch.empty(max(ps.ps_slab_size(nv, jb, je), 1), dtype=torch.float32, device="cuda")
         main_kernel = "mgemm3"
-        launches_per_step = 4  # sums, n2 table, pivot prefix, 3-way
+        launches_per_step = 5  # sums, n2 table, pivot prefix, item table, 3-way
+        cmp_mine = nf * ps.ps_slab_size(nv, jb, je) if strong else None
 
         def step():
-            ps.check(ps.ps_metrics_3way(h.h, ctypes.byref(m), 0, nv, out.data_ptr(), sptr), h.h)
+            ps.check(ps.ps_metrics_3way(h.h, ctypes.byref(m), jb, je, out.data_ptr(), sptr), h.h)
 
     out_bytes = out.numel() * out.element_size()
     cmp_per_step = comparisons(w)
+    # comparisons this rank's kernel makes per step (for its roofline)
+    cmp_rank = cmp_mine if strong else cmp_per_step
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
@@ -370,11 +474,13 @@ def main():
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         ms_total = float(t.item())
     ms_step = ms_total / args.steps
-    value = ws * cmp_per_step / (ms_step / 1e3)
+    # whole-job comparisons per second: one shared instance (strong) or one
+    # instance per rank (weak), over the slowest rank's time
+    value = (cmp_per_step if strong else ws * cmp_per_step) / (ms_step / 1e3)
 
     # ---- roofline of the dominant kernel ----
     k_avg_ms = k_ms.value / max(n_launch.value, 1)
-    achieved = cmp_per_step / (k_avg_ms / 1e3)
+    achieved = cmp_rank / (k_avg_ms / 1e3)
     peaks = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else {}
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     props = torch.cuda.get_device_properties(local)
@@ -401,15 +507,29 @@ def main():
     e2e = None
     if not args.no_e2e:
         Vh = torch.from_numpy(V).pin_memory()
-        outh = torch.empty(out.numel(), dtype=out.dtype).pin_memory()
         mh = ps.matrix(Vh)
-        if w["way"] == 2:
+        if w["way"] == 2 and strong:
+            # the part call writes device memory: copy V in and this rank's
+            # packed range out around it (inside the timed region)
+            outh = torch.empty(oe.value - ob.value, dtype=out.dtype).pin_memory()
+
+            def hstep():
+                X.copy_(Vh, non_blocking=True)
+                ps.check(ps.ps_metrics_2way_part(h.h, ctypes.byref(m), ws, rank, out.data_ptr(), out_dtype, sptr),
+                         h.h)
+                outh.copy_(out[ob.value:oe.value], non_blocking=True)
+                torch.cuda.current_stream().synchronize()
+        elif w["way"] == 2:
+            outh = torch.empty(out.numel(), dtype=out.dtype).pin_memory()
+
             def hstep():
                 ps.check(ps.ps_metrics_2way(h.h, ctypes.byref(mh), ps.PS_PATH_FP32, 0, outh.data_ptr(),
                                             out_dtype, sptr), h.h)
         else:
+            outh = torch.empty(out.numel(), dtype=out.dtype).pin_memory()
+
             def hstep():
-                ps.check(ps.ps_metrics_3way(h.h, ctypes.byref(mh), 0, nv, outh.data_ptr(), sptr), h.h)
+                ps.check(ps.ps_metrics_3way(h.h, ctypes.byref(mh), jb, je, outh.data_ptr(), sptr), h.h)
         hstep()
         if ws > 1:
             torch.distributed.barrier()
@@ -421,7 +541,7 @@ def main():
             t = torch.tensor([dt], device="cuda", dtype=torch.float64)
             torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
             dt = float(t.item())
-        e2e = {"value": ws * cmp_per_step / dt, "unit": UNIT, "ms_per_step": dt * 1e3,
+        e2e = {"value": (cmp_per_step if strong else ws * cmp_per_step) / dt, "unit": UNIT, "ms_per_step": dt * 1e3,
                "h2d_bytes_per_step": int(Vh.numel() * Vh.element_size()),
                "d2h_bytes_per_step": int(outh.numel() * outh.element_size())}
         if w["way"] == 2 and ws == 1:
@@ -475,9 +595,19 @@ def main():
         ps.check(ps.ps_timing_enable(h.h, 0), h.h)
         torch.cuda.synchronize()
         samples["half2"] = ("pairs", pairs, out[idx].double().cpu().numpy())
+        # its own peak: the measured register-only rate of its inner
+        # operation (one packed FP16 min for two comparisons, two FP32 adds of
+        # its halves; ps_probe_minadd_peak variant 2)
+        probe_h = ctypes.c_double()
+        ps.check(ps.ps_probe_minadd_peak(h.h, 2, ctypes.byref(probe_h)), h.h)
+        hach = cmp_per_step / (hk / 1e3)
         half2 = {"value": cmp_per_step / (hms / 1e3), "unit": UNIT, "ms_per_step": hms, "kernel_ms": hk,
                  "speedup_vs_fp32": ms_step / hms,
-                 "frac_of_fp32_min_peak": cmp_per_step / (hk / 1e3) / peak_cmp, "sampled_error": None,
+                 "roofline": {"bound": "alu", "achieved": hach / 1e12, "peak": probe_h.value / 1e12,
+                              "unit": "Tcmp/s", "frac": hach / probe_h.value,
+                              "peak_basis": "measured register-only rate of min.f16x2 + 2 FP32 adds "
+                                            "(ps_probe_minadd_peak variant 2)"},
+                 "sampled_error": None,
                  "note": "FP16-rounded inputs (power-of-two scaled), min.f16x2, FP32 accumulation"}
 
     # ---- thermometer tensor-core path on the same input (2-way only) ----
@@ -576,11 +706,30 @@ def main():
             ks = k_ms.value / max(n_launch.value, 1)
             byts = Vs.nbytes + os_.numel() * 4
             cs = nfs * nvs * (nvs - 1) // 2
+            # the same call with one-byte codes (PS_U8): a quarter of the bytes out
+            ou_ = torch.empty(os_.numel(), dtype=torch.uint8, device="cuda")
+            for _ in range(3):
+                ps.check(ps.ps_metrics_2way(h.h, ctypes.byref(ms_), ps.PS_PATH_FP32, 0, ou_.data_ptr(), ps.PS_U8,
+                                            sptr), h.h)
+            ps.check(ps.ps_timing_enable(h.h, 1), h.h)
+            torch.cuda.synchronize()
+            for _ in range(10):
+                ps.check(ps.ps_metrics_2way(h.h, ctypes.byref(ms_), ps.PS_PATH_FP32, 0, ou_.data_ptr(), ps.PS_U8,
+                                            sptr), h.h)
+            torch.cuda.synchronize()
+            ps.check(ps.ps_timing_read(h.h, b"mgemm2", ctypes.byref(n_launch), ctypes.byref(k_ms)), h.h)
+            ps.check(ps.ps_timing_enable(h.h, 0), h.h)
+            ku = k_ms.value / max(n_launch.value, 1)
+            bytu = Vs.nbytes + ou_.numel()
+            del ou_
             small[f"2way_32768x{nfs}_f32"] = {
                 "ms_per_step": mss, "mgemm2_ms": ks, "value": cs / (mss / 1e3), "unit": UNIT,
                 "algorithmic_gb": byts / 1e9, "achieved_gbs": byts / (ks / 1e3) / 1e9,
                 "frac_of_hbm": byts / (ks / 1e3) / 1e9 / hbm,
-                "frac_of_alu_peak": cs / (ks / 1e3) / peak_cmp}
+                "frac_of_alu_peak": cs / (ks / 1e3) / peak_cmp,
+                "u8_codes": {"mgemm2_ms": ku, "algorithmic_gb": bytu / 1e9,
+                             "achieved_gbs": bytu / (ku / 1e3) / 1e9, "frac_of_hbm": bytu / (ku / 1e3) / 1e9 / hbm,
+                             "frac_of_alu_peak": cs / (ku / 1e3) / peak_cmp}}
             del Xs
         secondary["small_nf_output_bound"] = small
         del os_
@@ -614,6 +763,11 @@ def main():
         secondary["sorenson_b1_32768x8192"] = sor
         del Wb, ob
 
+    # ---- batched uneven instances (64 problems, one persistent graph launch) ----
+    batched = None
+    if not args.no_batched and w["way"] == 2 and ws == 1:
+        batched = batched_section(ps, synth, h, torch, sptr, peak_cmp)
+
     # ---- thresholded 3-way search with proposals (8192 x 2048 latent profiles) ----
     thresh = None
     if not args.no_threshold and w["way"] == 2 and ws == 1:
@@ -634,17 +788,19 @@ def main():
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-                "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+                "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+                "scaling": "strong" if strong else "weak",
                 "vs_baseline": None, "dtype": "f32" if dtype == np.float32 else "f64", "data": "synthetic",
                 "config": {"workload": args.workload, "nv": nv, "nf": nf, "way": w["way"],
                            "comparisons_per_step": cmp_per_step, "path": "fp32 CUDA-core min+add",
                            "l2": f"inputs larger than L2 ({V.nbytes / 1e9:.2f} GB in, "
                                  f"{out_bytes / 1e9:.2f} GB out)",
-                           "parallelism": f"independent instance per rank x{ws}"},
+                           "parallelism": (f"one instance split over {ws} ranks (ps_partition, no collective)"
+                                           if strong else f"independent instance per rank x{ws}")},
                 "roofline": roofline, "cpu_baseline": cb, "e2e": e2e, "clocks": clk,
                 "gpu_launches": launches_per_step * args.steps,
                 "sampled_max_rel_err": max_rel, "half2_variant": half2, "thermo_tensor_core": thermo,
-                "secondary": secondary,
+                "secondary": secondary, "batched": batched,
                 "threshold_3way": thresh}
         print(json.dumps(line), flush=True)
     h.close()

@@ -500,9 +500,12 @@ ps_status ps_quantize(ps_handle h, const ps_matrix* V, int32_t levels,
  * (it waits for recorded events first).
  * ps_timing_read synchronises on the recorded events of `kernel` and returns
  * their number and summed duration.  Kernel names: "vector_sums", "pack",
- * "mgemm2", "mgemm2_f64", "mgemm2_half", "mgemm2_n2", "mgemm3", "quantize", "thermo_encode",
- * "thermo_gemm", "threshold3", "sort", "batched", "proposal_encode",
- * "proposal_score", "proposal_bound".
+ * "mgemm2", "mgemm2_f64", "mgemm2_half", "mgemm2_n2", "mgemm3", "quantize",
+ * "thermo_encode", "b1_encode", "thermo_gemm", "threshold2", "threshold3",
+ * "sort", "batched", "proposal_encode", "proposal_score", "proposal_bound";
+ * and two regions of ps_proposal_train: "proposal_labels" (the exact
+ * thresholded search of one training matrix, one record each) and
+ * "proposal_steps" (all training steps, one record).
  * Errors: PS_ERR_INVALID_ARG for null arguments. */
 ps_status ps_timing_enable(ps_handle h, int32_t enable);
 ps_status ps_timing_read(ps_handle h, const char* kernel, int64_t* launches,
@@ -512,7 +515,9 @@ ps_status ps_timing_read(ps_handle h, const char* kernel, int64_t* launches,
  * Measured CUDA-core issue rate of the paper's inner operation (one min plus
  * one add per element pair, Section 3.1), from a register-only kernel of
  * independent min/add chains over the whole GPU.  variant 0: scalar FP32
- * min + scalar FP32 add; variant 1: FP32 min + packed f32x2 add.
+ * min + scalar FP32 add; variant 1: FP32 min + packed f32x2 add; variant 2:
+ * the half2 path's operation, one packed FP16 min (two comparisons) and two
+ * FP32 adds of its halves.
  *   cmp_per_s : comparisons (min+add pairs) per second.
  * Synchronises the device.  Errors: PS_ERR_INVALID_ARG for a bad variant. */
 ps_status ps_probe_minadd_peak(ps_handle h, int32_t variant,

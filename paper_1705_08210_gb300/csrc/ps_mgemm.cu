@@ -4,6 +4,8 @@
 // issue-rate probe.
 #include "ps_mgemm_impl.cuh"
 
+#include <cuda_fp16.h>
+
 #include <algorithm>
 #include <mutex>
 
@@ -60,7 +62,9 @@ __global__ void __launch_bounds__(256)
 
 // ---------------------------------------------------------------------------
 // Issue-rate probe: independent chains x <- x + min(x, y) (one comparison per
-// chain step).  Variant 1 adds pairs with add.rn.f32x2.
+// chain step).  Variant 1 adds pairs with add.rn.f32x2.  Variant 2 is the
+// half2 path's inner operation: one packed min.f16x2 of two field pairs
+// (two comparisons), both halves added to FP32 accumulators.
 constexpr int PROBE_CHAINS = 16;
 
 template <int VARIANT>
@@ -68,7 +72,30 @@ __global__ void __launch_bounds__(256) probe_kernel(float* out, int iters, float
   float x[PROBE_CHAINS];
 #pragma unroll
   for (int c = 0; c < PROBE_CHAINS; ++c) x[c] = (float)(threadIdx.x + c) * 1e-3f;
-  for (int it = 0; it < iters; ++it) {
+  if (VARIANT == 2) {
+    // chain c: h[c] is the half2 operand, x[c] the FP32 accumulator
+    uint32_t hv[PROBE_CHAINS];
+    const __half2 yy = __floats2half2_rn(y, y);
+    const uint32_t yb = *reinterpret_cast<const uint32_t*>(&yy);
+#pragma unroll
+    for (int c = 0; c < PROBE_CHAINS; ++c) {
+      const __half2 t = __floats2half2_rn(x[c], x[c] + 1e-3f);
+      hv[c] = *reinterpret_cast<const uint32_t*>(&t);
+    }
+    for (int it = 0; it < iters / 2; ++it) {
+#pragma unroll
+      for (int c = 0; c < PROBE_CHAINS; ++c) {
+        uint32_t m;
+        asm("min.f16x2 %0, %1, %2;" : "=r"(m) : "r"(hv[c]), "r"(yb));
+        asm("{\n\t.reg .b16 l, h;\n\tmov.b32 {l, h}, %1;\n\tadd.rn.f32.f16 %0, l, %0;\n\t"
+            "add.rn.f32.f16 %0, h, %0;\n\t}"
+            : "+f"(x[c])
+            : "r"(m));
+        hv[c] = m;  // the next min depends on this one (an opaque chain)
+      }
+    }
+  }
+  for (int it = 0; VARIANT != 2 && it < iters; ++it) {
     if (VARIANT == 0) {
 #pragma unroll
       for (int c = 0; c < PROBE_CHAINS; ++c) x[c] = x[c] + fminf(x[c], y);
@@ -321,7 +348,8 @@ cudaError_t probe_minadd(ps_ctx* h, int variant, double* cmp_per_s) {
   for (int rep = 0; rep < 4; ++rep) {
     cudaEventRecord(e0, 0);
     if (variant == 0) probe_kernel<0><<<blocks, 256>>>(dout, iters, 1e-3f);
-    else probe_kernel<1><<<blocks, 256>>>(dout, iters, 1e-3f);
+    else if (variant == 1) probe_kernel<1><<<blocks, 256>>>(dout, iters, 1e-3f);
+    else probe_kernel<2><<<blocks, 256>>>(dout, iters, 1e-3f);
     cudaEventRecord(e1, 0);
     e = cudaEventSynchronize(e1);
     if (e != cudaSuccess) break;

@@ -420,11 +420,10 @@ __host__ __device__ __forceinline__ int64_t pivot_tiles(int nv, int64_t j, int B
 // exact, like the FP64 sum, whenever the sums are integers below 2^24 (the
 // FP64 pipe, at a small fraction of the FP32 rate, would otherwise bound the
 // epilogue at small n_f).  Tiles strictly above the diagonal and inside the
-// matrix (every i < j < nv) take a path without per-output checks; with
-// FASTDIV (kernels for small n_f, where the epilogue is most of the work)
-// their quotients come from the branch-free div_rn_fast.  Every path gives
-// the same correctly rounded values.
-template <class C, bool PACKED, bool FASTDIV = false>
+// matrix (every i < j < nv) take a path without per-output checks.  Every
+// path gives the same correctly rounded values (store_tile2_lean below
+// too).
+template <class C, bool PACKED>
 __device__ __forceinline__ void store_tile2(const Acc<PACKED, C::NJ>& acc, const Lanes<C>& L, int row0,
                                             int col0, int64_t nv, const double* __restrict__ S,
                                             void* __restrict__ out, int mode) {
@@ -455,58 +454,6 @@ __device__ __forceinline__ void store_tile2(const Acc<PACKED, C::NJ>& acc, const
       Sjf[c] = j < nv ? (float)S[j] : 0.0f;
     }
     const bool u8 = mode == OUT2_C2_U8;
-    if (FASTDIV && interior) {
-      // branch-free quotients; a warp that met an input outside the fast
-      // division's range rewrites its outputs with __fdiv_rn (same values).
-      // The numerators are collapsed first so that only 8 x NJ values stay
-      // live for the rewrite.
-      float n2[8][C::NJ];
-#pragma unroll
-      for (int r = 0; r < 8; ++r)
-#pragma unroll
-        for (int c = 0; c < C::NJ; ++c) {
-          const float2 hl = acc.hl(r, c);
-          n2[r][c] = __fadd_rn(hl.x, hl.y);
-        }
-      bool all_ok = true;
-#pragma unroll
-      for (int r = 0; r < 8; ++r) {
-        const int i = row0 + L.row(r);
-        const float Sif = (float)S[i];
-        const int64_t base = pair_index(nv, i, i + 1) - (i + 1);
-#pragma unroll
-        for (int c = 0; c < C::NJ; ++c) {
-          const int j = col0 + L.col(c);
-          const float d = __fadd_rn(Sif, Sjf[c]);
-          bool ok;
-          const float q = div_rn_fast(2.0f * n2[r][c], d, ok);
-          all_ok = all_ok && (ok || d == 0.0f);
-          const float c2 = (d == 0.0f) ? 0.0f : q;
-          if (u8)
-            static_cast<unsigned char*>(out)[base + j] = c2_code(c2);
-          else
-            static_cast<float*>(out)[base + j] = c2;
-        }
-      }
-      if (__all_sync(0xffffffffu, all_ok)) return;
-#pragma unroll
-      for (int r = 0; r < 8; ++r) {
-        const int i = row0 + L.row(r);
-        const float Sif = (float)S[i];
-        const int64_t base = pair_index(nv, i, i + 1) - (i + 1);
-#pragma unroll
-        for (int c = 0; c < C::NJ; ++c) {
-          const int j = col0 + L.col(c);
-          const float d = __fadd_rn(Sif, Sjf[c]);
-          const float c2 = (d == 0.0f) ? 0.0f : __fdiv_rn(2.0f * n2[r][c], d);
-          if (u8)
-            static_cast<unsigned char*>(out)[base + j] = c2_code(c2);
-          else
-            static_cast<float*>(out)[base + j] = c2;
-        }
-      }
-      return;
-    }
     if (interior) {
 #pragma unroll
       for (int r = 0; r < 8; ++r) {
@@ -566,6 +513,52 @@ __device__ __forceinline__ void store_tile2(const Acc<PACKED, C::NJ>& acc, const
       orow[j] = (d == 0.0) ? 0.0 : (2.0 * n2) / d;
     }
   }
+}
+
+// Interior-tile epilogue of the small-n_f kernels (FP32 or one-byte
+// output): Sfi / Sfj are this lane's rows' and columns' FP32 sums with 1.0 in
+// place of 0 (NarrowPrep; an all-zero vector has n2 = 0 with every partner,
+// so 0 / (S_j + 1) = 0 is the metric without a test for d = 0), and every
+// quotient comes from div_rn_lean, whose range the caller has checked once
+// for the whole call.  Values equal store_tile2's bit for bit.  Each row's
+// outputs go through one row pointer (no per-output index arithmetic).
+template <class C, bool PACKED, bool U8, bool LO_ONLY>
+__device__ __forceinline__ void store_tile2_lean(const Acc<PACKED, C::NJ>& acc, const Lanes<C>& L, int row0,
+                                                 int col0, int64_t nv, const float (&Sfi)[8],
+                                                 const float (&Sfj)[C::NJ], void* __restrict__ out) {
+  // packed position of (i, j) = base(i) + j with base(i) = P(i) - i - 1, P(i)
+  // the index of pair (i, i + 1); base(i + 1) = base(i) + nv - i - 2.  A
+  // lane's rows are two runs of four consecutive rows.
+  int64_t base = 0;
+#pragma unroll
+  for (int r = 0; r < 8; ++r) {
+    const int64_t i = row0 + L.row(r);
+    if (r == 0 || r == 4)
+      base = pair_index(nv, i, i + 1) - (i + 1);
+    else
+      base += nv - i - 1;
+    const int64_t off = base + col0 + L.col(0);
+#pragma unroll
+    for (int c = 0; c < C::NJ; ++c) {
+      const float2 hl = acc.hl(r, c);
+      // LO_ONLY: nothing was ever folded, hi is 0 and 0 + lo = lo (lo, a sum
+      // of non-negative terms from +0, is never -0)
+      const float n2 = LO_ONLY ? hl.y : __fadd_rn(hl.x, hl.y);
+      const float c2 = div_rn_lean(__fadd_rn(n2, n2), __fadd_rn(Sfi[r], Sfj[c]));
+      const int64_t o = off + (L.col(c) - L.col(0));
+      if (U8)
+        static_cast<unsigned char*>(out)[o] = c2_code(c2);
+      else
+        static_cast<float*>(out)[o] = c2;
+    }
+  }
+}
+
+// div_rn_lean's range (see there) from NarrowPrep's two words: every
+// denominator in [2^-80, 2^101] and every nonzero quotient >= 2^-100.
+__device__ __forceinline__ bool lean_division_ok(const unsigned* __restrict__ words) {
+  const float vmin = __uint_as_float(__ldg(words)), smax = __uint_as_float(__ldg(words + 1));
+  return vmin >= 0x1p-80f && smax <= 0x1p100f && vmin >= smax * 0x1p-100f;
 }
 
 // ---------------------------------------------------------------------------

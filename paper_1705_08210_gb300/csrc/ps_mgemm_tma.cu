@@ -36,7 +36,7 @@ struct __align__(128) SmemT {
   float B[STAGES][BK][C::BN];
   unsigned long long full[STAGES];
   unsigned long long empty[STAGES];
-  int tile_of[STAGES];  // dynamic schedule: tile of local tile lt at [lt % STAGES], -1 = none
+  int2 tile_of[STAGES];  // (I, J) of this CTA's local tile lt at [lt % STAGES]; I = -1: no tile left
   // producer state (thread 0 only; kept here to leave registers to the
   // micro-kernel): next slice to load, schedule exhausted, its tile
   uint32_t p_next;
@@ -59,12 +59,20 @@ __device__ __forceinline__ void compute_slice_tma(const float* As, const float* 
   }
 }
 
-template <int BK, int STAGES, int KU, bool FASTDIV, bool DYN>
+// EPI: epilogue of the interior tiles.  0: store_tile2 (__fdiv_rn).  1:
+// store_tile2_lean (branch-free correctly rounded division, FP32 sums with
+// zero-vector substitution from NarrowPrep) when the call's inputs are in
+// its range, else store_tile2.  2: as 1, for n_f <= 64: no compensated fold
+// (at most 64 fields per accumulator, the fold's own bound; values are the
+// same bit for bit, since a single fold of 0 + lo is exact) and the rows'
+// and columns' sums loaded when the tile starts.
+template <int BK, int STAGES, int KU, int EPI, bool DYN>
 __global__ void __launch_bounds__(C::NT, 1)
     mgemm2_tma_kernel(const __grid_constant__ CUtensorMap mapV, int nv, int nf,
                       const double* __restrict__ S, void* __restrict__ out, int mode, int T, int R0,
                       int R1, int G, int64_t ntiles, int* err, unsigned* __restrict__ sync, int sync_sl,
-                      unsigned long long* __restrict__ tile_ctr, unsigned long long wait_ns) {
+                      unsigned long long* __restrict__ tile_ctr, unsigned long long wait_ns,
+                      const float* __restrict__ Sf, const unsigned* __restrict__ lean_words) {
   static_assert(mg::FOLD * mg::BK % BK == 0, "a fold boundary ends a slice");
   constexpr int FOLD_SLICES = mg::FOLD * mg::BK / BK;  // 64 fields per compensated fold
   constexpr uint32_t SLICE_BYTES = 2u * BK * C::BM * sizeof(float);
@@ -88,7 +96,8 @@ __global__ void __launch_bounds__(C::NT, 1)
   // Tile schedule.  Static (tile_ctr null): this CTA's tiles are blockIdx.x,
   // blockIdx.x + gridDim.x, ...  Dynamic: the producer claims the next tile
   // of the walk from the grid-wide counter when it loads the tile's first
-  // slice and hands its index to the warps through tile_of; the tiles in
+  // slice.  Either way the producer hands the tile's coordinates (I, J) to
+  // the warps through tile_of (so no warp evaluates the walk); the tiles in
   // flight then always stay a window of about gridDim.x consecutive tiles
   // (which share their panels in L2), and a faster CTA simply takes more
   // tiles.  (Statically scheduled CTAs drift apart over the ~200 rounds at
@@ -106,6 +115,11 @@ __global__ void __launch_bounds__(C::NT, 1)
   const int cpt = (!DYN && sync_sl > 0) ? (nkb + sync_sl - 1) / sync_sl : 0;  // chunks per tile
   // producer: loads its next slice (waiting until the ring stage is free);
   // false on abort
+  // dynamic schedule: the producer's next claim, made one tile ahead of its
+  // use so that the atomic's latency is not on the producer's (a compute
+  // warp's) path; each CTA claims at most one tile past the end
+  unsigned long long next_claim = 0;
+  if (dyn && producer) next_claim = atomicAdd(tile_ctr, 1ull);
   auto issue_one = [&]() -> bool {
     SmemT<BK, STAGES>& sm = *reinterpret_cast<SmemT<BK, STAGES>*>(smem_raw);
     const uint32_t g = sm.p_next;
@@ -128,19 +142,21 @@ __global__ void __launch_bounds__(C::NT, 1)
     }
     if (!sy::bar_wait(&sm.empty[s], ph ^ 1u, &sm.abort, err, wait_ns)) return false;
     if (dyn && kb == 0) {
-      // (the stage being free means every warp has read tile_of of tile r - STAGES)
-      const unsigned long long t = atomicAdd(tile_ctr, 1ull);
+      const unsigned long long t = next_claim;
+      if (t < (unsigned long long)ntiles) next_claim = atomicAdd(tile_ctr, 1ull);
       if (t >= (unsigned long long)ntiles) {
-        sm.tile_of[r % STAGES] = -1;
+        sm.tile_of[r % STAGES] = make_int2(-1, -1);
         sy::bar_arrive(&sm.full[s]);  // completes the phase with no copies: the warps see -1 and stop
         sm.p_done = 1;
         return true;
       }
-      sm.tile_of[r % STAGES] = (int)t;  // published by the arrival below
       mg::band_tile((int64_t)t, T, R0, R1, G, pI, pJ);
       sm.pI = pI;
       sm.pJ = pJ;
     }
+    // the tile's coordinates for the warps, published by the arrival below
+    // (the stage being free means every warp has read entry r - STAGES)
+    if (kb == 0) sm.tile_of[r % STAGES] = make_int2(sm.pI, sm.pJ);
     pI = sm.pI;
     pJ = sm.pJ;
     sy::bar_arrive_tx(&sm.full[s], SLICE_BYTES);
@@ -156,10 +172,14 @@ __global__ void __launch_bounds__(C::NT, 1)
 
   const mg::Lanes<C> L;
   mg::Acc<true, C::NJ> acc;
+  // lean epilogue for this call: FP32 or one-byte output and inputs inside
+  // div_rn_lean's range (decided once, from NarrowPrep's words)
+  const bool lean = EPI != 0 && (mode == OUT2_C2_F32 || mode == OUT2_C2_U8) && mg::lean_division_ok(lean_words);
   uint32_t it = 0;
   bool ok = true;
   for (int lt = 0; ok && (dyn || lt < my_tiles); ++lt) {
-    int t = blockIdx.x + lt * gridDim.x;  // static schedule
+    int I = 0, J = 0;
+    float Sfi[8], Sfj[C::NJ];
     acc.zero();
     for (int kb = 0; kb < nkb; ++kb, ++it) {
       if (producer) ok = issue_one();  // slice it + STAGES - 1
@@ -169,38 +189,61 @@ __global__ void __launch_bounds__(C::NT, 1)
       // the common verdict so that it never diverges here
       const bool mine = ok && sy::bar_wait(&sm.full[s], ph, &sm.abort, err, wait_ns);
       if (!__all_sync(0xffffffffu, mine)) { ok = false; break; }
-      if (dyn && kb == 0) {
-        t = sm.tile_of[lt % STAGES];
-        if (t < 0) break;  // no tile left
+      if (kb == 0) {
+        const int2 ij = sm.tile_of[lt % STAGES];
+        I = ij.x;
+        J = ij.y;
+        if (I < 0) break;  // no tile left
+      }
+      if (EPI == 2 && kb == 0) {
+        // the epilogue's sums, loaded while the tile computes
+#pragma unroll
+        for (int r = 0; r < 8; ++r) Sfi[r] = lean ? __ldg(Sf + min(I * C::BM + L.row(r), nv - 1)) : 0.0f;
+#pragma unroll
+        for (int c = 0; c < C::NJ; ++c) Sfj[c] = lean ? __ldg(Sf + min(J * C::BN + L.col(c), nv - 1)) : 0.0f;
       }
       compute_slice_tma<BK, KU>(&sm.A[s][0][L.am], &sm.B[s][0][L.bn], acc);
       __syncwarp();
       if (lane == 0) sy::bar_arrive(&sm.empty[s]);
-      if ((kb + 1) % FOLD_SLICES == 0) acc.fold();
+      if (EPI != 2 && (kb + 1) % FOLD_SLICES == 0) acc.fold();
     }
-    if (!ok || t < 0) break;
-    acc.fold();
-    int I, J;
-    mg::band_tile(t, T, R0, R1, G, I, J);
-    mg::store_tile2<C, true, FASTDIV>(acc, L, I * C::BM, J * C::BN, nv, S, out, mode);
+    if (!ok || I < 0) break;
+    if (EPI != 2) acc.fold();
+    const int row0 = I * C::BM, col0 = J * C::BN;
+    if (EPI != 0 && lean && col0 >= row0 + C::BM && col0 + C::BN <= nv) {
+      if (EPI == 1) {
+#pragma unroll
+        for (int r = 0; r < 8; ++r) Sfi[r] = __ldg(Sf + row0 + L.row(r));
+#pragma unroll
+        for (int c = 0; c < C::NJ; ++c) Sfj[c] = __ldg(Sf + col0 + L.col(c));
+      }
+      // (EPI 2 never folds: hi is 0 and n2 is lo itself)
+      if (mode == OUT2_C2_U8)
+        mg::store_tile2_lean<C, true, true, EPI == 2>(acc, L, row0, col0, nv, Sfi, Sfj, out);
+      else
+        mg::store_tile2_lean<C, true, false, EPI == 2>(acc, L, row0, col0, nv, Sfi, Sfj, out);
+    } else {
+      mg::store_tile2<C, true>(acc, L, row0, col0, nv, S, out, mode);
+    }
   }
   __syncthreads();
   if (*(volatile int*)&sm.abort) sy::drain_after_abort();
 }
 
 // ---- host side ----
-template <int BK, int STAGES, int KU, bool FASTDIV = false, bool DYN = false>
+template <int BK, int STAGES, int KU, int EPI = 0, bool DYN = false>
 struct TmaLaunch {
   static constexpr size_t smem = sizeof(SmemT<BK, STAGES>);
   static cudaError_t run(ps_ctx* h, const VF32& V, const double* S, void* out, int mode, cudaStream_t st,
-                         int T, int R0, int R1, int G, int64_t ntiles, int* err, unsigned* sync) {
+                         int T, int R0, int R1, int G, int64_t ntiles, int* err, unsigned* sync,
+                         const NarrowPrep& np) {
     static std::mutex mu;
     static uint64_t attr_done = 0;
     {
       std::lock_guard<std::mutex> lk(mu);
       const uint64_t bit = 1ull << (h->device & 63);
       if (!(attr_done & bit)) {
-        const cudaError_t e = cudaFuncSetAttribute(mgemm2_tma_kernel<BK, STAGES, KU, FASTDIV, DYN>,
+        const cudaError_t e = cudaFuncSetAttribute(mgemm2_tma_kernel<BK, STAGES, KU, EPI, DYN>,
                                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         attr_done |= bit;
@@ -227,8 +270,8 @@ struct TmaLaunch {
     attr[0].val.cooperative = sync_sl ? 1 : 0;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, mgemm2_tma_kernel<BK, STAGES, KU, FASTDIV, DYN>, map, (int)V.nv, (int)V.nf, S, out,
-                              mode, T, R0, R1, G, ntiles, err, sync, sync_sl, tile_ctr, h->wait_ns);
+    return cudaLaunchKernelEx(&cfg, mgemm2_tma_kernel<BK, STAGES, KU, EPI, DYN>, map, (int)V.nv, (int)V.nf, S, out,
+                              mode, T, R0, R1, G, ntiles, err, sync, sync_sl, tile_ctr, h->wait_ns, np.Sf, np.words);
   }
 };
 
@@ -251,24 +294,35 @@ cudaError_t launch_mgemm2_tma(ps_ctx* h, const VF32& V, const double* S, void* o
   // k-steps per unrolled loop iteration: 16 (0 = automatic), 8 or 32
   const int ku = h->mgemm_tma_ku ? h->mgemm_tma_ku : 16;
   const int stages = h->mgemm_tma_stages;
-  // branch-free division in the epilogue where it is most of the work
-  // (n_f <= 256: 2.59 -> 2.33 ms at n_f = 16, nv = 32768); at large n_f its
-  // extra registers cost more than it saves (271.1 -> 275.8 ms at 8192)
-  const bool fastdiv = V.nf <= 256;
+  // the lean epilogue where the division is much of the work (n_f <= 256;
+  // see mgemm2_tma_kernel's EPI), without the compensated fold up to 64
+  // fields; at large n_f its registers would cost more than it saves
+  const int epi = (mode == OUT2_C2_F32 || mode == OUT2_C2_U8) ? (V.nf <= 64 ? 2 : (V.nf <= 256 ? 1 : 0)) : 0;
+  NarrowPrep np{nullptr, nullptr};
+  if (epi) {
+    float* Sf = static_cast<float*>(ws_get(h, WS_SUMSF, (size_t)round_up(V.nv, 64) * sizeof(float) + 256));
+    if (!Sf) return cudaErrorMemoryAllocation;
+    unsigned* words = reinterpret_cast<unsigned*>(Sf + round_up(V.nv, 64));
+    const cudaError_t e = launch_narrow_prep(V, S, Sf, words, st);
+    if (e != cudaSuccess) return e;
+    np = NarrowPrep{Sf, words};
+  }
   // dynamic tile schedule (the default) unless the producers are to meet,
   // which needs the static rounds; the other slice shapes are static only
   const bool dyn = h->mgemm_tma_dynamic && h->mgemm_tma_sync <= 0;
-#define PS_TMA_RUN(...) TmaLaunch<__VA_ARGS__>::run(h, V, S, out, mode, st, T, R0, R1, G, ntiles, err, sync)
+#define PS_TMA_RUN(...) TmaLaunch<__VA_ARGS__>::run(h, V, S, out, mode, st, T, R0, R1, G, ntiles, err, sync, np)
   if (bk == 16) {
-    if (fastdiv) return dyn ? PS_TMA_RUN(16, 8, 8, true, true) : PS_TMA_RUN(16, 8, 8, true);
-    return dyn ? PS_TMA_RUN(16, 8, 8, false, true) : PS_TMA_RUN(16, 8, 8);
+    // (16-field slices above n_f = 64 only when configured: the plain epilogue)
+    if (epi == 2) return dyn ? PS_TMA_RUN(16, 8, 8, 2, true) : PS_TMA_RUN(16, 8, 8, 2);
+    return dyn ? PS_TMA_RUN(16, 8, 8, 0, true) : PS_TMA_RUN(16, 8, 8);
   }
   if (bk == 64) return PS_TMA_RUN(64, 3, 16);
-  if (fastdiv) return dyn ? PS_TMA_RUN(32, 4, 16, true, true) : PS_TMA_RUN(32, 4, 16, true);
+  if (epi == 2) return dyn ? PS_TMA_RUN(32, 4, 16, 2, true) : PS_TMA_RUN(32, 4, 16, 2);
+  if (epi == 1) return dyn ? PS_TMA_RUN(32, 4, 16, 1, true) : PS_TMA_RUN(32, 4, 16, 1);
   if (stages == 6) return PS_TMA_RUN(32, 6, 16);
   if (ku == 8) return PS_TMA_RUN(32, 4, 8);
   if (ku == 32) return PS_TMA_RUN(32, 4, 32);
-  return dyn ? PS_TMA_RUN(32, 4, 16, false, true) : PS_TMA_RUN(32, 4, 16);
+  return dyn ? PS_TMA_RUN(32, 4, 16, 0, true) : PS_TMA_RUN(32, 4, 16);
 #undef PS_TMA_RUN
 }
 

@@ -184,6 +184,35 @@ __global__ void __launch_bounds__(256) count_invalid(const T* __restrict__ X, in
   if ((threadIdx.x & 31) == 0 && c) atomicAdd(bad, c);
 }
 
+// Epilogue inputs of the small-n_f 2-way kernels: Sf[i] = fl32(S_i), or 1.0
+// for an all-zero vector; words[1] = bits of max Sf; words[0] = bits of the
+// smallest nonzero entry of V (non-negative floats order like their bit
+// patterns; words are preset to 0x7f7f7f7f and 0 by the launcher).
+__global__ void __launch_bounds__(256) narrow_prep_kernel(VF32 V, const double* __restrict__ S,
+                                                          float* __restrict__ Sf, unsigned* __restrict__ words) {
+  unsigned smax = 0, vmin = 0xffffffffu;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < V.nv; i += stride) {
+    const float f = S[i] == 0.0 ? 1.0f : (float)S[i];
+    Sf[i] = f;
+    smax = max(smax, __float_as_uint(f));
+  }
+  const int64_t total = (int64_t)V.nf * V.nv;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += stride) {
+    const int64_t q = t / V.nv, i = t - q * V.nv;
+    const unsigned b = __float_as_uint(__ldg(V.p + q * V.ld + i));
+    if (b != 0u) vmin = min(vmin, b);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    smax = max(smax, __shfl_xor_sync(0xffffffffu, smax, o));
+    vmin = min(vmin, __shfl_xor_sync(0xffffffffu, vmin, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (vmin != 0xffffffffu) atomicMin(&words[0], vmin);
+    atomicMax(&words[1], smax);
+  }
+}
+
 }  // namespace
 
 cudaError_t launch_pack_half2(const VF32& V, uint32_t* out, int64_t ldo, unsigned* mx, float* inv_scale,
@@ -207,6 +236,16 @@ cudaError_t launch_count_invalid(const ps_matrix& V, unsigned long long* bad, cu
     count_invalid<float><<<grid, 256, 0, st>>>((const float*)V.data, V.ld, V.nv, V.nf, fm, bad);
   else
     count_invalid<double><<<grid, 256, 0, st>>>((const double*)V.data, V.ld, V.nv, V.nf, fm, bad);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_narrow_prep(const VF32& V, const double* S, float* Sf, unsigned* words, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(words, 0x7f, sizeof(unsigned), st);  // 3.4e38: no nonzero value yet
+  if (e == cudaSuccess) e = cudaMemsetAsync(words + 1, 0, sizeof(unsigned), st);
+  if (e != cudaSuccess || V.nv <= 0) return e;
+  const int64_t work = std::max<int64_t>(V.nv, (int64_t)V.nf * V.nv);
+  const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(work, 256), 152 * 16));
+  narrow_prep_kernel<<<grid, 256, 0, st>>>(V, S, Sf, words);
   return cudaGetLastError();
 }
 

@@ -495,7 +495,11 @@ extern "C" ps_status ps_proposal_train(ps_handle h, const ps_matrix* train, int3
       s = fail(h, PS_ERR_OOM, "training buffers");
       break;
     }
-    ps_status ts = ps_threshold_3way(h, &V, tau, 0, dh, cap, dcount, stream);
+    ps_status ts;
+    {
+      ScopedTimer tm(h, "proposal_labels", st);
+      ts = ps_threshold_3way(h, &V, tau, 0, dh, cap, dcount, stream);
+    }
     if (ts != PS_OK && ts != PS_ERR_CAPACITY) {
       s = ts;
       break;
@@ -564,21 +568,24 @@ extern "C" ps_status ps_proposal_train(ps_handle h, const ps_matrix* train, int3
     double* dloss = static_cast<double*>(mem.get(8));
     if (!buf || !grad || !dloss) s = fail(h, PS_ERR_OOM, "training state");
     double last = 0.0;
-    for (int it = 0; it < steps && s == PS_OK; ++it) {
-      const Set& S = sets[(size_t)it % sets.size()];
-      const int n = S.v.nv;
-      float* Hpre = buf;
-      float* H = Hpre + (size_t)n * MLP_HIDDEN;
-      float* E = H + (size_t)n * MLP_HIDDEN;
-      float* Pm = E + (size_t)n * MLP_OUT;
-      float* dE = Pm + (size_t)n * MLP_OUT;
-      float* dH = dE + (size_t)n * MLP_OUT;
-      cudaError_t e = mlp_pair_grad(h->mlp, S.v, S.r, S.pairs, S.y, S.np, Hpre, H, E, Pm, dE, dH, grad, dloss, st);
-      if (e == cudaSuccess) e = mlp_adam(h->mlp, grad, lr, st);
-      if (e != cudaSuccess) s = cuda_fail(h, e, "training step");
-      if (it == steps - 1 && s == PS_OK) {
-        cudaMemcpyAsync(&last, dloss, 8, cudaMemcpyDeviceToHost, st);
-        cudaStreamSynchronize(st);
+    {
+      ScopedTimer tm(h, "proposal_steps", st);  // the Adam steps, as one record
+      for (int it = 0; it < steps && s == PS_OK; ++it) {
+        const Set& S = sets[(size_t)it % sets.size()];
+        const int n = S.v.nv;
+        float* Hpre = buf;
+        float* H = Hpre + (size_t)n * MLP_HIDDEN;
+        float* E = H + (size_t)n * MLP_HIDDEN;
+        float* Pm = E + (size_t)n * MLP_OUT;
+        float* dE = Pm + (size_t)n * MLP_OUT;
+        float* dH = dE + (size_t)n * MLP_OUT;
+        cudaError_t e = mlp_pair_grad(h->mlp, S.v, S.r, S.pairs, S.y, S.np, Hpre, H, E, Pm, dE, dH, grad, dloss, st);
+        if (e == cudaSuccess) e = mlp_adam(h->mlp, grad, lr, st);
+        if (e != cudaSuccess) s = cuda_fail(h, e, "training step");
+        if (it == steps - 1 && s == PS_OK) {
+          cudaMemcpyAsync(&last, dloss, 8, cudaMemcpyDeviceToHost, st);
+          cudaStreamSynchronize(st);
+        }
       }
     }
     // theta: the (1 - target_recall) quantile of the positive pair scores

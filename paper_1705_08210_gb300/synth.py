@@ -61,14 +61,18 @@ def integer_levels(nv: int, nf: int, seed: int, levels: int = 16,
 
 def latent_profiles(nv: int, nf: int, seed: int, n_profiles: int = 64,
                     sigma: float = 0.25, p_zero: float = 0.85,
-                    dtype=np.float32):
+                    dtype=np.float32, profile_seed: int | None = None):
     """(nf, nv) field-major matrix v_i = a_i * P[z_i] + sigma * N_i.
 
     P holds n_profiles zero-inflated profiles, z_i ~ U{0..n_profiles-1},
     a_i ~ U[0.5, 1.5], N_i zero-inflated noise of the same distribution.
-    Returns (V, z) where z is the latent profile index of each vector."""
+    P is drawn from profile_seed (default: seed), z, a and N from seed, so
+    calls with the same profile_seed and different seeds draw fresh vectors
+    from one population.  Returns (V, z) where z is the latent profile index
+    of each vector."""
     rng = np.random.Generator(np.random.PCG64(seed))
-    P = zero_inflated(n_profiles, nf, seed + 7, p_zero=p_zero, dtype=np.float64)
+    pseed = seed if profile_seed is None else profile_seed
+    P = zero_inflated(n_profiles, nf, pseed + 7, p_zero=p_zero, dtype=np.float64)
     z = rng.integers(0, n_profiles, size=nv)
     a = rng.uniform(0.5, 1.5, size=nv)
     N = zero_inflated(nv, nf, seed + 11, p_zero=p_zero, dtype=np.float64)

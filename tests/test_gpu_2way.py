@@ -300,3 +300,41 @@ def test_fast_division_fallback_range(ps, handle, scale):
         np.testing.assert_array_equal(metrics_2way(ps, h, V), got)
     finally:
         h.close()
+
+
+@pytest.mark.parametrize("case", ["zero_inflated", "integer", "wide_range", "tiny_fallback", "huge_fallback"])
+@pytest.mark.parametrize("nf", [16, 64, 200])
+def test_lean_division_bit_identical(ps, handle, case, nf):
+    # the small-n_f epilogue (branch-free correctly rounded division, FP32
+    # sums with 1.0 for all-zero vectors, one range check per call) against
+    # the cp.async kernel, which divides with __fdiv_rn: every FP32 output
+    # and one-byte code bit-identical.  Integer data give many quotients that
+    # are powers of two; zero-inflated data at n_f = 16 many all-zero
+    # vectors; the fallback cases fall outside the range (smallest value
+    # below 2^-80, or sums above 2^100) and take __fdiv_rn everywhere.
+    nv = 3000
+    seed = synth.seed_for(1, 600 + nf)
+    if case == "integer":
+        V = synth.integer_levels(nv, nf, seed)
+    else:
+        V = synth.zero_inflated(nv, nf, seed)
+        if case == "wide_range":
+            rng = np.random.default_rng(seed)
+            V = (V * np.exp(rng.uniform(-14.0, 14.0, size=(1, nv)))).astype(np.float32)
+        elif case == "tiny_fallback":
+            V = (V.astype(np.float64) * 2.0 ** -90).astype(np.float32)
+        elif case == "huge_fallback":
+            V = (V.astype(np.float64) * 2.0 ** 100).astype(np.float32)
+    ref = oracle.c2_packed(oracle.to_vector_major(V))
+    lean32 = metrics_2way(ps, handle, V)
+    lean8 = metrics_2way(ps, handle, V, out_dtype=np.uint8)
+    if case == "integer":
+        np.testing.assert_array_equal(lean32, ref.astype(np.float32))
+    else:
+        assert_rel(lean32, ref, RTOL32, f"lean {case} nf={nf}")
+    h = ps.Handle(0, mgemm_feed=2)
+    try:
+        np.testing.assert_array_equal(metrics_2way(ps, h, V), lean32)
+        np.testing.assert_array_equal(metrics_2way(ps, h, V, out_dtype=np.uint8), lean8)
+    finally:
+        h.close()

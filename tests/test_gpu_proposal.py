@@ -58,6 +58,61 @@ def test_encoder_gradient_matches_fp64_oracle(ps, handle):
         assert err <= 2e-3 * scale, (name, err, scale)
 
 
+def _pair_grad_gpu(ps, handle, V, pairs, y, theta):
+    import torch
+    nv = V.shape[1]
+    n = ps.ps_proposal_param_count(handle.h)
+    ps.check(ps.ps_proposal_params(handle.h, 1, theta.ctypes.data, n, None), handle.h)
+    X = _dev(V)
+    m = ps.matrix(X)
+    dp, dy = _dev(pairs.astype(np.int32)), _dev(y.astype(np.float32))
+    E = torch.empty(nv * 64, device="cuda")
+    g = torch.empty(n, device="cuda")
+    loss = ctypes.c_double()
+    ps.check(ps.ps_proposal_pair_grad(handle.h, ctypes.byref(m), dp.data_ptr(), dy.data_ptr(), len(y),
+                                      E.data_ptr(), g.data_ptr(), ctypes.addressof(loss),
+                                      torch.cuda.current_stream().cuda_stream), handle.h)
+    return E.cpu().numpy().reshape(nv, 64), loss.value, g.cpu().numpy()
+
+
+@pytest.mark.parametrize("nv,d_in,scale", [(1100, 2048, 0.03), (300, 385, 0.08)])
+def test_encoder_full_width_within_derived_bounds(ps, handle, nv, d_in, scale):
+    # the encoder at the width of the searched 8192 x 2048 workload (d_in =
+    # 2048, 256 hidden, 64 outputs) on 1100 vectors (not a multiple of the
+    # 64-wide GEMM tiles): embeddings, loss and every gradient block against
+    # the FP64 oracle with the same BF16 weights, each element within the
+    # a-priori rounding-error bound of the FP32 arithmetic (tests/mlp_bounds.py)
+    from mlp_bounds import encoder_bounds
+    ps.check(ps.ps_proposal_init(handle.h, d_in, 4321), handle.h)
+    n = ps.ps_proposal_param_count(handle.h)
+    rng = np.random.default_rng(d_in)
+    theta = rng.normal(0, scale, size=n).astype(np.float32)
+    V, _ = synth.latent_profiles(nv, d_in, synth.seed_for(5, 400 + d_in), n_profiles=16, sigma=0.4)
+    npair = 3000
+    pairs = np.stack([rng.integers(0, nv, npair), rng.integers(0, nv, npair)], axis=1)
+    pairs = pairs[pairs[:, 0] != pairs[:, 1]]
+    y = (rng.random(len(pairs)) < 0.3).astype(np.float64)
+    gE, gloss, gg = _pair_grad_gpu(ps, handle, V, pairs, y, theta)
+    th = theta.astype(np.float64)
+    n1 = 256 * d_in
+    th[:n1] = mo.bf16_round(theta[:n1])
+    o = n1 + 256
+    th[o:o + 64 * 256] = mo.bf16_round(theta[o:o + 64 * 256])
+    ref_loss, ref_g, ref_E = mo.pair_loss_and_grad(th, V, pairs, y)
+    B = encoder_bounds(th, V, pairs, y)
+    errE = np.abs(gE - ref_E)
+    assert np.all(errE <= B["E"]), (errE.max(), float((errE / B["E"]).max()))
+    assert abs(gloss - ref_loss) <= B["loss"], (gloss, ref_loss, B["loss"])
+    worst = {}
+    for lo, hi, name in [(0, n1, "W1"), (n1, n1 + 256, "b1"), (o, o + 64 * 256, "W2"), (o + 64 * 256, n, "b2")]:
+        err = np.abs(gg[lo:hi] - ref_g[lo:hi])
+        ratio = err / np.maximum(B[name], 1e-300)
+        worst[name] = float(ratio.max())
+        assert np.all(err <= B[name]), (name, float(err.max()), worst[name])
+    print(f"encoder d_in={d_in} nv={nv}: max error / bound: E {float((errE / B['E']).max()):.3f}, "
+          + ", ".join(f"{k} {v:.3f}" for k, v in worst.items()))
+
+
 def _train_on_subsets(ps, handle, V, n_sub, size, steps=300, seed=5):
     """Train the encoder on the exact results of small random subsets of V."""
     import torch

@@ -36,13 +36,43 @@ def _run_both(ps, handle, V, out_dtype):
 
 def test_static_entry_matches_allocating_entry_twice(ps, handle):
     # two calls in a row with different sizes: the second must not see the
-    # first call's scratch contents
+    # first call's scratch contents.  Same values as ps_metrics_2way bit for
+    # bit (both kernels sum in the same order and round the same way), and
+    # sampled pairs against the FP64 oracle
+    import oracle
     cases = [((1000, 777, 1), ps.PS_F32), ((1500, 300, 2), ps.PS_F64)]
     for (nv, nf, sub), odt in cases:
         V = synth.zero_inflated(nv, nf, synth.seed_for(6, sub))
         got, ref = _run_both(ps, handle, V, odt)
         assert not np.isnan(got).any()
-        assert_rel(got, ref, RTOL32, f"static nv={nv}")
+        np.testing.assert_array_equal(got, ref)
+        pairs = synth.sample_pairs(nv, 3000, seed=sub)
+        idx = pairs[:, 0] * (2 * nv - pairs[:, 0] - 1) // 2 + (pairs[:, 1] - pairs[:, 0] - 1)
+        assert_rel(got[idx], oracle.c2_pairs(oracle.to_vector_major(V), pairs), RTOL32, f"static nv={nv}")
+
+
+def test_static_entry_allocates_no_device_memory(ps, handle):
+    # the property the entry point exists for: across a call (after the
+    # first one on this device, which loads the library's kernels) the
+    # device's free memory does not change
+    import torch
+    nv, nf = 4000, 500
+    V = synth.zero_inflated(nv, nf, synth.seed_for(6, 3))
+    X = torch.from_numpy(V).cuda()
+    m = ps.matrix(X)
+    out = torch.empty(nv * (nv - 1) // 2, device="cuda")
+    st = torch.cuda.current_stream().cuda_stream
+    assert ps.ps_metrics_2way_static(ctypes.byref(m), out.data_ptr(), ps.PS_F32, st) == ps.PS_OK
+    torch.cuda.synchronize()
+    first = out.clone()
+    free0, _ = torch.cuda.mem_get_info()
+    out.fill_(float("nan"))
+    torch.cuda.synchronize()
+    assert ps.ps_metrics_2way_static(ctypes.byref(m), out.data_ptr(), ps.PS_F32, st) == ps.PS_OK
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0, (free0, free1)
+    assert torch.equal(out, first)
 
 
 def test_static_entry_rejects_limits(ps, handle):
