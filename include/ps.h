@@ -202,12 +202,14 @@ typedef struct {
  *                    GEMM's producers; 0 = automatic (960), -1 = never.
  *   test_batched_stall : testing aid for the timeout path, 0 by default.
  *                    1 = the next ps_metrics_batched call (persistent mode)
- *                    raises its first dependency target by one item that
- *                    does not exist, so that the launch's dependency wait
- *                    runs out after wait_limit_ns and the call returns
- *                    PS_ERR_TIMEOUT; the setting then clears itself.  No
- *                    kernel is altered: the wait is an ordinary bounded
- *                    wait on a count that nothing completes. */
+ *                    raises one dependency target by one item that does not
+ *                    exist (the first 3-way problem's n2 table with the
+ *                    TMA-fed kernel, problem 0's sums with the cp.async
+ *                    kernels), so that the launch's dependency wait runs out
+ *                    after wait_limit_ns and the call returns PS_ERR_TIMEOUT;
+ *                    the setting then clears itself.  No kernel is altered:
+ *                    the wait is an ordinary bounded wait on a count that
+ *                    nothing completes. */
 typedef struct {
   int32_t precision;
   int32_t debug_checks;
@@ -397,17 +399,21 @@ typedef struct {
 #define PS_BATCH_PERSISTENT 0   /* one persistent launch, CUDA graph */
 #define PS_BATCH_PER_INSTANCE 1 /* one ps_metrics_2way/3way call each */
 
-/* All problems of the batch.  PS_BATCH_PERSISTENT: one persistent kernel
- * whose CTAs take work items (per-vector sum blocks, 2-way tiles, n2-table
- * tiles, 3-way pivot tiles of every problem, longest first) from an atomic
- * queue; a tile's epilogue waits for the items it depends on, which sit
- * earlier in the queue.  The launch is captured once per batch (same
- * shapes, pointers and kernel variant) into a CUDA graph kept in the handle
- * and replayed on later calls; the handle also keeps that batch's device
- * state (sums, n2 tables, work list) until ps_destroy.  Results are
- * bit-identical to PS_BATCH_PER_INSTANCE, which is the comparison point.
- * The kernel variant is the one ps_autotune_batched chose for these shapes,
- * else the default.  Synchronises `stream` (it reads the launch's error flag).
+/* All problems of the batch.  PS_BATCH_PERSISTENT: one CUDA graph holding
+ * the per-vector sums of every problem and one persistent kernel whose CTAs
+ * take work items (2-way tiles, n2-table tiles, 3-way pivot tiles of every
+ * problem, longest first) from an atomic queue; a 3-way epilogue waits for
+ * its problem's n2 table, whose tiles sit earlier in the queue.  Default
+ * kernel: TMA-fed (tensor maps per problem, mbarrier ring); the autotuner's
+ * other candidates are cp.async kernels that also take the sum blocks from
+ * the queue.  The graph is captured once per batch (same shapes, pointers,
+ * kernel variant and wait limit), kept in the handle and replayed on later
+ * calls; the handle also keeps that batch's device state (sums, n2 tables,
+ * work list) until ps_destroy.  Results are bit-identical to
+ * PS_BATCH_PER_INSTANCE, which is the comparison point.  The kernel variant
+ * is the one ps_autotune_batched chose for these shapes (or the configured
+ * autotune cache holds), else the default.  Synchronises `stream` (it reads
+ * the launch's error flag).
  * Errors: PS_ERR_INVALID_ARG for a problem outside the limits above;
  *   PS_ERR_TIMEOUT if a dependency wait inside the launch ran out
  *   (ps_config.wait_limit_ns; the handle stays usable);
@@ -415,9 +421,9 @@ typedef struct {
 ps_status ps_metrics_batched(ps_handle h, const ps_problem* probs, int32_t n,
                              int32_t mode, ps_stream stream);
 
-/* Autotuner of the batched launch: times every kernel configuration (tile
- * 128 x 128 with 8 or 16 warps or 64 x 64 with 2 warps; k-unroll depth 16, 8
- * or 4) on these problems, keeps the fastest for this batch shape in the
+/* Autotuner of the batched launch: times every kernel configuration (the
+ * TMA-fed kernel; cp.async kernels with tile 128 x 128 and 8 or 16 warps or
+ * 64 x 64 with 2 warps, k-unroll depth 16, 8 or 4) on these problems, keeps the fastest for this batch shape in the
  * handle and appends {"shape_signature", "variant", "ms"} as one JSON line to
  * cache_path (NULL: the handle's ps_config.autotune_cache, if any).  If that
  * file already holds this shape signature, its variant is used without

@@ -80,9 +80,12 @@ int cached_variant(const char* path, const char* sigs) {
   return best;
 }
 
-// candidate configurations of the autotuner (see mgemm_variant_code):
-// tile 128 (8 or 16 warps) or 64 x unroll depth 16, 8, 4, all packed adds
-const int kVariants[9] = {108, 116, 104, 1108, 1116, 1104, 2108, 2116, 2104};
+// candidate configurations of the autotuner: the TMA-fed kernel
+// (ps_batch_tma.cu, code 3000), and the cp.async kernel with tile 128 (8 or
+// 16 warps) or 64 x unroll depth 16, 8, 4, all packed adds (see
+// mgemm_variant_code)
+constexpr int kTmaVariant = 3000;
+const int kVariants[10] = {kTmaVariant, 108, 116, 104, 1108, 1116, 1104, 2108, 2116, 2104};
 
 bool known_variant(int v) {
   for (int k : kVariants)
@@ -225,6 +228,114 @@ ps_status build_batch(ps_ctx* h, const ps_problem* probs, int n, int variant, Ca
   return PS_OK;
 }
 
+// The TMA-fed variant (every problem needs n_f >= 1): problem records with
+// their tensor maps, (problem, 32-vector) sum blocks, and the work list
+// [2-way tiles + n2 tiles][3-way items], each group longest (largest n_f)
+// first.  stall: testing aid (ps_config.test_batched_stall): the first 3-way
+// problem's n2 target is raised by one warp store that never comes.
+ps_status build_batch_tma(ps_ctx* h, const ps_problem* probs, int n, CachedBatch* cb, bool stall = false) {
+  constexpr int B = 128;
+  std::vector<BatchProbTma> bp(n);
+  size_t off_S = 0, off_n2 = 0;
+  std::vector<size_t> oS(n), oN(n);
+  for (int t = 0; t < n; ++t) {
+    oS[t] = off_S;
+    off_S += (size_t)round_up(probs[t].V.nv, 32);
+    oN[t] = off_n2;
+    if (probs[t].way == 3) off_n2 += (size_t)probs[t].V.nv * probs[t].V.nv;
+  }
+  std::vector<int2> sblk;
+  std::vector<BatchItem> mid, tail;
+  bool stalled = false;
+  for (int t = 0; t < n; ++t) {
+    const ps_problem& p = probs[t];
+    const int nv = (int)p.V.nv;
+    for (int b = 0; b < (int)ceil_div(nv, 32); ++b) sblk.push_back(make_int2(t, b));
+    const int T = (int)ceil_div(nv, B);
+    for (int I = 0; I < T; ++I)
+      for (int J = I; J < T; ++J) mid.push_back({t, p.way == 2 ? BK_TILE2 : BK_N2, I, J});
+    if (p.way == 3) {
+      if (T >= 65536) return fail(h, PS_ERR_INVALID_ARG, "batched: nv too large for the 3-way item table");
+      for (int j = 0; j < nv; ++j) {
+        const int nI = (j + B - 1) / B, k0 = (j + 1) / B;
+        if (j + 1 >= nv) continue;
+        for (int I = 0; I < nI; ++I)
+          for (int K = k0; K < T; ++K) tail.push_back({t, BK_TILE3, j, (I << 16) | K});
+      }
+    }
+    if (!make_batch_prob_tma(&bp[t], static_cast<const float*>(p.V.data), p.V.nv, p.V.nf, p.V.ld))
+      return fail(h, PS_ERR_CUDA, "batched: tensor map of problem %d", t);
+    bp[t].way = p.way;
+    bp[t].out_f64 = p.out_dtype == PS_F64;
+    bp[t].out = p.out;
+    bp[t].n2_target = p.way == 3 ? (int)((int64_t)T * (T + 1) / 2 * 16) : 0;
+    if (stall && p.way == 3 && !stalled) {
+      bp[t].n2_target += 1;
+      stalled = true;
+    }
+  }
+  auto by_cost = [&](const BatchItem& a, const BatchItem& b) { return probs[a.prob].V.nf > probs[b.prob].V.nf; };
+  std::stable_sort(mid.begin(), mid.end(), by_cost);
+  std::stable_sort(tail.begin(), tail.end(), by_cost);
+  std::vector<BatchItem> items;
+  items.reserve(mid.size() + tail.size());
+  items.insert(items.end(), mid.begin(), mid.end());
+  items.insert(items.end(), tail.begin(), tail.end());
+  if (items.size() > 0x7fffffff || sblk.size() > 0x7fffffff)
+    return fail(h, PS_ERR_INVALID_ARG, "batched: too many work items");
+
+  const size_t bytes_S = round_up((int64_t)off_S * 8, 256);
+  const size_t bytes_n2 = round_up((int64_t)off_n2 * 4, 256);
+  const size_t bytes_p = round_up((int64_t)n * sizeof(BatchProbTma), 256);
+  const size_t bytes_b = round_up((int64_t)sblk.size() * sizeof(int2), 256);
+  const size_t bytes_i = round_up((int64_t)items.size() * sizeof(BatchItem), 256);
+  const size_t bytes_c = round_up((int64_t)(2 + n) * sizeof(int), 256);
+  char* mem = nullptr;
+  cudaError_t e = cudaMalloc(&mem, bytes_S + bytes_n2 + bytes_p + bytes_b + bytes_i + bytes_c);
+  if (e != cudaSuccess) return cuda_fail(h, e, "batched state");
+  cb->mem = mem;
+  double* S = reinterpret_cast<double*>(mem);
+  float* N2 = reinterpret_cast<float*>(mem + bytes_S);
+  char* q = mem + bytes_S + bytes_n2;
+  BatchProbTma* dprob = reinterpret_cast<BatchProbTma*>(q);
+  int2* dblk = reinterpret_cast<int2*>(q + bytes_p);
+  BatchItem* ditems = reinterpret_cast<BatchItem*>(q + bytes_p + bytes_b);
+  int* counters = reinterpret_cast<int*>(q + bytes_p + bytes_b + bytes_i);
+  for (int t = 0; t < n; ++t) {
+    bp[t].S = S + oS[t];
+    bp[t].n2 = probs[t].way == 3 ? N2 + oN[t] : nullptr;
+  }
+  PS_CUDA_TRY(h, cudaMemcpy(dprob, bp.data(), n * sizeof(BatchProbTma), cudaMemcpyHostToDevice));
+  PS_CUDA_TRY(h, cudaMemcpy(dblk, sblk.data(), sblk.size() * sizeof(int2), cudaMemcpyHostToDevice));
+  PS_CUDA_TRY(h, cudaMemcpy(ditems, items.data(), items.size() * sizeof(BatchItem), cudaMemcpyHostToDevice));
+  cb->counters = counters;
+  cb->nprob = n;
+  cb->nitems = (int)items.size();
+
+  // attributes are set outside the capture (an empty launch)
+  PS_CUDA_TRY(h, launch_batched_tma(h, dprob, dblk, 0, ditems, 0, counters, 0));
+  cudaStream_t cs;
+  PS_CUDA_TRY(h, cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  cudaGraph_t g = nullptr;
+  e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    cudaMemsetAsync(counters, 0, (2 + n) * sizeof(int), cs);
+    launch_batched_tma(h, dprob, dblk, (int)sblk.size(), ditems, cb->nitems, counters, cs);
+    e = cudaStreamEndCapture(cs, &g);
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&cb->exec, g, 0);
+  if (g) cudaGraphDestroy(g);
+  cudaStreamDestroy(cs);
+  if (e != cudaSuccess) return cuda_fail(h, e, "batched graph capture");
+  return PS_OK;
+}
+
+bool all_fields_nonempty(const ps_problem* probs, int n) {
+  for (int t = 0; t < n; ++t)
+    if (probs[t].V.nf < 1) return false;
+  return true;
+}
+
 // Reads the launch's error flag; PS_ERR_TIMEOUT if a dependency wait ran out.
 ps_status graph_status(ps_ctx* h, const CachedBatch& cb, cudaStream_t st) {
   int herr = 0;
@@ -241,7 +352,8 @@ ps_status run_graph(ps_ctx* h, const ps_problem* probs, int n, int variant, cuda
     h->batched_stall = 0;
     h->cfg.test_batched_stall = 0;
     CachedBatch cb;
-    ps_status s = build_batch(h, probs, n, variant, &cb, true);
+    ps_status s = variant == kTmaVariant ? build_batch_tma(h, probs, n, &cb, true)
+                                         : build_batch(h, probs, n, variant, &cb, true);
     if (s == PS_OK) {
       const cudaError_t e = cudaGraphLaunch(cb.exec, st);
       s = e == cudaSuccess ? graph_status(h, cb, st) : cuda_fail(h, e, "cudaGraphLaunch");
@@ -255,7 +367,7 @@ ps_status run_graph(ps_ctx* h, const ps_problem* probs, int n, int variant, cuda
   auto it = h->batch->graphs.find(key);
   if (it == h->batch->graphs.end()) {
     CachedBatch cb;
-    ps_status s = build_batch(h, probs, n, variant, &cb);
+    ps_status s = variant == kTmaVariant ? build_batch_tma(h, probs, n, &cb) : build_batch(h, probs, n, variant, &cb);
     if (s != PS_OK) {
       if (cb.exec) cudaGraphExecDestroy(cb.exec);
       if (cb.mem) cudaFree(cb.mem);
@@ -270,7 +382,11 @@ ps_status run_graph(ps_ctx* h, const ps_problem* probs, int n, int variant, cuda
   return graph_status(h, it->second, st);
 }
 
-int default_variant(ps_ctx* h) { return mgemm_variant_code(h); }
+// The TMA-fed kernel (every problem needs at least one field), else the
+// configured cp.async variant.
+int default_variant(ps_ctx* h, const ps_problem* probs, int n) {
+  return all_fields_nonempty(probs, n) ? kTmaVariant : mgemm_variant_code(h);
+}
 
 }  // namespace
 
@@ -312,7 +428,7 @@ extern "C" ps_status ps_metrics_batched(ps_handle h, const ps_problem* probs, in
     } else {
       // the handle's own tuning, else the configured autotune cache, else
       // the default variant
-      int variant = default_variant(h);
+      int variant = default_variant(h, probs, n);
       const uint64_t sig = shape_signature(probs, n);
       bool tuned = false;
       if (h->batch) {
@@ -326,7 +442,7 @@ extern "C" ps_status ps_metrics_batched(ps_handle h, const ps_problem* probs, in
         char sigs[32];
         snprintf(sigs, sizeof(sigs), "%016llx", (unsigned long long)sig);
         const int v = cached_variant(h->cache_path.c_str(), sigs);
-        if (known_variant(v)) variant = v;
+        if (known_variant(v) && (v != kTmaVariant || all_fields_nonempty(probs, n))) variant = v;
       }
       s = run_graph(h, probs, n, variant, st);
     }
@@ -358,6 +474,7 @@ extern "C" ps_status ps_autotune_batched(ps_handle h, const ps_problem* probs, i
     PS_CUDA_TRY(h, cudaEventCreate(&e1));
     float best_ms = 1e30f;
     for (int vc : kVariants) {
+      if (vc == kTmaVariant && !all_fields_nonempty(probs, n)) continue;
       s = run_graph(h, probs, n, vc, st);  // build + warm up
       if (s != PS_OK) break;
       float ms_min = 1e30f;
@@ -402,9 +519,13 @@ extern "C" ps_status ps_autotune_batched(ps_handle h, const ps_problem* probs, i
   h->batch->tuned[sig] = best;
   if (choice && choice_len > 0) {
     const int shape = best / 1000;
-    snprintf(choice, (size_t)choice_len, "tile %d x %d (%d warps), %s add, %d-step unroll%s",
-             shape == 1 ? 64 : 128, shape == 1 ? 64 : 128, shape == 1 ? 2 : (shape == 2 ? 16 : 8),
-             (best / 100) % 10 ? "packed f32x2" : "scalar", best % 100, detail.empty() ? " (cached)" : "");
+    if (best == kTmaVariant)
+      snprintf(choice, (size_t)choice_len, "TMA-fed pipeline, tile 128 x 128 (16 warps), 32-field slices%s",
+               detail.empty() ? " (cached)" : "");
+    else
+      snprintf(choice, (size_t)choice_len, "cp.async tile %d x %d (%d warps), %s add, %d-step unroll%s",
+               shape == 1 ? 64 : 128, shape == 1 ? 64 : 128, shape == 1 ? 2 : (shape == 2 ? 16 : 8),
+               (best / 100) % 10 ? "packed f32x2" : "scalar", best % 100, detail.empty() ? " (cached)" : "");
   }
   return PS_OK;
 }

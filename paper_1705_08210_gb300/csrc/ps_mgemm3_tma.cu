@@ -39,22 +39,7 @@ using C = mg::T128W16;  // 128 x 128 tile, 16 warps, 8 x 4 outputs per lane
 constexpr int NW = C::NT / 32;
 constexpr int PBOX = 4;  // pivot box: 4 vectors (16 bytes) x BK fields
 
-// Thread -> output coordinates (same interface as mg::Lanes).
-struct Lanes3 {
-  int am, bn;  // smem column offsets of the A / B fragments
-  int wrow0, wcol0;  // first row / column of this warp's 64 x 16 block
-  __device__ __forceinline__ Lanes3() {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int g = warp >> 2, s = warp & 3, e = (s + g) & 3;
-    const int wm = e & 1, wn = 2 * g + (e >> 1);
-    wrow0 = wm * 64;
-    wcol0 = wn * 16;
-    am = wrow0 + (lane >> 2) * 4;
-    bn = wcol0 + (lane & 3) * 4;
-  }
-  __device__ __forceinline__ int row(int r) const { return am + (r < 4 ? r : 28 + r); }
-  __device__ __forceinline__ int col(int c) const { return bn + c; }
-};
+using Lanes3 = mg::Lanes3;
 
 template <int BK, int STAGES>
 struct __align__(128) Smem3 {

@@ -337,6 +337,32 @@ struct Lanes {
   __device__ __forceinline__ int col(int c) const { return bn + (c < 4 ? c : 12 + c); }
 };
 
+// Thread -> output coordinates of the 16-warp 128 x 128 tile (T128W16) in
+// the TMA-fed 3-way and batched kernels (same interface as Lanes).  A warp
+// owns a 64-row x 16-column block.  In a 3-way tile that straddles the pivot,
+// warps whose whole block has no row i < j or no column k > j skip the
+// min-add loop; a skipped warp only helps if another warp on the same
+// scheduler (warps w, w+4, w+8, w+12 share one) takes the pipe, so warp
+// w = 4g + s (scheduler s) takes block e = (s + g) mod 4 of column group g
+// (columns 32g..32g+31): row half e & 1, column half e >> 1.  Then skipping
+// the lower row half, or any whole number of 32-column groups at the left
+// edge, removes the same number of blocks from every scheduler.
+struct Lanes3 {
+  int am, bn;        // smem column offsets of the A / B fragments
+  int wrow0, wcol0;  // first row / column of this warp's 64 x 16 block
+  __device__ __forceinline__ Lanes3() {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int g = warp >> 2, s = warp & 3, e = (s + g) & 3;
+    const int wm = e & 1, wn = 2 * g + (e >> 1);
+    wrow0 = wm * 64;
+    wcol0 = wn * 16;
+    am = wrow0 + (lane >> 2) * 4;
+    bn = wcol0 + (lane & 3) * 4;
+  }
+  __device__ __forceinline__ int row(int r) const { return am + (r < 4 ? r : 28 + r); }
+  __device__ __forceinline__ int col(int c) const { return bn + c; }
+};
+
 __host__ __device__ __forceinline__ int64_t pair_index(int64_t nv, int64_t i, int64_t j) {
   return i * (2 * nv - i - 1) / 2 + (j - i - 1);
 }
@@ -423,8 +449,8 @@ __host__ __device__ __forceinline__ int64_t pivot_tiles(int nv, int64_t j, int B
 // matrix (every i < j < nv) take a path without per-output checks.  Every
 // path gives the same correctly rounded values (store_tile2_lean below
 // too).
-template <class C, bool PACKED>
-__device__ __forceinline__ void store_tile2(const Acc<PACKED, C::NJ>& acc, const Lanes<C>& L, int row0,
+template <class C, bool PACKED, class LN = Lanes<C>>
+__device__ __forceinline__ void store_tile2(const Acc<PACKED, C::NJ>& acc, const LN& L, int row0,
                                             int col0, int64_t nv, const double* __restrict__ S,
                                             void* __restrict__ out, int mode) {
   const bool interior = col0 >= row0 + C::BM && col0 + C::BN <= nv;

@@ -89,7 +89,7 @@ def test_autotuner_writes_cache_and_reuses_it(ps, handle, tmp_path):
     buf = ctypes.create_string_buffer(128)
     ps.check(ps.ps_autotune_batched(handle.h, probs, 5, path.encode(), buf, 128, st), handle.h)
     lines = [json.loads(x) for x in open(path)]
-    assert len(lines) == 1 and len(lines[0]["ms"]) == 9
+    assert len(lines) == 1 and len(lines[0]["ms"]) == 10  # the TMA-fed kernel and 9 cp.async variants
     assert str(lines[0]["variant"]) in lines[0]["ms"]
     buf2 = ctypes.create_string_buffer(128)
     ps.check(ps.ps_autotune_batched(handle.h, probs, 5, path.encode(), buf2, 128, st), handle.h)
@@ -116,9 +116,10 @@ def test_batched_rejects_bad_problems(ps, handle):
 
 def test_dependency_wait_timeout_reports_and_handle_recovers(ps):
     # The timeout path of the persistent launch, in the allowed form: a
-    # dependency count that nothing completes.  test_batched_stall raises
-    # problem 0's per-vector-sums target by one block that does not exist;
-    # with a 1 ms wait limit the first tile epilogue that waits on it gives
+    # dependency count that nothing completes.  test_batched_stall raises the
+    # first 3-way problem's n2-table target by one store that never comes
+    # (TMA-fed kernel; the cp.async kernel raises problem 0's sums target);
+    # with a 1 ms wait limit the first 3-way epilogue that waits on it gives
     # up, raises the launch's error flag, every later wait sees the flag, and
     # the call returns PS_ERR_TIMEOUT.  No kernel is altered and no GPU wait
     # is unbounded.  The next call on the same handle is normal and correct.
