@@ -44,7 +44,8 @@ WORKLOADS = {
     # small cases of the same kernels for profiler captures
     "2way_8192x8192_f32": dict(way=2, nv=8192, nf=8192, number=2),
     "3way_1024x4096_f32": dict(way=3, nv=1024, nf=4096, number=3),
-    # output-bound shapes (few fields)
+    # output-bound shapes (few fields), and a small one for profiler captures
+    "2way_16384x16_f32": dict(way=2, nv=16384, nf=16, number=2),
     "2way_32768x16_f32": dict(way=2, nv=32768, nf=16, number=2),
     "2way_32768x64_f32": dict(way=2, nv=32768, nf=64, number=2),
     "2way_32768x385_f32": dict(way=2, nv=32768, nf=385, number=2),

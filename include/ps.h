@@ -523,7 +523,8 @@ ps_status ps_timing_read(ps_handle h, const char* kernel, int64_t* launches,
  * independent min/add chains over the whole GPU.  variant 0: scalar FP32
  * min + scalar FP32 add; variant 1: FP32 min + packed f32x2 add; variant 2:
  * the half2 path's operation, one packed FP16 min (two comparisons) and two
- * FP32 adds of its halves.
+ * FP32 adds of its halves; variant 3: the min as the signed-integer min of
+ * the bit patterns (equal for non-negative floats) + scalar FP32 add.
  *   cmp_per_s : comparisons (min+add pairs) per second.
  * Synchronises the device.  Errors: PS_ERR_INVALID_ARG for a bad variant. */
 ps_status ps_probe_minadd_peak(ps_handle h, int32_t variant,

@@ -96,7 +96,13 @@ __global__ void __launch_bounds__(256) probe_kernel(float* out, int iters, float
     }
   }
   for (int it = 0; VARIANT != 2 && it < iters; ++it) {
-    if (VARIANT == 0) {
+    if (VARIANT == 3) {
+      // the min of two non-negative floats as the signed-integer min of
+      // their bit patterns (the same value), scalar FP32 add
+#pragma unroll
+      for (int c = 0; c < PROBE_CHAINS; ++c)
+        x[c] = x[c] + __int_as_float(min(__float_as_int(x[c]), __float_as_int(y)));
+    } else if (VARIANT == 0) {
 #pragma unroll
       for (int c = 0; c < PROBE_CHAINS; ++c) x[c] = x[c] + fminf(x[c], y);
     } else {
@@ -349,7 +355,8 @@ cudaError_t probe_minadd(ps_ctx* h, int variant, double* cmp_per_s) {
     cudaEventRecord(e0, 0);
     if (variant == 0) probe_kernel<0><<<blocks, 256>>>(dout, iters, 1e-3f);
     else if (variant == 1) probe_kernel<1><<<blocks, 256>>>(dout, iters, 1e-3f);
-    else probe_kernel<2><<<blocks, 256>>>(dout, iters, 1e-3f);
+    else if (variant == 2) probe_kernel<2><<<blocks, 256>>>(dout, iters, 1e-3f);
+    else probe_kernel<3><<<blocks, 256>>>(dout, iters, 1e-3f);
     cudaEventRecord(e1, 0);
     e = cudaEventSynchronize(e1);
     if (e != cudaSuccess) break;

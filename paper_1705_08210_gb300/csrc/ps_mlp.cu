@@ -1,18 +1,15 @@
-// ps_mlp.cu -- the encoder of the learned block proposal: forward, pair-loss
-// backward and Adam kernels.
+// ps_mlp.cu -- the encoder of the learned block proposal: element-wise and
+// reduction kernels, the pair loss and its backward pass, Adam.
 //
 // Not in the paper.  e_i = W2 relu(W1 x_i + b1) + b2 with x_iq =
-// log1p(v_iq n_f / S_i) (scale-free input)
-// (d_in = n_f inputs, 256 hidden, 64 outputs), BF16 weights in the forward
-// and backward products, FP32 accumulation, FP32 master weights for Adam.
-// p_i = softmax(e_i) is a soft assignment to 64 learned clusters; a pair is
-// scored P_ij = p_i . p_j (probability of sharing a cluster), and training
-// minimises the binary cross-entropy of P against the label "the pair
-// belongs to a triple with c3 >= tau" (labels from the exact search).
-//
-// The products are small (n x d_in x 256 with n <= 8192): a shared-memory
-// tiled CUDA-core GEMM with FP32 accumulation is used for all of them; the
-// encoder costs well under 1% of the proposal pipeline.
+// log1p(v_iq n_f / S_i) (scale-free input) (d_in = n_f inputs, 256 hidden,
+// 64 outputs).  The five products of the forward and backward passes run on
+// the tensor cores (ps_mlp_tc.cu: BF16 operands, FP32 accumulation); FP32
+// master weights for Adam.  p_i = softmax(e_i) is a soft assignment to 64
+// learned clusters; a pair is scored P_ij = p_i . p_j (probability of sharing
+// a cluster), and training minimises the binary cross-entropy of P against
+// the label "the pair belongs to a triple with c3 >= tau" (labels from the
+// exact search).
 #include "ps_internal.cuh"
 
 #include <cuda_bf16.h>
@@ -23,63 +20,7 @@
 namespace ps {
 namespace {
 
-constexpr int GT = 64, GK = 16;  // GEMM tile (GT x GT outputs), k slice
-
-// C[m][n] = sum_k A(m, k) * B(n, k), then epi(m, n, acc).  256 threads, each
-// 4 x 4 outputs (rows ty + 16 r, columns tx + 16 c).
-template <class AccA, class AccB, class Epi>
-__global__ void __launch_bounds__(256) gemm_kernel(int M, int N, int K, AccA A, AccB B, Epi epi) {
-  __shared__ float As[GK][GT + 1];
-  __shared__ float Bs[GK][GT + 1];
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  const int m0 = blockIdx.y * GT, n0 = blockIdx.x * GT;
-  float acc[4][4] = {};
-  for (int k0 = 0; k0 < K; k0 += GK) {
-    for (int e = threadIdx.x; e < GK * GT; e += 256) {
-      const int kk = e / GT, r = e % GT;
-      const int k = k0 + kk;
-      As[kk][r] = (k < K && m0 + r < M) ? A(m0 + r, k) : 0.f;
-      Bs[kk][r] = (k < K && n0 + r < N) ? B(n0 + r, k) : 0.f;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int kk = 0; kk < GK; ++kk)
-#pragma unroll
-      for (int r = 0; r < 4; ++r)
-#pragma unroll
-        for (int c = 0; c < 4; ++c) acc[r][c] = fmaf(As[kk][ty + 16 * r], Bs[kk][tx + 16 * c], acc[r][c]);
-    __syncthreads();
-  }
-#pragma unroll
-  for (int r = 0; r < 4; ++r)
-#pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      const int m = m0 + ty + 16 * r, n = n0 + tx + 16 * c;
-      if (m < M && n < N) epi(m, n, acc[r][c]);
-    }
-}
-
-template <class AccA, class AccB, class Epi>
-cudaError_t gemm(int M, int N, int K, AccA A, AccB B, Epi epi, cudaStream_t st) {
-  if (M <= 0 || N <= 0) return cudaSuccess;
-  dim3 grid((unsigned)ceil_div(N, GT), (unsigned)ceil_div(M, GT));
-  gemm_kernel<<<grid, 256, 0, st>>>(M, N, K, A, B, epi);
-  return cudaGetLastError();
-}
-
-// ---- operand accessors ----
-struct XLog {  // x(i, q) = log1p(V[q*ld + i] * r[i]),  r[i] = n_f / S_i
-  const float* p;
-  int64_t ld;
-  const float* r;
-  __device__ float operator()(int i, int q) const { return log1pf(__ldg(p + (int64_t)q * ld + i) * r[i]); }
-};
-struct XLogT {  // x(q, i) (k = vector index)
-  const float* p;
-  int64_t ld;
-  const float* r;
-  __device__ float operator()(int q, int i) const { return log1pf(__ldg(p + (int64_t)q * ld + i) * r[i]); }
-};
+using bf16 = __nv_bfloat16;
 
 // r[i] = n_f / S_i (0 for an all-zero vector): the encoder input
 // log1p(v_iq * r_i) does not change when a vector is scaled.
@@ -87,64 +28,25 @@ __global__ void input_scale_kernel(const double* __restrict__ S, int n, int nf, 
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) r[i] = S[i] > 0.0 ? (float)((double)nf / S[i]) : 0.f;
 }
-struct RowBF {  // w(r, c) = W[r*ld + c] in BF16
-  const __nv_bfloat16* p;
-  int ld;
-  __device__ float operator()(int r, int c) const { return __bfloat162float(p[(int64_t)r * ld + c]); }
-};
-struct ColBF {  // w(c, r) = W[r*ld + c]
-  const __nv_bfloat16* p;
-  int ld;
-  __device__ float operator()(int c, int r) const { return __bfloat162float(p[(int64_t)r * ld + c]); }
-};
-struct RowF {  // a(r, c) = A[r*ld + c]
-  const float* p;
-  int ld;
-  __device__ float operator()(int r, int c) const { return p[(int64_t)r * ld + c]; }
-};
-struct ColF {  // a(c, r) = A[r*ld + c]
-  const float* p;
-  int ld;
-  __device__ float operator()(int c, int r) const { return p[(int64_t)r * ld + c]; }
-};
 
-// ---- epilogues ----
-struct EpiHidden {  // Hpre = acc + b1, H = relu(Hpre)
-  const float* b1;
-  float* Hpre;
-  float* H;
-  __device__ void operator()(int i, int h, float acc) const {
-    const float v = acc + b1[h];
-    Hpre[(int64_t)i * MLP_HIDDEN + h] = v;
-    H[(int64_t)i * MLP_HIDDEN + h] = v > 0.f ? v : 0.f;
-  }
-};
-struct EpiOut {  // E = acc + b2
-  const float* b2;
-  float* E;
-  __device__ void operator()(int i, int o, float acc) const { E[(int64_t)i * MLP_OUT + o] = acc + b2[o]; }
-};
-struct EpiStore {  // G[m][n] = acc
-  float* G;
-  int ld;
-  __device__ void operator()(int m, int n, float acc) const { G[(int64_t)m * ld + n] = acc; }
-};
-struct EpiReluGrad {  // dH = acc * [Hpre > 0]
-  const float* Hpre;
-  float* dH;
-  __device__ void operator()(int i, int h, float acc) const {
-    const int64_t o = (int64_t)i * MLP_HIDDEN + h;
-    dH[o] = Hpre[o] > 0.f ? acc : 0.f;
-  }
-};
-
-// Column sums of G (rows x cols) into out[cols] (fixed order per column).
-__global__ void colsum_kernel(const float* __restrict__ G, int rows, int cols, float* __restrict__ out) {
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= cols) return;
+// Column sums of G (rows x cols, row-major) into out[cols]: block b covers
+// columns 32b .. 32b + 31; thread (slice, column) adds rows slice, slice + 8,
+// ...; the eight partials are added in a fixed order (deterministic).
+__global__ void __launch_bounds__(256) colsum_kernel(const float* __restrict__ G, int rows, int cols,
+                                                     float* __restrict__ out) {
+  __shared__ float part[8][33];
+  const int c = blockIdx.x * 32 + (threadIdx.x & 31), sl = threadIdx.x >> 5;
   float s = 0.f;
-  for (int r = 0; r < rows; ++r) s += G[(int64_t)r * cols + c];
-  out[c] = s;
+  if (c < cols)
+    for (int r = sl; r < rows; r += 8) s += G[(int64_t)r * cols + c];
+  part[sl][threadIdx.x & 31] = s;
+  __syncthreads();
+  if (sl == 0 && c < cols) {
+    float t = part[0][threadIdx.x];
+#pragma unroll
+    for (int k = 1; k < 8; ++k) t += part[k][threadIdx.x];
+    out[c] = t;
+  }
 }
 
 // Row softmax P = softmax(E) (n x 64), one warp per row.
@@ -197,9 +99,11 @@ __global__ void pair_loss_kernel(const float* __restrict__ Pm, const int* __rest
   if (threadIdx.x == 0) atomicAdd(loss, sl[0] / (double)npairs);
 }
 
-// dE = p * (dP - (p . dP)) per row (softmax Jacobian), one warp per row.
-__global__ void softmax_backward_kernel(const float* __restrict__ Pm, const float* dPm, int n,
-                                        float* dE) {
+// dE = p * (dP - (p . dP)) per row (softmax Jacobian), one warp per row; also
+// the BF16 operands of the backward products: dEb (n x 64) and dEbT
+// (64 x ldn).
+__global__ void softmax_backward_kernel(const float* __restrict__ Pm, const float* dPm, int n, float* dE,
+                                        bf16* __restrict__ dEb, bf16* __restrict__ dEbT, int64_t ldn) {
   const int row = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
   if (row >= n) return;
   const int64_t o = (int64_t)row * MLP_OUT;
@@ -207,14 +111,27 @@ __global__ void softmax_backward_kernel(const float* __restrict__ Pm, const floa
   const float ga = dPm[o + lane], gb = dPm[o + 32 + lane];
   float dot = pa * ga + pb * gb;
   for (int s = 16; s > 0; s >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, s);
-  dE[o + lane] = pa * (ga - dot);
-  dE[o + 32 + lane] = pb * (gb - dot);
+  const float da = pa * (ga - dot), db = pb * (gb - dot);
+  dE[o + lane] = da;
+  dE[o + 32 + lane] = db;
+  const bf16 ba = __float2bfloat16_rn(da), bb = __float2bfloat16_rn(db);
+  dEb[o + lane] = ba;
+  dEb[o + 32 + lane] = bb;
+  dEbT[(int64_t)lane * ldn + row] = ba;
+  dEbT[(int64_t)(32 + lane) * ldn + row] = bb;
 }
 
-// Adam on the FP32 master weights; BF16 copies for the products.
+// The step counter of Adam lives on the device, so that a training step can
+// be replayed from a CUDA graph.
+__global__ void adam_step_kernel(int* __restrict__ step) { *step += 1; }
+
+// Adam on the FP32 master weights, step t = *step (bias corrections
+// 1 - b1^t and 1 - b2^t).
 __global__ void adam_kernel(float* __restrict__ w, const float* __restrict__ g, float* __restrict__ m,
-                            float* __restrict__ v, __nv_bfloat16* __restrict__ wb, int64_t n, float lr,
-                            float b1, float b2, float eps, float c1, float c2) {
+                            float* __restrict__ v, int64_t n, float lr, float b1, float b2, float eps,
+                            const int* __restrict__ step) {
+  const float t1 = (float)*step;
+  const float c1 = 1.f - powf(b1, t1), c2 = 1.f - powf(b2, t1);
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n;
        t += (int64_t)gridDim.x * blockDim.x) {
     const float gt = g[t];
@@ -222,16 +139,27 @@ __global__ void adam_kernel(float* __restrict__ w, const float* __restrict__ g, 
     const float vt = b2 * v[t] + (1.f - b2) * gt * gt;
     m[t] = mt;
     v[t] = vt;
-    const float wt = w[t] - lr * (mt / c1) / (sqrtf(vt / c2) + eps);
-    w[t] = wt;
-    if (wb) wb[t] = __float2bfloat16_rn(wt);
+    w[t] = w[t] - lr * (mt / c1) / (sqrtf(vt / c2) + eps);
   }
 }
 
-__global__ void to_bf16_kernel(const float* __restrict__ w, __nv_bfloat16* __restrict__ wb, int64_t n) {
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n;
-       t += (int64_t)gridDim.x * blockDim.x)
-    wb[t] = __float2bfloat16_rn(w[t]);
+// BF16 copies of the weights for the products: W1 (rows of pitch ld1), W2 and
+// its transpose.
+__global__ void to_bf16_kernel(const float* __restrict__ W1, int d_in, int64_t ld1, const float* __restrict__ W2,
+                               bf16* __restrict__ w1b, bf16* __restrict__ w2b, bf16* __restrict__ w2bt) {
+  const int64_t n1 = (int64_t)MLP_HIDDEN * d_in, n2 = (int64_t)MLP_OUT * MLP_HIDDEN;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n1 + n2;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    if (t < n1) {
+      const int64_t h = t / d_in, q = t - h * d_in;
+      w1b[h * ld1 + q] = __float2bfloat16_rn(W1[t]);
+    } else {
+      const int64_t u = t - n1, o = u / MLP_HIDDEN, h = u - o * MLP_HIDDEN;
+      const bf16 b = __float2bfloat16_rn(W2[u]);
+      w2b[u] = b;
+      w2bt[h * MLP_OUT + o] = b;
+    }
+  }
 }
 
 }  // namespace
@@ -249,9 +177,8 @@ cudaError_t mlp_softmax(const float* E, int n, float* Pm, cudaStream_t st) {
 }
 
 cudaError_t mlp_sync_bf16(MlpState& M, cudaStream_t st) {
-  const int64_t n1 = (int64_t)MLP_HIDDEN * M.d_in, n2 = (int64_t)MLP_OUT * MLP_HIDDEN;
-  to_bf16_kernel<<<256, 256, 0, st>>>(M.w, M.w1b, n1);
-  to_bf16_kernel<<<64, 256, 0, st>>>(M.w + n1 + MLP_HIDDEN, M.w2b, n2);
+  const float* W2 = M.w + (int64_t)MLP_HIDDEN * M.d_in + MLP_HIDDEN;
+  to_bf16_kernel<<<512, 256, 0, st>>>(M.w, M.d_in, round_up(M.d_in, 8), W2, M.w1b, M.w2b, M.w2bt);
   return cudaGetLastError();
 }
 
@@ -261,63 +188,37 @@ cudaError_t mlp_input_scale(const double* S, int n, int nf, float* r, cudaStream
   return cudaGetLastError();
 }
 
-// E (n x 64) for the n vectors of the FP32 field-major view V (n = V.nv);
-// r: per-vector input scales (mlp_input_scale).
-cudaError_t mlp_forward(MlpState& M, const VF32& V, const float* r, float* Hpre, float* H, float* E,
-                        cudaStream_t st) {
-  const float* b1 = M.w + (int64_t)MLP_HIDDEN * M.d_in;
-  const float* b2 = b1 + MLP_HIDDEN + (int64_t)MLP_OUT * MLP_HIDDEN;
-  cudaError_t e = gemm(V.nv, MLP_HIDDEN, M.d_in, XLog{V.p, V.ld, r}, RowBF{M.w1b, M.d_in},
-                       EpiHidden{b1, Hpre, H}, st);
-  if (e != cudaSuccess) return e;
-  return gemm(V.nv, MLP_OUT, MLP_HIDDEN, RowF{H, MLP_HIDDEN}, RowBF{M.w2b, MLP_HIDDEN}, EpiOut{b2, E},
-              st);
-}
-
-// Gradient of the mean pair loss w.r.t. all parameters (layout as above);
-// loss receives the mean loss.  Buffers: Hpre, H, dH (n x 256), E, Pm, dE
-// (n x 64); dE is also used for dP.
-cudaError_t mlp_pair_grad(MlpState& M, const VF32& V, const float* r, const int* pairs, const float* y,
-                          int64_t npairs, float* Hpre, float* H, float* E, float* Pm, float* dE, float* dH,
+cudaError_t mlp_pair_grad(MlpState& M, const MlpBufs& B, const int* pairs, const float* y, int64_t npairs,
                           float* grad, double* loss, cudaStream_t st) {
-  cudaError_t e = mlp_forward(M, V, r, Hpre, H, E, st);
+  cudaError_t e = mlp_forward_tc(M, B, true, st);
   if (e != cudaSuccess) return e;
-  const int n = V.nv;
+  const int n = B.n;
   const int64_t n1 = (int64_t)MLP_HIDDEN * M.d_in, n2 = (int64_t)MLP_OUT * MLP_HIDDEN;
   float* gW1 = grad;
   float* gb1 = grad + n1;
   float* gW2 = gb1 + MLP_HIDDEN;
   float* gb2 = gW2 + n2;
-  if ((e = mlp_softmax(E, n, Pm, st))) return e;
-  if ((e = cudaMemsetAsync(dE, 0, (size_t)n * MLP_OUT * sizeof(float), st))) return e;
+  if ((e = mlp_softmax(B.E, n, B.Pm, st))) return e;
+  if ((e = cudaMemsetAsync(B.dE, 0, (size_t)n * MLP_OUT * sizeof(float), st))) return e;
   if ((e = cudaMemsetAsync(loss, 0, sizeof(double), st))) return e;
   const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(npairs, 256), 1024));
-  pair_loss_kernel<<<g, 256, 0, st>>>(Pm, pairs, y, npairs, dE, loss);
+  pair_loss_kernel<<<g, 256, 0, st>>>(B.Pm, pairs, y, npairs, B.dE, loss);
   if ((e = cudaGetLastError())) return e;
   // dP -> dE in place (each row reads its own dP before writing)
-  softmax_backward_kernel<<<(unsigned)ceil_div(n, 8), 256, 0, st>>>(Pm, dE, n, dE);
+  softmax_backward_kernel<<<(unsigned)ceil_div(n, 8), 256, 0, st>>>(B.Pm, B.dE, n, B.dE, B.dEb, B.dEbT, B.ldn);
   if ((e = cudaGetLastError())) return e;
-  // dW2[o][h] = sum_i dE[i][o] H[i][h];  db2 = colsum(dE)
-  if ((e = gemm(MLP_OUT, MLP_HIDDEN, n, ColF{dE, MLP_OUT}, ColF{H, MLP_HIDDEN}, EpiStore{gW2, MLP_HIDDEN}, st)))
-    return e;
-  colsum_kernel<<<1, 64, 0, st>>>(dE, n, MLP_OUT, gb2);
-  // dH = (dE W2) * relu'(Hpre)
-  if ((e = gemm(n, MLP_HIDDEN, MLP_OUT, RowF{dE, MLP_OUT}, ColBF{M.w2b, MLP_HIDDEN},
-                EpiReluGrad{Hpre, dH}, st)))
-    return e;
-  // dW1[h][q] = sum_i dH[i][h] x[i][q];  db1 = colsum(dH)
-  if ((e = gemm(MLP_HIDDEN, M.d_in, n, ColF{dH, MLP_HIDDEN}, XLogT{V.p, V.ld, r}, EpiStore{gW1, M.d_in}, st)))
-    return e;
-  colsum_kernel<<<1, 256, 0, st>>>(dH, n, MLP_HIDDEN, gb1);
+  colsum_kernel<<<MLP_OUT / 32, 256, 0, st>>>(B.dE, n, MLP_OUT, gb2);  // db2
+  if ((e = cudaGetLastError())) return e;
+  if ((e = mlp_backward_tc(M, B, gW1, gW2, st))) return e;             // dW2, dH, dW1
+  colsum_kernel<<<MLP_HIDDEN / 32, 256, 0, st>>>(B.dH, n, MLP_HIDDEN, gb1);  // db1
   return cudaGetLastError();
 }
 
 cudaError_t mlp_adam(MlpState& M, const float* grad, float lr, cudaStream_t st) {
-  M.step += 1;
   const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
-  const float c1 = 1.f - powf(b1, (float)M.step), c2 = 1.f - powf(b2, (float)M.step);
   const int64_t n = mlp_param_count(M.d_in);
-  adam_kernel<<<512, 256, 0, st>>>(M.w, grad, M.m, M.v, nullptr, n, lr, b1, b2, eps, c1, c2);
+  adam_step_kernel<<<1, 1, 0, st>>>(M.dstep);
+  adam_kernel<<<512, 256, 0, st>>>(M.w, grad, M.m, M.v, n, lr, b1, b2, eps, M.dstep);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   return mlp_sync_bf16(M, st);

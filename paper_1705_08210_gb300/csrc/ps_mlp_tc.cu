@@ -24,6 +24,8 @@
 #include "ps_internal.cuh"
 #include "ps_sync.cuh"
 
+#include <cuda_bf16.h>
+
 #include <algorithm>
 #include <mutex>
 
@@ -186,5 +188,195 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                  : "memory");
 }
 
+template <int TN, class Epi>
+cudaError_t gemm_bf16(const __nv_bfloat16* A, int64_t lda, const __nv_bfloat16* B, int64_t ldb, int M, int N, int K,
+                      Epi epi, int* err, unsigned long long wait_ns, int device, cudaStream_t st) {
+  static std::mutex mu;
+  static uint64_t attr_done = 0;
+  const size_t smem = sizeof(SmemG<TN>) + 1024;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    const uint64_t bit = 1ull << (device & 63);
+    if (!(attr_done & bit)) {
+      const cudaError_t e =
+          cudaFuncSetAttribute(gemm_bf16_kernel<TN, Epi>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      attr_done |= bit;
+    }
+  }
+  if (M <= 0 || N <= 0 || K <= 0) return cudaSuccess;
+  // K-major BF16 operands seen as byte matrices (rows of pitch 2 ld bytes,
+  // 2 K valid bytes), boxes of 128 bytes x (128 or TN) rows, 128-byte swizzle
+  if ((uintptr_t)A % 16 || (uintptr_t)B % 16 || lda % 8 || ldb % 8) return cudaErrorInvalidValue;
+  CUtensorMap mA, mB;
+  if (!sy::make_map_u8_sw128(&mA, A, 2 * (int64_t)K, M, 2 * lda, KBYTES, TM) ||
+      !sy::make_map_u8_sw128(&mB, B, 2 * (int64_t)K, N, 2 * ldb, KBYTES, TN))
+    return cudaErrorInvalidValue;
+  const dim3 grid((unsigned)ceil_div(N, TN), (unsigned)ceil_div(M, TM));
+  gemm_bf16_kernel<TN, Epi><<<grid, NTHREADS, smem, st>>>(mA, mB, M, N, K, epi, err, wait_ns);
+  return cudaGetLastError();
+}
+
 }  // namespace tc
+
+namespace {
+
+using bf16 = __nv_bfloat16;
+
+// ---- epilogues of the five products ----
+struct EpiHidden {  // Hpre = acc + b1, H = relu(Hpre) in BF16 (and transposed)
+  const float* b1;
+  float* Hpre;
+  bf16* Hb;
+  bf16* HbT;  // may be null
+  int64_t ldn;
+  __device__ void operator()(int i, int h, float acc) const {
+    const float v = acc + b1[h];
+    Hpre[(int64_t)i * MLP_HIDDEN + h] = v;
+    const bf16 hb = __float2bfloat16_rn(v > 0.f ? v : 0.f);
+    Hb[(int64_t)i * MLP_HIDDEN + h] = hb;
+    if (HbT) HbT[(int64_t)h * ldn + i] = hb;
+  }
+};
+struct EpiOut {  // E = acc + b2
+  const float* b2;
+  float* E;
+  __device__ void operator()(int i, int o, float acc) const { E[(int64_t)i * MLP_OUT + o] = acc + b2[o]; }
+};
+struct EpiStoreT {  // G[col][row] = acc
+  float* G;
+  int64_t ld;
+  __device__ void operator()(int r, int c, float acc) const { G[(int64_t)c * ld + r] = acc; }
+};
+struct EpiStore {  // G[row][col] = acc
+  float* G;
+  int64_t ld;
+  __device__ void operator()(int r, int c, float acc) const { G[(int64_t)r * ld + c] = acc; }
+};
+struct EpiReluGrad {  // dH = acc [Hpre > 0] (FP32, and transposed in BF16)
+  const float* Hpre;
+  float* dH;
+  bf16* dHbT;
+  int64_t ldn;
+  __device__ void operator()(int i, int h, float acc) const {
+    const int64_t o = (int64_t)i * MLP_HIDDEN + h;
+    const float d = Hpre[o] > 0.f ? acc : 0.f;
+    dH[o] = d;
+    dHbT[(int64_t)h * ldn + i] = __float2bfloat16_rn(d);
+  }
+};
+
+// Encoder input x_iq = log1p(v_iq r_i) in BF16, vector-major (Xb, n x ldx)
+// and, when XbT is not null, field-major (XbT, d_in x ldn); 32 x 32 tiles
+// through shared memory.
+__global__ void __launch_bounds__(256) prep_x_kernel(VF32 V, const float* __restrict__ r, bf16* __restrict__ Xb,
+                                                     int64_t ldx, bf16* __restrict__ XbT, int64_t ldn) {
+  __shared__ bf16 tile[32][34];
+  const int i0 = blockIdx.x * 32, q0 = blockIdx.y * 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
+  for (int k = ty; k < 32; k += 8) {
+    const int q = q0 + k, i = i0 + tx;
+    bf16 x = __float2bfloat16_rn(0.f);
+    if (q < V.nf && i < V.nv) x = __float2bfloat16_rn(log1pf(__ldg(V.p + (int64_t)q * V.ld + i) * r[i]));
+    tile[k][tx] = x;
+    if (XbT && q < V.nf && i < V.nv) XbT[(int64_t)q * ldn + i] = x;
+  }
+  __syncthreads();
+  for (int k = ty; k < 32; k += 8) {
+    const int i = i0 + k, q = q0 + tx;
+    if (i < V.nv && q < V.nf) Xb[(int64_t)i * ldx + q] = tile[tx][k];
+  }
+}
+
+}  // namespace
+
+// The three forward / backward activations' BF16 operands and FP32 values of
+// n vectors, carved from one buffer of mlp_bufs_bytes(n, d_in) bytes.
+size_t mlp_bufs_bytes(int n, int d_in, bool with_x) {
+  const int64_t ldn = round_up(n, 8), ldx = round_up(d_in, 8);
+  size_t b = 0;
+  auto add = [&b](int64_t bytes) { b += (size_t)round_up(bytes, 256); };
+  add((int64_t)n * MLP_HIDDEN * 4);  // Hpre
+  add((int64_t)n * MLP_OUT * 4);     // E
+  add((int64_t)n * MLP_OUT * 4);     // Pm
+  add((int64_t)n * MLP_OUT * 4);     // dE
+  add((int64_t)n * MLP_HIDDEN * 4);  // dH
+  add((int64_t)n * 4);               // r
+  add((int64_t)n * MLP_HIDDEN * 2);  // Hb
+  add((int64_t)MLP_HIDDEN * ldn * 2);  // HbT
+  add((int64_t)n * MLP_OUT * 2);     // dEb
+  add((int64_t)MLP_OUT * ldn * 2);   // dEbT
+  add((int64_t)MLP_HIDDEN * ldn * 2);  // dHbT
+  if (with_x) {
+    add((int64_t)n * ldx * 2);       // Xb
+    add((int64_t)d_in * ldn * 2);    // XbT
+  }
+  return b + 256;
+}
+
+MlpBufs mlp_bufs_at(void* base, int n, int d_in, bool with_x) {
+  const int64_t ldn = round_up(n, 8), ldx = round_up(d_in, 8);
+  char* p = reinterpret_cast<char*>(round_up((int64_t)reinterpret_cast<uintptr_t>(base), 256));
+  auto take = [&p](int64_t bytes) {
+    char* q = p;
+    p += round_up(bytes, 256);
+    return q;
+  };
+  MlpBufs B;
+  B.n = n;
+  B.ldn = ldn;
+  B.ldx = ldx;
+  B.Hpre = reinterpret_cast<float*>(take((int64_t)n * MLP_HIDDEN * 4));
+  B.E = reinterpret_cast<float*>(take((int64_t)n * MLP_OUT * 4));
+  B.Pm = reinterpret_cast<float*>(take((int64_t)n * MLP_OUT * 4));
+  B.dE = reinterpret_cast<float*>(take((int64_t)n * MLP_OUT * 4));
+  B.dH = reinterpret_cast<float*>(take((int64_t)n * MLP_HIDDEN * 4));
+  B.r = reinterpret_cast<float*>(take((int64_t)n * 4));
+  B.Hb = reinterpret_cast<bf16*>(take((int64_t)n * MLP_HIDDEN * 2));
+  B.HbT = reinterpret_cast<bf16*>(take((int64_t)MLP_HIDDEN * ldn * 2));
+  B.dEb = reinterpret_cast<bf16*>(take((int64_t)n * MLP_OUT * 2));
+  B.dEbT = reinterpret_cast<bf16*>(take((int64_t)MLP_OUT * ldn * 2));
+  B.dHbT = reinterpret_cast<bf16*>(take((int64_t)MLP_HIDDEN * ldn * 2));
+  if (with_x) {
+    B.Xb = reinterpret_cast<bf16*>(take((int64_t)n * ldx * 2));
+    B.XbT = reinterpret_cast<bf16*>(take((int64_t)d_in * ldn * 2));
+  }
+  return B;
+}
+
+cudaError_t mlp_prep_x(const VF32& V, const float* r, bf16* Xb, int64_t ldx, bf16* XbT, int64_t ldn,
+                       cudaStream_t st) {
+  if (V.nv <= 0 || V.nf <= 0) return cudaSuccess;
+  if (ceil_div(V.nf, 32) > 65535) return cudaErrorInvalidConfiguration;
+  const dim3 grid((unsigned)ceil_div(V.nv, 32), (unsigned)ceil_div(V.nf, 32));
+  prep_x_kernel<<<grid, 256, 0, st>>>(V, r, Xb, ldx, XbT, ldn);
+  return cudaGetLastError();
+}
+
+// Hpre, Hb (and HbT when with_t) and E of the n vectors whose inputs are in
+// B.Xb: the first two products on the tensor cores.
+cudaError_t mlp_forward_tc(const MlpState& M, const MlpBufs& B, bool with_t, cudaStream_t st) {
+  const float* b1 = M.w + (int64_t)MLP_HIDDEN * M.d_in;
+  const float* b2 = b1 + MLP_HIDDEN + (int64_t)MLP_OUT * MLP_HIDDEN;
+  cudaError_t e = tc::gemm_bf16<128>(B.Xb, B.ldx, M.w1b, round_up(M.d_in, 8), B.n, MLP_HIDDEN, M.d_in,
+                                     EpiHidden{b1, B.Hpre, B.Hb, with_t ? B.HbT : nullptr, B.ldn}, M.err,
+                                     M.wait_ns, M.device, st);
+  if (e != cudaSuccess) return e;
+  return tc::gemm_bf16<64>(B.Hb, MLP_HIDDEN, M.w2b, MLP_HIDDEN, B.n, MLP_OUT, MLP_HIDDEN, EpiOut{b2, B.E},
+                           M.err, M.wait_ns, M.device, st);
+}
+
+// The three weight-side products of the backward pass: dW2^T = H^T dE (stored
+// transposed into dW2), dH = (dE W2) [Hpre > 0] and dW1 = dH^T X.
+cudaError_t mlp_backward_tc(const MlpState& M, const MlpBufs& B, float* gW1, float* gW2, cudaStream_t st) {
+  cudaError_t e = tc::gemm_bf16<64>(B.HbT, B.ldn, B.dEbT, B.ldn, MLP_HIDDEN, MLP_OUT, B.n, EpiStoreT{gW2, MLP_HIDDEN},
+                                    M.err, M.wait_ns, M.device, st);
+  if (e != cudaSuccess) return e;
+  e = tc::gemm_bf16<128>(B.dEb, MLP_OUT, M.w2bt, MLP_OUT, B.n, MLP_HIDDEN, MLP_OUT,
+                         EpiReluGrad{B.Hpre, B.dH, B.dHbT, B.ldn}, M.err, M.wait_ns, M.device, st);
+  if (e != cudaSuccess) return e;
+  return tc::gemm_bf16<128>(B.dHbT, B.ldn, B.XbT, B.ldn, MLP_HIDDEN, M.d_in, B.n, EpiStore{gW1, M.d_in}, M.err,
+                            M.wait_ns, M.device, st);
+}
+
 }  // namespace ps

@@ -205,16 +205,22 @@ ps_status mlp_alloc(ps_ctx* h, int d_in, uint64_t seed) {
   }
   M = MlpState();
   M.d_in = d_in;
+  M.device = h->device;
   const int64_t n = mlp_param_count(d_in);
   const int64_t n1 = (int64_t)MLP_HIDDEN * d_in, n2 = (int64_t)MLP_OUT * MLP_HIDDEN;
+  const int64_t n1p = (int64_t)MLP_HIDDEN * round_up(d_in, 8);  // W1 in BF16, rows padded to 16 bytes
   char* mem = nullptr;
-  const size_t bytes = (size_t)n * 12 + (size_t)(n1 + n2) * 2 + 1024;
+  const size_t bytes = (size_t)n * 12 + (size_t)(n1p + 2 * n2) * 2 + 4096;
   PS_CUDA_TRY(h, cudaMalloc(&mem, bytes));
+  PS_CUDA_TRY(h, cudaMemset(mem, 0, bytes));
   M.w = reinterpret_cast<float*>(mem);
   M.m = M.w + n;
   M.v = M.m + n;
   M.w1b = reinterpret_cast<__nv_bfloat16*>(reinterpret_cast<uintptr_t>(M.v + n + 64) & ~(uintptr_t)255);
-  M.w2b = M.w1b + n1;
+  M.w2b = reinterpret_cast<__nv_bfloat16*>(round_up((int64_t)reinterpret_cast<uintptr_t>(M.w1b + n1p), 256));
+  M.w2bt = M.w2b + n2;
+  M.err = reinterpret_cast<int*>(round_up((int64_t)reinterpret_cast<uintptr_t>(M.w2bt + n2), 256));
+  M.dstep = M.err + 32;
   // Glorot-uniform weights, zero biases (host generator)
   std::vector<float> w((size_t)n, 0.f);
   uint64_t s = seed;
@@ -236,6 +242,34 @@ void mlp_free(ps_ctx* h) {
   h->mlp = MlpState();
 }
 
+// The tensor-core products' error word: PS_ERR_TIMEOUT (and cleared) if a
+// pipeline wait ran out since the last check.  Synchronises `st`.
+ps_status mlp_take_error(ps_ctx* h, cudaStream_t st) {
+  int e = 0;
+  PS_CUDA_TRY(h, cudaMemcpyAsync(&e, h->mlp.err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  PS_CUDA_TRY(h, cudaStreamSynchronize(st));
+  if (e) {
+    PS_CUDA_TRY(h, cudaMemsetAsync(h->mlp.err, 0, sizeof(int), st));
+    return fail(h, PS_ERR_TIMEOUT, "encoder: a tensor-core pipeline wait timed out");
+  }
+  return PS_OK;
+}
+
+// Encoder outputs E of the n vectors of v (sums S) into buffers from WS_MLP.
+ps_status mlp_encode(ps_ctx* h, const VF32& v, const double* S, cudaStream_t st, MlpBufs* out) {
+  MlpState& M = h->mlp;
+  M.wait_ns = h->wait_ns;
+  const int n = v.nv;
+  void* base = ws_get(h, WS_MLP, mlp_bufs_bytes(n, M.d_in, true));
+  if (!base) return PS_ERR_OOM;
+  const MlpBufs B = mlp_bufs_at(base, n, M.d_in, true);
+  PS_CUDA_TRY(h, mlp_input_scale(S, n, v.nf, B.r, st));
+  PS_CUDA_TRY(h, mlp_prep_x(v, B.r, B.Xb, B.ldx, nullptr, B.ldn, st));
+  PS_CUDA_TRY(h, mlp_forward_tc(M, B, false, st));
+  *out = B;
+  return mlp_take_error(h, st);
+}
+
 // Reorder by learned cluster: perm, the reordered FP32 view and sums.
 ps_status proposal_reorder(ps_ctx* h, const VF32& v, const double* S, cudaStream_t st, VF32* vp,
                            double** Sp, int** perm) {
@@ -244,22 +278,19 @@ ps_status proposal_reorder(ps_ctx* h, const VF32& v, const double* S, cudaStream
   if (v.nf != M.d_in)
     return fail(h, PS_ERR_INVALID_ARG, "encoder expects nf=%d, matrix has nf=%d", M.d_in, v.nf);
   const int64_t ldp = round_up(n, 4);
-  float* buf = static_cast<float*>(ws_get(h, WS_MLP, (size_t)n * (2 * MLP_HIDDEN + 2 * MLP_OUT + 1) * 4));
   float* vperm = static_cast<float*>(ws_get(h, WS_PERMV, (size_t)v.nf * ldp * 4 + (size_t)n * 8 + 256));
   unsigned char* sortb = static_cast<unsigned char*>(ws_get(h, WS_HITS, (size_t)n * 24 + 256));
   int* dperm = static_cast<int*>(ws_get(h, WS_PERM, (size_t)n * 4 + 256));
   const size_t words = radix_sort_scratch_words(n);
   unsigned* scratch = static_cast<unsigned*>(ws_get(h, WS_SORT, words * 4));
-  if (!buf || !vperm || !sortb || !dperm || !scratch) return PS_ERR_OOM;
-  float* Hpre = buf;
-  float* H = Hpre + (size_t)n * MLP_HIDDEN;
-  float* E = H + (size_t)n * MLP_HIDDEN;
-  float* r = E + (size_t)n * 2 * MLP_OUT;
+  if (!vperm || !sortb || !dperm || !scratch) return PS_ERR_OOM;
+  MlpBufs B;
   {
     ScopedTimer tm(h, "proposal_encode", st);
-    PS_CUDA_TRY(h, mlp_input_scale(S, n, v.nf, r, st));
-    PS_CUDA_TRY(h, mlp_forward(M, v, r, Hpre, H, E, st));
+    const ps_status es = mlp_encode(h, v, S, st, &B);
+    if (es != PS_OK) return es;
   }
+  const float* E = B.E;
   unsigned long long* keys = reinterpret_cast<unsigned long long*>(sortb);
   unsigned long long* ktmp = keys + n;
   float* vals = reinterpret_cast<float*>(ktmp + n);
@@ -287,20 +318,15 @@ ps_status proposal_blocks_learned(ps_ctx* h, const VF32& vp, const double* Sp, c
   MlpState& M = h->mlp;
   const int n = vp.nv;
   const int T = (int)ceil_div(n, PT);
-  float* buf = static_cast<float*>(ws_get(h, WS_MLP, (size_t)n * (2 * MLP_HIDDEN + 2 * MLP_OUT + 1) * 4));
   float* tmax = static_cast<float*>(ws_get(h, WS_AUX2, (size_t)T * T * 4 + 256));
-  if (!buf || !tmax) return PS_ERR_OOM;
-  float* Hpre = buf;
-  float* H = Hpre + (size_t)n * MLP_HIDDEN;
-  float* E = H + (size_t)n * MLP_HIDDEN;
-  float* Pm = E + (size_t)n * MLP_OUT;
-  float* r = Pm + (size_t)n * MLP_OUT;
+  if (!tmax) return PS_ERR_OOM;
   {
     ScopedTimer tm(h, "proposal_score", st);
-    PS_CUDA_TRY(h, mlp_input_scale(Sp, n, vp.nf, r, st));
-    PS_CUDA_TRY(h, mlp_forward(M, vp, r, Hpre, H, E, st));
-    PS_CUDA_TRY(h, mlp_softmax(E, n, Pm, st));
-    tile_pair_max_kernel<<<(unsigned)((int64_t)T * (T + 1) / 2), 256, 0, st>>>(Pm, n, T, tmax);
+    MlpBufs B;
+    const ps_status es = mlp_encode(h, vp, Sp, st, &B);
+    if (es != PS_OK) return es;
+    PS_CUDA_TRY(h, mlp_softmax(B.E, n, B.Pm, st));
+    tile_pair_max_kernel<<<(unsigned)((int64_t)T * (T + 1) / 2), 256, 0, st>>>(B.Pm, n, T, tmax);
     PS_CUDA_TRY(h, cudaGetLastError());
   }
   std::vector<float> tm_h((size_t)T * T);
@@ -428,31 +454,27 @@ extern "C" ps_status ps_proposal_pair_grad(ps_handle h, const ps_matrix* V, cons
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   const int n = (int)V->nv;
   const VF32 v{static_cast<const float*>(V->data), V->ld, n, (int)V->nf};
-  float* buf = static_cast<float*>(ws_get(h, WS_MLP, (size_t)n * (3 * MLP_HIDDEN + 3 * MLP_OUT + 1) * 4 + 1024));
+  h->mlp.wait_ns = h->wait_ns;
+  void* base = ws_get(h, WS_MLP, mlp_bufs_bytes(n, h->mlp.d_in, true));
   double* dloss = static_cast<double*>(ws_get(h, WS_AUX3, 256));
   double* dS = static_cast<double*>(ws_get(h, WS_SUMS, (size_t)std::max(n, 1) * 8));
-  if (!buf || !dloss || !dS) return PS_ERR_OOM;
-  float* Hpre = buf;
-  float* H = Hpre + (size_t)n * MLP_HIDDEN;
-  float* E = H + (size_t)n * MLP_HIDDEN;
-  float* Pm = E + (size_t)n * MLP_OUT;
-  float* dE = Pm + (size_t)n * MLP_OUT;
-  float* dH = dE + (size_t)n * MLP_OUT;
-  float* r = dH + (size_t)n * MLP_HIDDEN;
+  if (!base || !dloss || !dS) return PS_ERR_OOM;
+  const MlpBufs B = mlp_bufs_at(base, n, h->mlp.d_in, true);
   cudaError_t e = launch_vector_sums(*V, dS, st);
-  if (e == cudaSuccess) e = mlp_input_scale(dS, n, (int)V->nf, r, st);
+  if (e == cudaSuccess) e = mlp_input_scale(dS, n, (int)V->nf, B.r, st);
+  if (e == cudaSuccess) e = mlp_prep_x(v, B.r, B.Xb, B.ldx, B.XbT, B.ldn, st);
   if (e != cudaSuccess) {
   } else if (grad && npairs > 0) {
-    e = mlp_pair_grad(h->mlp, v, r, pairs, labels, npairs, Hpre, H, E, Pm, dE, dH, grad, dloss, st);
+    e = mlp_pair_grad(h->mlp, B, pairs, labels, npairs, grad, dloss, st);
     if (e == cudaSuccess && loss) e = cudaMemcpyAsync(loss, dloss, 8, cudaMemcpyDefault, st);
   } else {
-    e = mlp_forward(h->mlp, v, r, Hpre, H, E, st);
+    e = mlp_forward_tc(h->mlp, B, false, st);
   }
-  if (e == cudaSuccess && E_out) e = cudaMemcpyAsync(E_out, E, (size_t)n * MLP_OUT * 4, cudaMemcpyDefault, st);
+  if (e == cudaSuccess && E_out) e = cudaMemcpyAsync(E_out, B.E, (size_t)n * MLP_OUT * 4, cudaMemcpyDefault, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  ps_status s = e == cudaSuccess ? mlp_take_error(h, st) : cuda_fail(h, e, "ps_proposal_pair_grad");
   if (prev >= 0) cudaSetDevice(prev);
-  if (e != cudaSuccess) return cuda_fail(h, e, "ps_proposal_pair_grad");
-  return PS_OK;
+  return s;
 }
 
 extern "C" ps_status ps_proposal_train(ps_handle h, const ps_matrix* train, int32_t ntrain, float tau,
@@ -476,12 +498,15 @@ extern "C" ps_status ps_proposal_train(ps_handle h, const ps_matrix* train, int3
   struct Set {
     VF32 v;
     float* r;
+    __nv_bfloat16* Xb;   // encoder inputs in BF16 (n x ldx) and field-major (d_in x ldn)
+    __nv_bfloat16* XbT;
     int* pairs;
     float* y;
     int64_t np;
     int* pos;
     int64_t npos;
   };
+  h->mlp.wait_ns = h->wait_ns;
   std::vector<Set> sets;
   uint64_t rs = seed;
   for (int t = 0; t < ntrain && s == PS_OK; ++t) {
@@ -542,7 +567,15 @@ extern "C" ps_status ps_proposal_train(ps_handle h, const ps_matrix* train, int3
       s = fail(h, PS_ERR_OOM, "training scales");
       break;
     }
-    if (launch_vector_sums(V, sums, st) != cudaSuccess || mlp_input_scale(sums, n, (int)V.nf, S.r, st) != cudaSuccess) {
+    const int64_t ldn = round_up(n, 8), ldx = round_up(V.nf, 8);
+    S.Xb = static_cast<__nv_bfloat16*>(mem.get((size_t)n * ldx * 2));
+    S.XbT = static_cast<__nv_bfloat16*>(mem.get((size_t)V.nf * ldn * 2));
+    if (!S.Xb || !S.XbT) {
+      s = fail(h, PS_ERR_OOM, "training inputs");
+      break;
+    }
+    if (launch_vector_sums(V, sums, st) != cudaSuccess || mlp_input_scale(sums, n, (int)V.nf, S.r, st) != cudaSuccess ||
+        mlp_prep_x(S.v, S.r, S.Xb, ldx, S.XbT, ldn, st) != cudaSuccess) {
       s = fail(h, PS_ERR_CUDA, "training scales");
       break;
     }
@@ -563,24 +596,47 @@ extern "C" ps_status ps_proposal_train(ps_handle h, const ps_matrix* train, int3
     int nmax = 0;
     for (const Set& S : sets) nmax = std::max(nmax, S.v.nv);
     const int64_t np_all = mlp_param_count(h->mlp.d_in);
-    float* buf = static_cast<float*>(mem.get((size_t)nmax * (3 * MLP_HIDDEN + 3 * MLP_OUT) * 4));
+    void* buf = mem.get(mlp_bufs_bytes(nmax, h->mlp.d_in, false));
     float* grad = static_cast<float*>(mem.get((size_t)np_all * 4));
     double* dloss = static_cast<double*>(mem.get(8));
     if (!buf || !grad || !dloss) s = fail(h, PS_ERR_OOM, "training state");
+    // activations of set S (its own inputs)
+    auto bufs_of = [&](const Set& S) {
+      MlpBufs B = mlp_bufs_at(buf, S.v.nv, h->mlp.d_in, false);
+      B.Xb = S.Xb;
+      B.XbT = S.XbT;
+      return B;
+    };
     double last = 0.0;
+    // One CUDA graph per training matrix holds a whole step (forward,
+    // backward, Adam); the steps replay them in turn.  A gradient pass
+    // outside the capture first sets the kernels' attributes.
+    std::vector<cudaGraphExec_t> gx;
+    cudaStream_t cs = nullptr;
+    if (s == PS_OK && steps > 0) {
+      cudaError_t e = mlp_pair_grad(h->mlp, bufs_of(sets[0]), sets[0].pairs, sets[0].y, sets[0].np, grad, dloss, st);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+      if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+      for (size_t k = 0; k < sets.size() && e == cudaSuccess; ++k) {
+        const Set& S = sets[k];
+        cudaGraph_t g = nullptr;
+        e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) break;
+        cudaError_t e1 = mlp_pair_grad(h->mlp, bufs_of(S), S.pairs, S.y, S.np, grad, dloss, cs);
+        if (e1 == cudaSuccess) e1 = mlp_adam(h->mlp, grad, lr, cs);
+        e = cudaStreamEndCapture(cs, &g);
+        if (e == cudaSuccess) e = e1;
+        cudaGraphExec_t x = nullptr;
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&x, g, 0);
+        if (g) cudaGraphDestroy(g);
+        if (e == cudaSuccess) gx.push_back(x);
+      }
+      if (e != cudaSuccess) s = cuda_fail(h, e, "training step graphs");
+    }
     {
       ScopedTimer tm(h, "proposal_steps", st);  // the Adam steps, as one record
       for (int it = 0; it < steps && s == PS_OK; ++it) {
-        const Set& S = sets[(size_t)it % sets.size()];
-        const int n = S.v.nv;
-        float* Hpre = buf;
-        float* H = Hpre + (size_t)n * MLP_HIDDEN;
-        float* E = H + (size_t)n * MLP_HIDDEN;
-        float* Pm = E + (size_t)n * MLP_OUT;
-        float* dE = Pm + (size_t)n * MLP_OUT;
-        float* dH = dE + (size_t)n * MLP_OUT;
-        cudaError_t e = mlp_pair_grad(h->mlp, S.v, S.r, S.pairs, S.y, S.np, Hpre, H, E, Pm, dE, dH, grad, dloss, st);
-        if (e == cudaSuccess) e = mlp_adam(h->mlp, grad, lr, st);
+        cudaError_t e = cudaGraphLaunch(gx[(size_t)it % gx.size()], st);
         if (e != cudaSuccess) s = cuda_fail(h, e, "training step");
         if (it == steps - 1 && s == PS_OK) {
           cudaMemcpyAsync(&last, dloss, 8, cudaMemcpyDeviceToHost, st);
@@ -588,20 +644,20 @@ extern "C" ps_status ps_proposal_train(ps_handle h, const ps_matrix* train, int3
         }
       }
     }
+    cudaStreamSynchronize(st);
+    for (cudaGraphExec_t x : gx) cudaGraphExecDestroy(x);
+    if (cs) cudaStreamDestroy(cs);
     // theta: the (1 - target_recall) quantile of the positive pair scores
     std::vector<float> zs;
     for (const Set& S : sets) {
       if (s != PS_OK) break;
       const int n = S.v.nv;
-      float* Hpre = buf;
-      float* H = Hpre + (size_t)n * MLP_HIDDEN;
-      float* E = H + (size_t)n * MLP_HIDDEN;
+      const MlpBufs B = bufs_of(S);
       float* zz = static_cast<float*>(mem.get((size_t)std::max<int64_t>(S.npos, 1) * 4));
-      float* Pm = E + (size_t)n * MLP_OUT;
-      cudaError_t e = mlp_forward(h->mlp, S.v, S.r, Hpre, H, E, st);
-      if (e == cudaSuccess) e = mlp_softmax(E, n, Pm, st);
+      cudaError_t e = mlp_forward_tc(h->mlp, B, false, st);
+      if (e == cudaSuccess) e = mlp_softmax(B.E, n, B.Pm, st);
       if (e == cudaSuccess && S.npos > 0) {
-        pair_score_kernel<<<256, 256, 0, st>>>(Pm, S.pos, S.npos, zz);
+        pair_score_kernel<<<256, 256, 0, st>>>(B.Pm, S.pos, S.npos, zz);
         e = cudaGetLastError();
       }
       std::vector<float> hz((size_t)S.npos);
@@ -610,6 +666,7 @@ extern "C" ps_status ps_proposal_train(ps_handle h, const ps_matrix* train, int3
       if (e != cudaSuccess) s = cuda_fail(h, e, "calibration");
       zs.insert(zs.end(), hz.begin(), hz.end());
     }
+    if (s == PS_OK) s = mlp_take_error(h, st);
     if (s == PS_OK) {
       std::sort(zs.begin(), zs.end());
       float theta = -INFINITY;

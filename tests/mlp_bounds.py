@@ -2,19 +2,24 @@
 the tolerances of its GPU parity tests (test infrastructure).
 
 The GPU computes the encoder of oracle/mlp_oracle.py with the same BF16
-weights but in FP32: inputs x = log1pf(v * r) with r = fl32(n_f / S), every
-product as a sequential FMA dot product with FP32 accumulation, FP32 softmax
-and pair scores, and atomically accumulated (any-order) FP32 sums for the
-backward pass.  The standard bound for an n-term FP32 dot product,
+weights: inputs x = log1pf(v * r) with r = fl32(n_f / S); the five products
+(W1 x, W2 h, dW2 = dE^T h, dh = dE W2, dW1 = dh^T x) on the tensor cores with
+BF16 operands (x, h = relu(Hpre), dE and dh each rounded to BF16 before the
+product that reads them: relative error <= 2^-9) and FP32 accumulation; FP32
+softmax and pair scores; atomically accumulated (any-order) FP32 sums for
+the backward pass and FP32 column sums for the bias gradients.  The
+standard bound for an n-term dot product accumulated in FP32,
 |fl(a.b) - a.b| <= gamma_n |a|.|b| with gamma_n = n u / (1 - n u),
-u = 2^-24, is applied to every product, and errors of the inputs of each
-stage are carried forward to first order with the stage's absolute
-sensitivity (relu and the clamp are 1-Lipschitz; the softmax satisfies
-|dp_k| <= p_k (|dE_k| + max_m |dE_m|)).  The returned bounds are twice the
-first-order sums, which covers the neglected second-order terms (of relative
-size u) by a wide margin.  Where a rounding-level change could flip a ReLU
-mask (|Hpre| within its own bound), the bound of the affected hidden unit's
-gradient takes the whole unmasked value.
+u = 2^-24, is applied to every product (whatever the order the tensor cores
+add in), the BF16 rounding of each operand adds 2^-9 times its magnitude,
+and errors of the inputs of each stage are carried forward to first order
+with the stage's absolute sensitivity (relu and the clamp are 1-Lipschitz;
+the softmax satisfies |dp_k| <= p_k (|dE_k| + max_m |dE_m|)).  The returned
+bounds are twice the first-order sums, which covers the neglected
+second-order terms (of relative size 2^-9) by a wide margin.  Where a
+rounding-level change could flip a ReLU mask (|Hpre| within its own bound),
+the bound of the affected hidden unit's gradient takes the whole unmasked
+value.
 """
 from __future__ import annotations
 
@@ -23,6 +28,7 @@ import numpy as np
 from oracle import mlp_oracle as mo
 
 U = 2.0 ** -24
+UB = 2.0 ** -9  # BF16 round-to-nearest, relative
 
 
 def gamma(n: int) -> float:
@@ -38,10 +44,10 @@ def encoder_bounds(theta: np.ndarray, V_fm: np.ndarray, pairs: np.ndarray, y: np
     E, (X, Hpre, H, _, _) = mo.forward(theta, V_fm)
     aW1, aW2 = np.abs(W1), np.abs(W2)
     n = X.shape[0]
-    # inputs: r rounded once, v*r once, log1pf within 2 ulp
-    BX = 2.0 ** -22 * np.abs(X) + 2.0 ** -23
+    # inputs: r rounded once, v*r once, log1pf within 2 ulp, then BF16
+    BX = (2.0 ** -22 + UB) * np.abs(X) + 2.0 ** -23
     BHpre = gamma(d_in + 1) * (np.abs(X) @ aW1.T + np.abs(b1)) + BX @ aW1.T
-    BH = BHpre
+    BH = BHpre + UB * np.abs(H)  # the BF16 operand h
     BE = gamma(mo.HIDDEN + 1) * (np.abs(H) @ aW2.T + np.abs(b2)) + BH @ aW2.T
     Pm = mo.softmax(E)
     # softmax: first-order sensitivity plus its own FP32 arithmetic (exp,
@@ -75,17 +81,19 @@ def encoder_bounds(theta: np.ndarray, V_fm: np.ndarray, pairs: np.ndarray, y: np
     dE = Pm * (dP - s)
     BdE = BPm * (np.abs(dP) + np.abs(s)) + Pm * (BdP + Bs) + 4 * U * np.abs(dE)
     adE = np.abs(dE)
-    BdW2 = gamma(n) * (adE.T @ np.abs(H)) + BdE.T @ np.abs(H) + adE.T @ BH
+    BdEo = BdE + UB * adE                          # the BF16 operand dE
+    BdW2 = gamma(n) * (adE.T @ np.abs(H)) + BdEo.T @ np.abs(H) + adE.T @ BH
     Bdb2 = gamma(n) * adE.sum(axis=0) + BdE.sum(axis=0)
     mask = Hpre > 0
     dHu = dE @ W2                                  # before the ReLU mask
-    BdHu = gamma(64) * (adE @ aW2) + BdE @ aW2
+    BdHu = gamma(64) * (adE @ aW2) + BdEo @ aW2
     dH = dHu * mask
     BdH = np.where(mask, BdHu, 0.0)
     unsure = np.abs(Hpre) <= BHpre                 # a rounding-level change may flip the mask
     BdH = np.where(unsure, np.abs(dHu) + BdHu, BdH)
     adH = np.abs(dH)
-    BdW1 = gamma(n) * (adH.T @ np.abs(X)) + BdH.T @ np.abs(X) + adH.T @ BX
+    BdHo = BdH + UB * adH                          # the BF16 operand dh
+    BdW1 = gamma(n) * (adH.T @ np.abs(X)) + BdHo.T @ np.abs(X) + adH.T @ BX
     Bdb1 = gamma(n) * adH.sum(axis=0) + BdH.sum(axis=0)
     return {"E": 2 * BE, "loss": 2 * Bloss, "W1": 2 * BdW1.ravel(), "b1": 2 * Bdb1, "W2": 2 * BdW2.ravel(),
             "b2": 2 * Bdb2}
