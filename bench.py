@@ -384,6 +384,9 @@ def main():
     ap.add_argument("--scaling", default="strong", choices=["strong", "weak"],
                     help="with N > 1 ranks: strong = the ranks share one instance (ps_partition's equal-work "
                          "parts, no collective on the data path); weak = one independent instance per rank")
+    ap.add_argument("--ps-config", default="",
+                    help="kernel choices for the handle, as ps_config fields: name=value[,name=value...] "
+                         "(e.g. tma_schedule=2,tma_meet=32); default: every choice automatic")
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
     ws, rank, local = dist_env()
@@ -398,7 +401,11 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     from paper_1705_08210_gb300 import ps, synth
 
-    h = ps.Handle(local)
+    fields = {}
+    for item in filter(None, args.ps_config.split(",")):
+        k, v = item.split("=", 1)
+        fields[k.strip()] = int(v)
+    h = ps.Handle(local, **fields)
     nv, nf = w["nv"], w["nf"]
     dtype = np.float64 if args.workload.endswith("f64") else np.float32
     strong = ws > 1 and args.scaling == "strong"

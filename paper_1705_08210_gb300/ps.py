@@ -138,7 +138,10 @@ def config(**fields) -> ps_config:
     (autotune_cache may be a str)."""
     c = ps_config()
     ps_config_init(ctypes.byref(c))
+    names = {f[0] for f in ps_config._fields_}
     for k, v in fields.items():
+        if k not in names:
+            raise ValueError(f"ps_config has no field {k!r}")
         if k == "autotune_cache" and isinstance(v, str):
             v = v.encode()
         setattr(c, k, v)
