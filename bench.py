@@ -129,7 +129,8 @@ TRAFFIC = {
     "mgemm2": ("profiles/mgemm2_2way_32768x8192_dram.md",
                ["paper_1705_08210_gb300/csrc/ps_mgemm_impl.cuh", "paper_1705_08210_gb300/csrc/ps_mgemm_tma.cu",
                 "paper_1705_08210_gb300/csrc/ps_sync.cuh"]),
-    "thermo_gemm": ("profiles/thermo_gemm_2way_32768x8192_dram.md", ["paper_1705_08210_gb300/csrc/ps_thermo.cu"]),
+    "thermo_gemm": ("profiles/thermo_gemm_2way_32768x8192_dram.md",
+                    ["paper_1705_08210_gb300/csrc/ps_thermo.cu", "paper_1705_08210_gb300/csrc/ps_sync.cuh"]),
 }
 
 
@@ -214,7 +215,7 @@ def run_reference(args, w, ws, rank):
     if rank != 0:
         return
     from paper_1705_08210_gb300 import synth
-    n_sample = 2048 if w["way"] == 2 else 128
+    n_sample = min(2048 if w["way"] == 2 else 128, w["nv"])
     V = synth.zero_inflated(n_sample, w["nf"], synth.seed_for(w["number"]))
     times = []
     cb = None

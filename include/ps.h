@@ -200,6 +200,17 @@ typedef struct {
  *                    (automatic: by the operand width).
  *   thermo_meet_kb : k-blocks between grid-wide meetings of the thermometer
  *                    GEMM's producers; 0 = automatic (960), -1 = never.
+ *   mgemm_narrow   : FP32 / one-byte 2-way metrics with n_f <= 64: 1 = the
+ *                    narrow kernel, whose warps write each tile's metrics
+ *                    while they compute the next tile, each store
+ *                    instruction writing 32 consecutive metrics of a row
+ *                    (automatic); 2 = the general TMA kernel.  (The narrow
+ *                    kernel needs the automatic tma_schedule, tma_meet and
+ *                    tma_slice.)
+ *   tma_lookahead  : slices (tiles, in the narrow kernel) the producer of the
+ *                    2-way TMA kernels loads ahead of the one its warps
+ *                    compute, 1..7, capped at the ring depth minus one;
+ *                    0 = automatic.
  *   test_batched_stall : testing aid for the timeout path, 0 by default.
  *                    1 = the next ps_metrics_batched call (persistent mode)
  *                    raises one dependency target by one item that does not
@@ -231,6 +242,8 @@ typedef struct {
   int32_t thermo_tile_m;
   int32_t thermo_meet_kb;
   int32_t test_batched_stall;
+  int32_t mgemm_narrow;
+  int32_t tma_lookahead;
 } ps_config;
 
 /* Defaults: precision PS_PATH_FP32, no debug checks, 2 s wait limit, no

@@ -141,6 +141,8 @@ ps_status apply_config(ps_ctx* h, const ps_config* user) {
   if (!one_of(c.thermo_tile_m, {0, 128, 256})) return bad("thermo_tile_m", c.thermo_tile_m);
   if (c.thermo_meet_kb < -1 || c.thermo_meet_kb > 1 << 20) return bad("thermo_meet_kb", c.thermo_meet_kb);
   if (!one_of(c.test_batched_stall, {0, 1})) return bad("test_batched_stall", c.test_batched_stall);
+  if (!one_of(c.mgemm_narrow, {0, 1, 2})) return bad("mgemm_narrow", c.mgemm_narrow);
+  if (c.tma_lookahead < 0 || c.tma_lookahead > 7) return bad("tma_lookahead", c.tma_lookahead);
   h->cache_path = c.autotune_cache ? c.autotune_cache : "";
   c.autotune_cache = c.autotune_cache ? h->cache_path.c_str() : nullptr;
   h->cfg = c;
@@ -161,6 +163,8 @@ ps_status apply_config(ps_ctx* h, const ps_config* user) {
   h->thermo_tile_m = c.thermo_tile_m;
   h->thermo_sync_kb = c.thermo_meet_kb == 0 ? 960 : (c.thermo_meet_kb < 0 ? 0 : c.thermo_meet_kb);
   h->batched_stall = c.test_batched_stall;
+  h->mgemm_narrow = c.mgemm_narrow;
+  h->tma_lookahead = c.tma_lookahead;
   return PS_OK;
 }
 

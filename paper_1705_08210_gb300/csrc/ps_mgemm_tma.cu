@@ -9,7 +9,7 @@
 // panel and the 128-vector column panel of V, field-major, zero-filled past
 // nv and nf) into an STAGES-deep shared-memory ring guarded by full/empty
 // mbarriers.  Lane 0 of warp 0 is the producer: before computing slice s it
-// loads slice s + STAGES - 1 (the walk over this CTA's tiles is one flat
+// loads slice s + look, look <= STAGES - 1 (the walk over this CTA's tiles is one flat
 // sequence of slices, so near the end of a tile it already loads the next
 // tile's first slices, which then land while the warps write outputs).  A
 // warp releases a slice with one arrival when it is done with it.  The 16
@@ -72,7 +72,7 @@ __global__ void __launch_bounds__(C::NT, 1)
                       const double* __restrict__ S, void* __restrict__ out, int mode, int T, int R0,
                       int R1, int G, int64_t ntiles, int* err, unsigned* __restrict__ sync, int sync_sl,
                       unsigned long long* __restrict__ tile_ctr, unsigned long long wait_ns,
-                      const float* __restrict__ Sf, const unsigned* __restrict__ lean_words) {
+                      const float* __restrict__ Sf, const unsigned* __restrict__ lean_words, int look) {
   static_assert(mg::FOLD * mg::BK % BK == 0, "a fold boundary ends a slice");
   constexpr int FOLD_SLICES = mg::FOLD * mg::BK / BK;  // 64 fields per compensated fold
   constexpr uint32_t SLICE_BYTES = 2u * BK * C::BM * sizeof(float);
@@ -167,7 +167,7 @@ __global__ void __launch_bounds__(C::NT, 1)
     return true;
   };
   if (producer)
-    for (int p = 0; p < STAGES - 1; ++p)
+    for (int p = 0; p < look; ++p)
       if (!issue_one()) break;
 
   const mg::Lanes<C> L;
@@ -182,7 +182,7 @@ __global__ void __launch_bounds__(C::NT, 1)
     float Sfi[8], Sfj[C::NJ];
     acc.zero();
     for (int kb = 0; kb < nkb; ++kb, ++it) {
-      if (producer) ok = issue_one();  // slice it + STAGES - 1
+      if (producer) ok = issue_one();  // slice it + look
       const int s = (int)(it % STAGES);
       const uint32_t ph = (it / STAGES) & 1u;
       // every lane waits (each gets the barrier's acquire); the warp follows
@@ -271,7 +271,8 @@ struct TmaLaunch {
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, mgemm2_tma_kernel<BK, STAGES, KU, EPI, DYN>, map, (int)V.nv, (int)V.nf, S, out,
-                              mode, T, R0, R1, G, ntiles, err, sync, sync_sl, tile_ctr, h->wait_ns, np.Sf, np.words);
+                              mode, T, R0, R1, G, ntiles, err, sync, sync_sl, tile_ctr, h->wait_ns, np.Sf, np.words,
+                              h->tma_lookahead ? std::min(h->tma_lookahead, STAGES - 1) : STAGES - 1);
   }
 };
 
@@ -310,6 +311,10 @@ cudaError_t launch_mgemm2_tma(ps_ctx* h, const VF32& V, const double* S, void* o
   // dynamic tile schedule (the default) unless the producers are to meet,
   // which needs the static rounds; the other slice shapes are static only
   const bool dyn = h->mgemm_tma_dynamic && h->mgemm_tma_sync <= 0;
+  // few fields: the kernel that overlaps each tile's epilogue with the next
+  // tile's comparisons (unless a slice width is configured)
+  if (epi == 2 && !h->mgemm_tma_bk && narrow_applies(h, V.nf, mode))
+    return launch_mgemm2_narrow(h, V, np, out, mode, st, T, R0, R1, G, ntiles, err, sync);
 #define PS_TMA_RUN(...) TmaLaunch<__VA_ARGS__>::run(h, V, S, out, mode, st, T, R0, R1, G, ntiles, err, sync, np)
   if (bk == 16) {
     // (16-field slices above n_f = 64 only when configured: the plain epilogue)

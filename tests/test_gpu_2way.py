@@ -338,3 +338,25 @@ def test_lean_division_bit_identical(ps, handle, case, nf):
         np.testing.assert_array_equal(metrics_2way(ps, h, V, out_dtype=np.uint8), lean8)
     finally:
         h.close()
+
+
+@pytest.mark.parametrize("nv,nf", [(129, 1), (1000, 7), (1300, 16), (257, 17), (1000, 32), (1300, 33), (640, 64),
+                                   (2100, 16)])
+def test_narrow_kernel_layouts_bit_identical(ps, nv, nf):
+    # the n_f <= 64 kernel (each warp writes its previous tile's metrics
+    # while it computes the next tile) against the general TMA kernel: FP32
+    # metrics and one-byte codes bit-identical, FP32 within the rounding
+    # bound of the FP64 oracle.  Ragged nv leaves partial tiles on the right
+    # edge; nv = 2100 gives runs of interior tiles between diagonal ones.
+    V = synth.zero_inflated(nv, nf, synth.seed_for(1, 700 + nf))
+    ref = oracle.c2_packed(oracle.to_vector_major(V))
+    outs = {}
+    for choice in (1, 2):
+        h = ps.Handle(0, mgemm_narrow=choice)
+        try:
+            outs[choice] = (metrics_2way(ps, h, V), metrics_2way(ps, h, V, out_dtype=np.uint8))
+        finally:
+            h.close()
+    assert_rel(outs[1][0], ref, RTOL32, f"narrow nv={nv} nf={nf}")
+    np.testing.assert_array_equal(outs[1][0], outs[2][0])
+    np.testing.assert_array_equal(outs[1][1], outs[2][1])
