@@ -49,7 +49,6 @@ struct __align__(128) Smem3 {
   int pcol[STAGES];            // j % 4 of the slice's pivot (written by the producer)
   int tile_of[STAGES];         // counter schedule: work item of local item lt at [lt % STAGES], -1 = none
   int2 pitem;                  // the producer's current work item
-  int2 p_next_item;            // counter schedule: the producer's next work item (cp.async)
   int p_done;                  // counter schedule: the producer has issued the end marker
   unsigned long long full[STAGES];
   unsigned long long ready[STAGES];
@@ -122,24 +121,6 @@ __global__ void __launch_bounds__(C::NT, 1)
   // stage is free); false on abort.  Its work item is kept in shared memory
   // (registers are the micro-kernel's).
   const bool producer = threadIdx.x == 0;
-  // counter schedule: the producer's next claim (32 bits: item indices are
-  // below 2^31) and its work item, fetched one item ahead of their use so
-  // that neither the atomic's nor the table load's latency lands on the
-  // producer's (a compute warp's) path.  The item is copied into shared
-  // memory by cp.async (no register held across the item); each CTA claims
-  // at most one item past the end.
-  unsigned* const ctr32 = reinterpret_cast<unsigned*>(item_ctr);
-  unsigned next_claim = 0;
-  auto fetch_item = [&](unsigned t) {
-    if (t < (unsigned long long)ntiles)
-      asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(sy::smem_addr(&sm.p_next_item)),
-                   "l"(items + t)
-                   : "memory");
-  };
-  if (DYN && producer) {
-    next_claim = atomicAdd(ctr32, 1u);
-    fetch_item(next_claim);
-  }
   auto issue_one = [&](uint32_t g) -> bool {
     Smem3<BK, STAGES>& sm = *reinterpret_cast<Smem3<BK, STAGES>*>(smem_raw);
     if (g >= n_slices || (DYN && sm.p_done)) return true;
@@ -150,7 +131,7 @@ __global__ void __launch_bounds__(C::NT, 1)
     if (!DYN && kb == 0) sm.pitem = items[blockIdx.x + (int64_t)r * gridDim.x];
     if (!sy::bar_wait(&sm.empty[s], ph ^ 1u, &sm.abort, err, wait_ns)) return false;
     if (DYN && kb == 0) {
-      const unsigned t = next_claim;
+      const unsigned long long t = atomicAdd(item_ctr, 1ull);
       if (t >= (unsigned long long)ntiles) {
         sm.tile_of[r % STAGES] = -1;
         sy::bar_arrive(&sm.full[s]);  // completes the phase with no copies
@@ -158,10 +139,7 @@ __global__ void __launch_bounds__(C::NT, 1)
         return true;
       }
       sm.tile_of[r % STAGES] = (int)t;  // published by the arrival below
-      asm volatile("cp.async.wait_all;" ::: "memory");
-      sm.pitem = sm.p_next_item;
-      next_claim = atomicAdd(ctr32, 1u);
-      fetch_item(next_claim);
+      sm.pitem = items[t];
     }
     int pj, prow0, pcol0;
     item3(sm.pitem, pj, prow0, pcol0);
