@@ -34,9 +34,11 @@
  *   tensors, managed memory) or HOST memory (pinned or pageable).  The kind
  *   is detected with cudaPointerGetAttributes.  Host buffers are staged
  *   through library-owned device memory inside the call, and a call that
- *   touches any host buffer synchronises `stream` before returning (the FP32
- *   2-way path with a host output computes in row bands and copies each
- *   finished band while the next one computes).  A call
+ *   touches any host buffer synchronises `stream` before returning.  The FP32
+ *   2-way path with a host output either lets the kernel write the metrics
+ *   straight into it (pinned or registered memory, n_f >= 256; see
+ *   ps_config.host_direct) or computes in row bands and copies each
+ *   finished band while the next one computes.  A call
  *   on device buffers only is asynchronous on `stream`.  The caller owns all
  *   buffers it passes; the library owns only its workspace (grown on demand,
  *   freed by ps_destroy).
@@ -211,6 +213,13 @@ typedef struct {
  *                    2-way TMA kernels loads ahead of the one its warps
  *                    compute, 1..7, capped at the ring depth minus one;
  *                    0 = automatic.
+ *   host_direct    : FP32 2-way calls (ps_metrics_2way, PS_PATH_FP32) whose
+ *                    output is host memory pinned or registered with CUDA:
+ *                    0 (default) = for n_f >= 256 the kernel writes the
+ *                    metrics straight into it through its device mapping
+ *                    (no staging buffer, no copy); 1 = always stage in the
+ *                    workspace and copy (in row bands that overlap the
+ *                    compute).
  *   test_batched_stall : testing aid for the timeout path, 0 by default.
  *                    1 = the next ps_metrics_batched call (persistent mode)
  *                    raises one dependency target by one item that does not
@@ -244,6 +253,7 @@ typedef struct {
   int32_t test_batched_stall;
   int32_t mgemm_narrow;
   int32_t tma_lookahead;
+  int32_t host_direct;
 } ps_config;
 
 /* Defaults: precision PS_PATH_FP32, no debug checks, 2 s wait limit, no

@@ -143,6 +143,7 @@ ps_status apply_config(ps_ctx* h, const ps_config* user) {
   if (!one_of(c.test_batched_stall, {0, 1})) return bad("test_batched_stall", c.test_batched_stall);
   if (!one_of(c.mgemm_narrow, {0, 1, 2})) return bad("mgemm_narrow", c.mgemm_narrow);
   if (c.tma_lookahead < 0 || c.tma_lookahead > 7) return bad("tma_lookahead", c.tma_lookahead);
+  if (!one_of(c.host_direct, {0, 1})) return bad("host_direct", c.host_direct);
   h->cache_path = c.autotune_cache ? c.autotune_cache : "";
   c.autotune_cache = c.autotune_cache ? h->cache_path.c_str() : nullptr;
   h->cfg = c;
@@ -165,6 +166,7 @@ ps_status apply_config(ps_ctx* h, const ps_config* user) {
   h->batched_stall = c.test_batched_stall;
   h->mgemm_narrow = c.mgemm_narrow;
   h->tma_lookahead = c.tma_lookahead;
+  h->host_direct = c.host_direct;
   return PS_OK;
 }
 
@@ -321,6 +323,17 @@ ps_status fp64_operand(ps_ctx* h, const ps_matrix* V, const Prepared& P, cudaStr
   *X = d;
   *ld = ldp;
   return PS_OK;
+}
+
+// Device address of host memory that is pinned or registered with CUDA
+// (device-mapped), else null.
+void* mapped_host(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
 }
 
 // Output buffer: caller device memory, or workspace staging for host memory.
@@ -675,8 +688,18 @@ ps_status ps_metrics_2way(ps_handle h, const ps_matrix* V, int32_t path, int32_t
   const int64_t npairs = V->nv * (V->nv - 1) / 2;
   const size_t obytes = (size_t)npairs * dtype_size(out_dtype);
   OutBuf o;
-  s = resolve_out(h, out, obytes, WS_OUTPUT, &o);
-  if (s != PS_OK) return s;
+  // FP32 path, n_f >= 256 (at most ~8 GB/s of metrics): a pinned or
+  // registered host output is written by the kernel itself through its
+  // device mapping, with no staging buffer and no copy
+  void* direct = (path == PS_PATH_FP32 && V->nf >= 256 && h->host_direct != 1) ? mapped_host(out) : nullptr;
+  if (direct) {
+    o.dev = direct;
+    o.user = out;
+    o.host = true;  // (bytes 0: nothing to copy; the call synchronises)
+  } else {
+    s = resolve_out(h, out, obytes, WS_OUTPUT, &o);
+    if (s != PS_OK) return s;
+  }
   Prepared P;
   if (binary) {
     s = prepare(h, *V, st, false, &P, false);
@@ -704,7 +727,7 @@ ps_status ps_metrics_2way(ps_handle h, const ps_matrix* V, int32_t path, int32_t
     const VF32 hv{reinterpret_cast<const float*>(vh), ldh, (int)V->nv, (int)np};
     ScopedTimer tm(h, "mgemm2_half", st);
     PS_CUDA_TRY(h, launch_mgemm2_half(h->num_sms, h->mgemm_band, h->mgemm_warps, hv, P.S, o.dev, out_dtype == PS_F64, inv_scale, st));
-  } else if (path == PS_PATH_FP32 && o.host && V->nv >= 8 * 128) {
+  } else if (path == PS_PATH_FP32 && o.host && !direct && V->nv >= 8 * 128) {
     // host output: compute in equal-work row bands and copy each finished
     // band (a contiguous packed range) to the host on the handle's copy
     // stream while the next band computes

@@ -45,7 +45,8 @@ class ps_config(ctypes.Structure):
                 ("tma_schedule", ctypes.c_int32), ("tma_meet", ctypes.c_int32),
                 ("mgemm3_schedule", ctypes.c_int32), ("thermo_tile_m", ctypes.c_int32),
                 ("thermo_meet_kb", ctypes.c_int32), ("test_batched_stall", ctypes.c_int32),
-                ("mgemm_narrow", ctypes.c_int32), ("tma_lookahead", ctypes.c_int32)]
+                ("mgemm_narrow", ctypes.c_int32), ("tma_lookahead", ctypes.c_int32),
+                ("host_direct", ctypes.c_int32)]
 
 
 class ps_problem(ctypes.Structure):

@@ -11,21 +11,27 @@ def _torch():
 
 def metrics_2way(ps, handle, V, path=0, out_dtype=np.float32, layout=0, levels=0,
                  on_host=False, stream=None):
-    """Run ps_metrics_2way on a numpy matrix (shape per `layout`); returns numpy."""
+    """Run ps_metrics_2way on a numpy matrix (shape per `layout`); returns numpy.
+    on_host: True = pageable host input and output; "pinned" = pageable host
+    input, pinned (device-mapped) host output."""
     torch = _torch()
     if layout == 0:
         nf, nv = V.shape
     else:
         nv, nf = V.shape
     npairs = nv * (nv - 1) // 2
+    tdt = {np.float32: torch.float32, np.float64: torch.float64, np.uint8: torch.uint8}[out_dtype]
     if on_host:
         X = np.ascontiguousarray(V)
-        out = np.empty(npairs, dtype=out_dtype)
+        if on_host == "pinned":
+            out_p = torch.empty(npairs, dtype=tdt).pin_memory()
+            out = out_p.numpy()
+        else:
+            out = np.empty(npairs, dtype=out_dtype)
         m = ps.matrix(X, layout)
         optr = out.ctypes.data
     else:
         X = torch.from_numpy(np.ascontiguousarray(V)).cuda()
-        tdt = {np.float32: torch.float32, np.float64: torch.float64, np.uint8: torch.uint8}[out_dtype]
         out_t = torch.empty(npairs, dtype=tdt, device="cuda")
         m = ps.matrix(X, layout)
         optr = out_t.data_ptr()

@@ -84,7 +84,8 @@ def test_config_defaults_and_validation_without_gpu(ps):
                          ("mgemm_warps", 4), ("mgemm_unroll", 5), ("mgemm_add", 7), ("mgemm_band", 65),
                          ("tma_slice", 48), ("tma_unroll", 12), ("tma_stages", 5), ("tma_schedule", 3),
                          ("tma_meet", -1), ("mgemm3_schedule", 9), ("thermo_tile_m", 64),
-                         ("thermo_meet_kb", -2), ("test_batched_stall", 2)]:
+                         ("thermo_meet_kb", -2), ("test_batched_stall", 2), ("mgemm_narrow", 3),
+                         ("tma_lookahead", 8), ("host_direct", 2)]:
         bad = ps.config(**{field: value})
         assert ps.ps_create(ctypes.byref(h), 0, ctypes.byref(bad)) == ps.PS_ERR_INVALID_ARG, field
         assert field.encode() in ps.ps_last_error(None)

@@ -360,3 +360,24 @@ def test_narrow_kernel_layouts_bit_identical(ps, nv, nf):
     assert_rel(outs[1][0], ref, RTOL32, f"narrow nv={nv} nf={nf}")
     np.testing.assert_array_equal(outs[1][0], outs[2][0])
     np.testing.assert_array_equal(outs[1][1], outs[2][1])
+
+
+@pytest.mark.parametrize("nv,nf,dt", [(1300, 300, np.float32), (1100, 256, np.uint8), (1024, 512, np.float64)])
+def test_host_output_direct_and_staged_bit_identical(ps, nv, nf, dt):
+    # a pinned host output at n_f >= 256 is written by the kernel through
+    # its device mapping; host_direct=1 stages it and copies in row bands;
+    # both equal the device-output call bit for bit
+    V = synth.zero_inflated(nv, nf, synth.seed_for(1, 800 + nf))
+    out_dtype = {np.float32: ps.PS_F32, np.uint8: ps.PS_U8, np.float64: ps.PS_F64}[dt]
+    res = []
+    for direct in (0, 1):
+        h = ps.Handle(0, host_direct=direct)
+        try:
+            res.append(metrics_2way(ps, h, V, out_dtype=dt, on_host="pinned"))
+            dev = metrics_2way(ps, h, V, out_dtype=dt)
+        finally:
+            h.close()
+        np.testing.assert_array_equal(res[-1], dev)
+    np.testing.assert_array_equal(res[0], res[1])
+    if dt is not np.uint8:
+        assert_rel(res[0], oracle.c2_packed(oracle.to_vector_major(V)), RTOL32, "host output")
