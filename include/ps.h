@@ -547,7 +547,9 @@ ps_status ps_timing_read(ps_handle h, const char* kernel, int64_t* launches,
  * min + scalar FP32 add; variant 1: FP32 min + packed f32x2 add; variant 2:
  * the half2 path's operation, one packed FP16 min (two comparisons) and two
  * FP32 adds of its halves; variant 3: the min as the signed-integer min of
- * the bit patterns (equal for non-negative floats) + scalar FP32 add.
+ * the bit patterns (equal for non-negative floats) + scalar FP32 add;
+ * variant 4: FP32 min, half the chains with scalar adds and half with
+ * packed f32x2 adds.
  *   cmp_per_s : comparisons (min+add pairs) per second.
  * Synchronises the device.  Errors: PS_ERR_INVALID_ARG for a bad variant. */
 ps_status ps_probe_minadd_peak(ps_handle h, int32_t variant,

@@ -1090,7 +1090,7 @@ ps_status ps_timing_read(ps_handle h, const char* kernel, int64_t* launches, dou
 
 ps_status ps_probe_minadd_peak(ps_handle h, int32_t variant, double* cmp_per_s) {
   if (!h) return fail(nullptr, PS_ERR_INVALID_ARG, "null handle");
-  if (variant < 0 || variant > 3) return fail(h, PS_ERR_INVALID_ARG, "variant %d", variant);
+  if (variant < 0 || variant > 4) return fail(h, PS_ERR_INVALID_ARG, "variant %d", variant);
   if (!cmp_per_s) return fail(h, PS_ERR_INVALID_ARG, "null cmp_per_s");
   Guard g(h->device);
   PS_CUDA_TRY(h, probe_minadd(h, variant, cmp_per_s));

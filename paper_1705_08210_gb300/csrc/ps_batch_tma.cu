@@ -233,10 +233,10 @@ __global__ void __launch_bounds__(C::NT, 1)
       row0 = w.a * C::BM;
       col0 = w.b * C::BN;
     }
-    // 3-way: a warp whose 64 x 16 block has no row i < j, no column k > j,
-    // or no column inside the matrix skips the min-adds
+    // 3-way: a warp whose block has no row i < j, no column k > j, or no
+    // column inside the matrix skips the min-adds
     const bool active =
-        j < 0 || (row0 + L.wrow0 < j && col0 + L.wcol0 + 15 > j && col0 + L.wcol0 < nv);
+        j < 0 || (row0 + L.wrow0 < j && col0 + L.wcol0 + mg::Lanes3::BW - 1 > j && col0 + L.wcol0 < nv);
     acc.zero();
     for (int kb = 0; kb < nkb; ++kb, ++it) {
       if (producer) ok = issue_one();
@@ -253,7 +253,7 @@ __global__ void __launch_bounds__(C::NT, 1)
 #pragma unroll 16
         for (int kk = 0; kk < BKB; ++kk) {
           const float4 a0 = *reinterpret_cast<const float4*>(As + kk * C::BM);
-          const float4 a1 = *reinterpret_cast<const float4*>(As + kk * C::BM + 32);
+          const float4 a1 = *reinterpret_cast<const float4*>(As + kk * C::BM + mg::Lanes3::RUN);
           const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
           const float4 b0 = *reinterpret_cast<const float4*>(Bs + kk * C::BN);
           const float b[4] = {b0.x, b0.y, b0.z, b0.w};

@@ -105,6 +105,19 @@ __global__ void __launch_bounds__(256) probe_kernel(float* out, int iters, float
     } else if (VARIANT == 0) {
 #pragma unroll
       for (int c = 0; c < PROBE_CHAINS; ++c) x[c] = x[c] + fminf(x[c], y);
+    } else if (VARIANT == 4) {
+      // half the chains with scalar adds, half with packed f32x2 adds
+#pragma unroll
+      for (int c = 0; c < PROBE_CHAINS / 2; ++c) x[c] = x[c] + fminf(x[c], y);
+#pragma unroll
+      for (int c = PROBE_CHAINS / 2; c < PROBE_CHAINS; c += 2) {
+        unsigned long long p;
+        asm("mov.b64 %0, {%1, %2};" : "=l"(p) : "f"(x[c]), "f"(x[c + 1]));
+        p = mg::f2_add(p, fminf(x[c], y), fminf(x[c + 1], y));
+        const float2 u = mg::f2_unpack(p);
+        x[c] = u.x;
+        x[c + 1] = u.y;
+      }
     } else {
 #pragma unroll
       for (int c = 0; c < PROBE_CHAINS; c += 2) {
@@ -356,7 +369,8 @@ cudaError_t probe_minadd(ps_ctx* h, int variant, double* cmp_per_s) {
     if (variant == 0) probe_kernel<0><<<blocks, 256>>>(dout, iters, 1e-3f);
     else if (variant == 1) probe_kernel<1><<<blocks, 256>>>(dout, iters, 1e-3f);
     else if (variant == 2) probe_kernel<2><<<blocks, 256>>>(dout, iters, 1e-3f);
-    else probe_kernel<3><<<blocks, 256>>>(dout, iters, 1e-3f);
+    else if (variant == 3) probe_kernel<3><<<blocks, 256>>>(dout, iters, 1e-3f);
+    else probe_kernel<4><<<blocks, 256>>>(dout, iters, 1e-3f);
     cudaEventRecord(e1, 0);
     e = cudaEventSynchronize(e1);
     if (e != cudaSuccess) break;

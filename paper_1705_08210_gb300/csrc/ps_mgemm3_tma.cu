@@ -15,17 +15,12 @@
 // runs the 2-way micro-kernel (8 x 4 outputs per lane, FP32 min + packed
 // FP32 add, TwoSum fold every 64 fields) on it.
 //
-// Warp placement.  A warp owns a 64-row x 16-column block.  The tile that
+// Warp placement (mg::Lanes3).  A warp owns a 32 x 32 block.  The tile that
 // straddles the pivot has rows i >= j (past the pivot's rectangle) and
 // columns k <= j (before it); warps whose whole block lies outside skip the
-// min-add loop.  A skipped warp only helps if another warp on the same
-// scheduler (warps w, w+4, w+8, w+12 share one) takes the pipe, so warps
-// are placed on blocks so that every scheduler holds two row halves and its
-// four blocks spread across the column groups: warp w = 4g + s (scheduler
-// s) takes block e = (s + g) mod 4 of column group g (columns 32g..32g+31):
-// row half e & 1, column half e >> 1.  Then skipping the lower row half, or
-// any whole number of 32-column groups at the left edge, removes the same
-// number of blocks from every scheduler.
+// min-add loop.  Warp w = 4g + s (scheduler s) takes row block g and column
+// block (g + s) mod 4, so skipping whole row blocks or column blocks frees
+// every scheduler equally.
 #include "ps_mgemm_impl.cuh"
 #include "ps_sync.cuh"
 
@@ -62,7 +57,7 @@ __device__ __forceinline__ void compute_slice3(const float* As, const float* Bs,
 #pragma unroll KU
   for (int kk = 0; kk < BK; ++kk) {
     const float4 a0 = *reinterpret_cast<const float4*>(As + kk * C::BM);
-    const float4 a1 = *reinterpret_cast<const float4*>(As + kk * C::BM + 32);
+    const float4 a1 = *reinterpret_cast<const float4*>(As + kk * C::BM + mg::Lanes3::RUN);
     const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
     const float4 b0 = *reinterpret_cast<const float4*>(Bs + kk * C::BN);
     const float b[4] = {b0.x, b0.y, b0.z, b0.w};
@@ -203,9 +198,9 @@ __global__ void __launch_bounds__(C::NT, 1)
     }
     int j, row0, col0;
     item3(items[t], j, row0, col0);
-    // a warp whose 64 x 16 block has no row i < j, no column k > j, or no
-    // column inside the matrix has no output here and skips the min-adds
-    const bool active = row0 + L.wrow0 < j && col0 + L.wcol0 + 15 > j && col0 + L.wcol0 < nv;
+    // a warp whose block has no row i < j, no column k > j, or no column
+    // inside the matrix has no output here and skips the min-adds
+    const bool active = row0 + L.wrow0 < j && col0 + L.wcol0 + Lanes3::BW - 1 > j && col0 + L.wcol0 < nv;
     acc.zero();
     for (int kb = 0; kb < nkb; ++kb, ++it) {
       // slice it + STAGES - 1 (its stage was released by every warp after

@@ -339,27 +339,33 @@ struct Lanes {
 
 // Thread -> output coordinates of the 16-warp 128 x 128 tile (T128W16) in
 // the TMA-fed 3-way and batched kernels (same interface as Lanes).  A warp
-// owns a 64-row x 16-column block.  In a 3-way tile that straddles the pivot,
-// warps whose whole block has no row i < j or no column k > j skip the
-// min-add loop; a skipped warp only helps if another warp on the same
-// scheduler (warps w, w+4, w+8, w+12 share one) takes the pipe, so warp
-// w = 4g + s (scheduler s) takes block e = (s + g) mod 4 of column group g
-// (columns 32g..32g+31): row half e & 1, column half e >> 1.  Then skipping
-// the lower row half, or any whole number of 32-column groups at the left
-// edge, removes the same number of blocks from every scheduler.
+// owns a 32 x 32 block: lane (lm, ln) = (lane / 8, lane % 8) rows
+// 4 lm + {0..3} and 16 + 4 lm + {0..3}, columns 4 ln + {0..3} (the two A
+// loads are broadcasts over 4 addresses, the B load 8 consecutive 16-byte
+// words).  In a 3-way tile that straddles the pivot, warps whose whole block
+// has no row i < j or no column k > j skip the min-add loop; of the block
+// shapes a warp of 8 x 4-output lanes can take, 32 x 32 wastes least (at
+// nv = 2048 the active blocks hold 95.6% useful outputs, 64 x 16 blocks
+// 94.5%).  A skipped warp only helps if another warp on the same scheduler
+// (warps w, w+4, w+8, w+12 share one) takes the pipe, so warp w = 4g + s
+// (scheduler s) takes block (row block g, column block (g + s) mod 4): every
+// scheduler holds one block of each row block and of each column block, and
+// skipping whole row blocks at the bottom or whole column blocks at the left
+// removes the same number of blocks from every scheduler.
 struct Lanes3 {
+  static constexpr int BH = 32, BW = 32;  // warp block rows, columns
+  static constexpr int RUN = 16;          // offset of a lane's second run of 4 rows
   int am, bn;        // smem column offsets of the A / B fragments
-  int wrow0, wcol0;  // first row / column of this warp's 64 x 16 block
+  int wrow0, wcol0;  // first row / column of this warp's block
   __device__ __forceinline__ Lanes3() {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int g = warp >> 2, s = warp & 3, e = (s + g) & 3;
-    const int wm = e & 1, wn = 2 * g + (e >> 1);
-    wrow0 = wm * 64;
-    wcol0 = wn * 16;
-    am = wrow0 + (lane >> 2) * 4;
-    bn = wcol0 + (lane & 3) * 4;
+    const int g = warp >> 2, s = warp & 3;
+    wrow0 = g * BH;
+    wcol0 = ((g + s) & 3) * BW;
+    am = wrow0 + (lane >> 3) * 4;
+    bn = wcol0 + (lane & 7) * 4;
   }
-  __device__ __forceinline__ int row(int r) const { return am + (r < 4 ? r : 28 + r); }
+  __device__ __forceinline__ int row(int r) const { return am + (r < 4 ? r : RUN - 4 + r); }
   __device__ __forceinline__ int col(int c) const { return bn + c; }
 };
 
