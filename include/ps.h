@@ -184,8 +184,13 @@ typedef struct {
  *                    kernels (automatic: 16 for 2-way, 8 for 3-way).
  *   mgemm_unroll   : 4, 8 (automatic) or 16 k-steps per loop iteration of
  *                    the cp.async kernels.
- *   mgemm_add      : 1 = packed add.rn.f32x2 (automatic), 2 = scalar adds
- *                    (8-warp 128 x 128 cp.async kernels).
+ *   mgemm_add      : add form of the FP32 accumulators (identical values).
+ *                    cp.async kernels: packed add.rn.f32x2 (automatic, 1,
+ *                    3) or scalar adds (2; 8-warp 128 x 128 tiles).  TMA
+ *                    2-way kernel: half of each lane's columns packed, half
+ *                    scalar (automatic, 3), all packed (1) or all scalar (2;
+ *                    these two with 32-field slices).  The TMA 3-way and
+ *                    batched kernels always use the mixed form.
  *   mgemm_band     : tile rows per band of the 2-way tile walk, 1..64
  *                    (automatic 16).
  *   tma_slice      : fields per TMA slice, 16, 32 or 64 (automatic: by n_f).

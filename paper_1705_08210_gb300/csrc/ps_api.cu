@@ -130,7 +130,7 @@ ps_status apply_config(ps_ctx* h, const ps_config* user) {
   if (!one_of(c.mgemm_tile, {0, 64, 128})) return bad("mgemm_tile", c.mgemm_tile);
   if (!one_of(c.mgemm_warps, {0, 8, 16})) return bad("mgemm_warps", c.mgemm_warps);
   if (!one_of(c.mgemm_unroll, {0, 4, 8, 16})) return bad("mgemm_unroll", c.mgemm_unroll);
-  if (!one_of(c.mgemm_add, {0, 1, 2})) return bad("mgemm_add", c.mgemm_add);
+  if (!one_of(c.mgemm_add, {0, 1, 2, 3})) return bad("mgemm_add", c.mgemm_add);
   if (c.mgemm_band < 0 || c.mgemm_band > 64) return bad("mgemm_band", c.mgemm_band);
   if (!one_of(c.tma_slice, {0, 16, 32, 64})) return bad("tma_slice", c.tma_slice);
   if (!one_of(c.tma_unroll, {0, 8, 16, 32})) return bad("tma_unroll", c.tma_unroll);
@@ -154,6 +154,7 @@ ps_status apply_config(ps_ctx* h, const ps_config* user) {
   h->mgemm_warps = c.mgemm_warps;
   h->mgemm_ku = c.mgemm_unroll ? c.mgemm_unroll : 8;
   h->mgemm_packed_add = c.mgemm_add != 2;
+  h->mgemm_add = c.mgemm_add;
   h->mgemm_band = c.mgemm_band ? c.mgemm_band : 16;
   h->mgemm_tma_bk = c.tma_slice;
   h->mgemm_tma_ku = c.tma_unroll;

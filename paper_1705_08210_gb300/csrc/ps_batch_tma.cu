@@ -214,7 +214,7 @@ __global__ void __launch_bounds__(C::NT, 1)
   };
 
   const mg::Lanes3 L;
-  mg::Acc<true, C::NJ> acc;
+  mg::AccMix<C::NJ> acc;  // packed adds for columns 0, 1, scalar for 2, 3 (identical values)
   uint32_t it = 0;
   bool ok = prepare(0, 0, true);
   for (int lt = 0; ok; ++lt) {

@@ -53,7 +53,7 @@ struct __align__(128) Smem3 {
 
 // BK k-steps of the micro-kernel on one prepared slice.
 template <int BK, int KU>
-__device__ __forceinline__ void compute_slice3(const float* As, const float* Bs, mg::Acc<true, C::NJ>& acc) {
+__device__ __forceinline__ void compute_slice3(const float* As, const float* Bs, mg::AccMix<C::NJ>& acc) {
 #pragma unroll KU
   for (int kk = 0; kk < BK; ++kk) {
     const float4 a0 = *reinterpret_cast<const float4*>(As + kk * C::BM);
@@ -182,7 +182,9 @@ __global__ void __launch_bounds__(C::NT, 1)
   };
 
   const Lanes3 L;
-  mg::Acc<true, C::NJ> acc;
+  // columns 0, 1 of each lane by packed adds, 2, 3 by scalar adds (more FP32
+  // mins per clock than all-packed adds; identical values)
+  mg::AccMix<C::NJ> acc;
   uint32_t it = 0;
   // slices are prepared one ahead of the compute, so that a warp waiting for
   // the other warps' rows of slice it waited a whole slice earlier

@@ -201,6 +201,56 @@ struct Acc<true, NJ> {
   }
 };
 
+// 8 x 4 accumulators with the adds split between the two forms: columns 0
+// and 1 by one packed add.rn.f32x2, columns 2 and 3 by scalar adds (every
+// element sees the same round-to-nearest adds in the same order as in
+// Acc<true, 4>, so the values are identical).  fold(), hl() as in Acc.
+template <int NJ>
+struct AccMix {
+  static_assert(NJ == 4, "4 columns per lane");
+  unsigned long long hp[8], lp[8];  // columns 0, 1
+  float hs[8][2], ls[8][2];         // columns 2, 3
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      hp[r] = lp[r] = 0ull;
+      hs[r][0] = hs[r][1] = ls[r][0] = ls[r][1] = 0.0f;
+    }
+  }
+  __device__ __forceinline__ void step(const float (&a)[8], const float (&b)[NJ]) {
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      lp[r] = f2_add(lp[r], fminf(a[r], b[0]), fminf(a[r], b[1]));
+      ls[r][0] = __fadd_rn(ls[r][0], fminf(a[r], b[2]));
+      ls[r][1] = __fadd_rn(ls[r][1], fminf(a[r], b[3]));
+    }
+  }
+  __device__ __forceinline__ void fold() {
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      const unsigned long long s = f2_add2(hp[r], lp[r]);
+      const unsigned long long bp = f2_sub2(s, hp[r]);
+      const unsigned long long ap = f2_sub2(s, bp);
+      lp[r] = f2_add2(f2_sub2(hp[r], ap), f2_sub2(lp[r], bp));
+      hp[r] = s;
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        const float t = __fadd_rn(hs[r][c], ls[r][c]);
+        const float bq = __fsub_rn(t, hs[r][c]);
+        const float aq = __fsub_rn(t, bq);
+        ls[r][c] = __fadd_rn(__fsub_rn(hs[r][c], aq), __fsub_rn(ls[r][c], bq));
+        hs[r][c] = t;
+      }
+    }
+  }
+  __device__ __forceinline__ float2 hl(int r, int c) const {
+    if (c >= 2) return make_float2(hs[r][c - 2], ls[r][c - 2]);
+    const float2 h = f2_unpack(hp[r]);
+    const float2 l = f2_unpack(lp[r]);
+    return (c & 1) ? make_float2(h.y, l.y) : make_float2(h.x, l.x);
+  }
+};
+
 template <int NJ>
 struct Acc<false, NJ> {
   float hi[8][NJ];
@@ -455,8 +505,8 @@ __host__ __device__ __forceinline__ int64_t pivot_tiles(int nv, int64_t j, int B
 // matrix (every i < j < nv) take a path without per-output checks.  Every
 // path gives the same correctly rounded values (store_tile2_lean below
 // too).
-template <class C, bool PACKED, class LN = Lanes<C>>
-__device__ __forceinline__ void store_tile2(const Acc<PACKED, C::NJ>& acc, const LN& L, int row0,
+template <class C, bool PACKED, class LN = Lanes<C>, class ACC = Acc<PACKED, C::NJ>>
+__device__ __forceinline__ void store_tile2(const ACC& acc, const LN& L, int row0,
                                             int col0, int64_t nv, const double* __restrict__ S,
                                             void* __restrict__ out, int mode) {
   const bool interior = col0 >= row0 + C::BM && col0 + C::BN <= nv;
@@ -554,8 +604,8 @@ __device__ __forceinline__ void store_tile2(const Acc<PACKED, C::NJ>& acc, const
 // quotient comes from div_rn_lean, whose range the caller has checked once
 // for the whole call.  Values equal store_tile2's bit for bit.  Each row's
 // outputs go through one row pointer (no per-output index arithmetic).
-template <class C, bool PACKED, bool U8, bool LO_ONLY>
-__device__ __forceinline__ void store_tile2_lean(const Acc<PACKED, C::NJ>& acc, const Lanes<C>& L, int row0,
+template <class C, bool PACKED, bool U8, bool LO_ONLY, class ACC = Acc<PACKED, C::NJ>>
+__device__ __forceinline__ void store_tile2_lean(const ACC& acc, const Lanes<C>& L, int row0,
                                                  int col0, int64_t nv, const float (&Sfi)[8],
                                                  const float (&Sfj)[C::NJ], void* __restrict__ out) {
   // packed position of (i, j) = base(i) + j with base(i) = P(i) - i - 1, P(i)

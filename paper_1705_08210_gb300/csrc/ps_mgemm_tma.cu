@@ -23,6 +23,7 @@
 
 #include <algorithm>
 #include <mutex>
+#include <type_traits>
 
 namespace ps {
 namespace {
@@ -45,9 +46,8 @@ struct __align__(128) SmemT {
 };
 
 // BK k-steps of the micro-kernel on one landed slice.
-template <int BK, int KU>
-__device__ __forceinline__ void compute_slice_tma(const float* As, const float* Bs,
-                                                  mg::Acc<true, C::NJ>& acc) {
+template <int BK, int KU, class ACC>
+__device__ __forceinline__ void compute_slice_tma(const float* As, const float* Bs, ACC& acc) {
 #pragma unroll KU
   for (int kk = 0; kk < BK; ++kk) {
     const float4 a0 = *reinterpret_cast<const float4*>(As + kk * C::BM);
@@ -66,7 +66,18 @@ __device__ __forceinline__ void compute_slice_tma(const float* As, const float* 
 // (at most 64 fields per accumulator, the fold's own bound; values are the
 // same bit for bit, since a single fold of 0 + lo is exact) and the rows'
 // and columns' sums loaded when the tile starts.
-template <int BK, int STAGES, int KU, int EPI, bool DYN>
+// ADDS: the add form of the accumulators (identical values).  1 (default):
+// columns 0 and 1 of each lane by one packed add.rn.f32x2, columns 2 and 3
+// by scalar adds (mg::AccMix); 0: all packed; 2: all scalar.  Packed adds
+// halve the add instructions, but the SM then retires fewer FP32 mins per
+// clock (measured register-only: 16.7 Tcmp/s with packed adds, 19.3 with
+// scalar ones, 18.8 mixed); mixed keeps the issue count below the ALU
+// pipe's two cycles per min: 266.98 vs 273.66 ms at 32768 x 8192.
+template <int ADDS>
+using AccT = std::conditional_t<ADDS == 1, mg::AccMix<C::NJ>,
+                                std::conditional_t<ADDS == 0, mg::Acc<true, C::NJ>, mg::Acc<false, C::NJ>>>;
+
+template <int BK, int STAGES, int KU, int EPI, bool DYN, int ADDS = 1>
 __global__ void __launch_bounds__(C::NT, 1)
     mgemm2_tma_kernel(const __grid_constant__ CUtensorMap mapV, int nv, int nf,
                       const double* __restrict__ S, void* __restrict__ out, int mode, int T, int R0,
@@ -171,7 +182,7 @@ __global__ void __launch_bounds__(C::NT, 1)
       if (!issue_one()) break;
 
   const mg::Lanes<C> L;
-  mg::Acc<true, C::NJ> acc;
+  AccT<ADDS> acc;
   // lean epilogue for this call: FP32 or one-byte output and inputs inside
   // div_rn_lean's range (decided once, from NarrowPrep's words)
   const bool lean = EPI != 0 && (mode == OUT2_C2_F32 || mode == OUT2_C2_U8) && mg::lean_division_ok(lean_words);
@@ -231,7 +242,7 @@ __global__ void __launch_bounds__(C::NT, 1)
 }
 
 // ---- host side ----
-template <int BK, int STAGES, int KU, int EPI = 0, bool DYN = false>
+template <int BK, int STAGES, int KU, int EPI = 0, bool DYN = false, int ADDS = 1>
 struct TmaLaunch {
   static constexpr size_t smem = sizeof(SmemT<BK, STAGES>);
   static cudaError_t run(ps_ctx* h, const VF32& V, const double* S, void* out, int mode, cudaStream_t st,
@@ -243,7 +254,7 @@ struct TmaLaunch {
       std::lock_guard<std::mutex> lk(mu);
       const uint64_t bit = 1ull << (h->device & 63);
       if (!(attr_done & bit)) {
-        const cudaError_t e = cudaFuncSetAttribute(mgemm2_tma_kernel<BK, STAGES, KU, EPI, DYN>,
+        const cudaError_t e = cudaFuncSetAttribute(mgemm2_tma_kernel<BK, STAGES, KU, EPI, DYN, ADDS>,
                                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         attr_done |= bit;
@@ -270,7 +281,7 @@ struct TmaLaunch {
     attr[0].val.cooperative = sync_sl ? 1 : 0;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, mgemm2_tma_kernel<BK, STAGES, KU, EPI, DYN>, map, (int)V.nv, (int)V.nf, S, out,
+    return cudaLaunchKernelEx(&cfg, mgemm2_tma_kernel<BK, STAGES, KU, EPI, DYN, ADDS>, map, (int)V.nv, (int)V.nf, S, out,
                               mode, T, R0, R1, G, ntiles, err, sync, sync_sl, tile_ctr, h->wait_ns, np.Sf, np.words,
                               h->tma_lookahead ? std::min(h->tma_lookahead, STAGES - 1) : STAGES - 1);
   }
@@ -325,6 +336,9 @@ cudaError_t launch_mgemm2_tma(ps_ctx* h, const VF32& V, const double* S, void* o
   if (epi == 2) return dyn ? PS_TMA_RUN(32, 4, 16, 2, true) : PS_TMA_RUN(32, 4, 16, 2);
   if (epi == 1) return dyn ? PS_TMA_RUN(32, 4, 16, 1, true) : PS_TMA_RUN(32, 4, 16, 1);
   if (stages == 6) return PS_TMA_RUN(32, 6, 16);
+  // add forms other than the mixed default: packed (1) or scalar (2) adds
+  if (h->mgemm_add == 1) return dyn ? PS_TMA_RUN(32, 4, 16, 0, true, 0) : PS_TMA_RUN(32, 4, 16, 0, false, 0);
+  if (h->mgemm_add == 2) return dyn ? PS_TMA_RUN(32, 4, 16, 0, true, 2) : PS_TMA_RUN(32, 4, 16, 0, false, 2);
   if (ku == 8) return PS_TMA_RUN(32, 4, 8);
   if (ku == 32) return PS_TMA_RUN(32, 4, 32);
   return dyn ? PS_TMA_RUN(32, 4, 16, 0, true) : PS_TMA_RUN(32, 4, 16);

@@ -81,7 +81,7 @@ def test_config_defaults_and_validation_without_gpu(ps):
     h = ps._h()
     for field, value in [("precision", ps.PS_PATH_THERMO), ("debug_checks", 2), ("wait_limit_ns", 10),
                          ("wait_limit_ns", 10**12), ("mgemm_feed", 3), ("mgemm3_feed", -1), ("mgemm_tile", 96),
-                         ("mgemm_warps", 4), ("mgemm_unroll", 5), ("mgemm_add", 7), ("mgemm_band", 65),
+                         ("mgemm_warps", 4), ("mgemm_unroll", 5), ("mgemm_add", 4), ("mgemm_band", 65),
                          ("tma_slice", 48), ("tma_unroll", 12), ("tma_stages", 5), ("tma_schedule", 3),
                          ("tma_meet", -1), ("mgemm3_schedule", 9), ("thermo_tile_m", 64),
                          ("thermo_meet_kb", -2), ("test_batched_stall", 2), ("mgemm_narrow", 3),
