@@ -352,15 +352,15 @@ def test_narrow_kernel_layouts_bit_identical(ps, nv, nf):
     V = synth.zero_inflated(nv, nf, synth.seed_for(1, 700 + nf))
     ref = oracle.c2_packed(oracle.to_vector_major(V))
     outs = {}
-    for choice in (1, 2):
-        h = ps.Handle(0, mgemm_narrow=choice)
+    for key, fields in (("narrow", dict(mgemm_narrow=1)), ("general", dict(mgemm_narrow=2))):
+        h = ps.Handle(0, **fields)
         try:
-            outs[choice] = (metrics_2way(ps, h, V), metrics_2way(ps, h, V, out_dtype=np.uint8))
+            outs[key] = (metrics_2way(ps, h, V), metrics_2way(ps, h, V, out_dtype=np.uint8))
         finally:
             h.close()
-    assert_rel(outs[1][0], ref, RTOL32, f"narrow nv={nv} nf={nf}")
-    np.testing.assert_array_equal(outs[1][0], outs[2][0])
-    np.testing.assert_array_equal(outs[1][1], outs[2][1])
+    assert_rel(outs["narrow"][0], ref, RTOL32, f"narrow nv={nv} nf={nf}")
+    np.testing.assert_array_equal(outs["narrow"][0], outs["general"][0])
+    np.testing.assert_array_equal(outs["narrow"][1], outs["general"][1])
 
 
 @pytest.mark.parametrize("nv,nf,dt", [(1300, 300, np.float32), (1100, 256, np.uint8), (1024, 512, np.float64)])
