@@ -729,6 +729,42 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
 // of every vector, scaled by a power of two `scale` before rounding to FP16;
 // n2 = (hi + lo) / scale is exact rescaling.  Denominators S come from the
 // caller's values.
+// Epilogue of the half2 kernels: n2 = (hi + lo) / scale (an exact
+// power-of-two rescaling of the FP32 sums of the scaled FP16 operands), then
+// c2 as in store_tile2 (FP32 with __fdiv_rn, or FP64).
+template <class C, class ACC>
+__device__ __forceinline__ void store_tile2_half(const ACC& acc, const Lanes<C>& L, int row0, int col0,
+                                                 int64_t nv, const double* __restrict__ S,
+                                                 void* __restrict__ out, int out_f64, float inv_scale) {
+  float Sjf[C::NJ];
+#pragma unroll
+  for (int c = 0; c < C::NJ; ++c) {
+    const int j = col0 + L.col(c);
+    Sjf[c] = j < nv ? (float)S[j] : 0.0f;
+  }
+#pragma unroll
+  for (int r = 0; r < 8; ++r) {
+    const int i = row0 + L.row(r);
+    if (i >= nv) continue;
+    const double Si = S[i];
+#pragma unroll
+    for (int c = 0; c < C::NJ; ++c) {
+      const int j = col0 + L.col(c);
+      if (j <= i || j >= nv) continue;
+      const float2 hl = acc.hl(r, c);
+      if (out_f64) {
+        const double n2 = ((double)hl.x + (double)hl.y) * (double)inv_scale;
+        const double d = Si + S[j];
+        static_cast<double*>(out)[pair_index(nv, i, j)] = (d == 0.0) ? 0.0 : (2.0 * n2) / d;
+      } else {
+        const float n2 = __fmul_rn(__fadd_rn(hl.x, hl.y), inv_scale);
+        const float d = __fadd_rn((float)Si, Sjf[c]);
+        static_cast<float*>(out)[pair_index(nv, i, j)] = (d == 0.0f) ? 0.0f : __fdiv_rn(2.0f * n2, d);
+      }
+    }
+  }
+}
+
 template <class C, int KU>
 __global__ void __launch_bounds__(C::NT, C::MINB)
     mgemm2_half_kernel(VF32 V, const double* __restrict__ S, void* __restrict__ out, int out_f64,
@@ -744,33 +780,7 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
     band_tile(t, T, 0, T, G, I, J);
     const int row0 = I * C::BM, col0 = J * C::BN;
     tile_minsum<C, false, false, KU, true>(sm, V, row0, col0, 0, L.am, L.bn, acc);
-    float Sjf[C::NJ];
-#pragma unroll
-    for (int c = 0; c < C::NJ; ++c) {
-      const int j = col0 + L.col(c);
-      Sjf[c] = j < nv ? (float)S[j] : 0.0f;
-    }
-#pragma unroll
-    for (int r = 0; r < 8; ++r) {
-      const int i = row0 + L.row(r);
-      if (i >= nv) continue;
-      const double Si = S[i];
-#pragma unroll
-      for (int c = 0; c < C::NJ; ++c) {
-        const int j = col0 + L.col(c);
-        if (j <= i || j >= nv) continue;
-        const float2 hl = acc.hl(r, c);
-        if (out_f64) {
-          const double n2 = ((double)hl.x + (double)hl.y) * (double)inv_scale;
-          const double d = Si + S[j];
-          static_cast<double*>(out)[pair_index(nv, i, j)] = (d == 0.0) ? 0.0 : (2.0 * n2) / d;
-        } else {
-          const float n2 = __fmul_rn(__fadd_rn(hl.x, hl.y), inv_scale);
-          const float d = __fadd_rn((float)Si, Sjf[c]);
-          static_cast<float*>(out)[pair_index(nv, i, j)] = (d == 0.0f) ? 0.0f : __fdiv_rn(2.0f * n2, d);
-        }
-      }
-    }
+    store_tile2_half<C>(acc, L, row0, col0, nv, S, out, out_f64, inv_scale);
   }
 }
 
