@@ -520,7 +520,7 @@ extern "C" ps_status ps_autotune_batched(ps_handle h, const ps_problem* probs, i
   if (choice && choice_len > 0) {
     const int shape = best / 1000;
     if (best == kTmaVariant)
-      snprintf(choice, (size_t)choice_len, "TMA-fed pipeline, tile 128 x 128 (16 warps), 32-field slices%s",
+      snprintf(choice, (size_t)choice_len, "TMA-fed pipeline, tile 128 x 128 (16 warps), 64-field slices%s",
                detail.empty() ? " (cached)" : "");
     else
       snprintf(choice, (size_t)choice_len, "cp.async tile %d x %d (%d warps), %s add, %d-step unroll%s",

@@ -9,8 +9,8 @@
 // separate launch before it (batched_sums_kernel), so no tile waits for
 // them.
 //
-// Pipeline (as the TMA-fed 2-way and 3-way kernels): 16 warps, a 4-stage
-// shared-memory ring of 32-field slices guarded by full / ready / empty
+// Pipeline (as the TMA-fed 2-way and 3-way kernels): 16 warps, a 3-stage
+// shared-memory ring of 64-field slices guarded by full / ready / empty
 // mbarriers; lane 0 of warp 0 is the producer.  It claims the next work
 // item from a grid-wide counter (one item ahead of its use), reads the
 // item's problem record (whose tensor maps live in global memory, 128-byte
@@ -45,8 +45,11 @@ namespace {
 
 using C = mg::T128W16;
 constexpr int NW = C::NT / 32;
-constexpr int BKB = 32;      // fields per slice
-constexpr int STAGES_B = 4;  // ring depth
+// 64-field slices in a 3-slice ring (as the single-problem 3-way kernel,
+// which carries most of a batch's comparisons: the pivot min, waits and
+// releases per field halve against 32-field slices)
+constexpr int BKB = 64;      // fields per slice
+constexpr int STAGES_B = 3;  // ring depth
 constexpr int PBOX = 4;      // pivot box: 4 vectors x BKB fields
 
 struct __align__(128) SmemB {
