@@ -290,7 +290,7 @@ def batched_section(ps, synth, h, torch, sptr, peak_cmp, steps=3):
                       "call includes its error-flag read back)"}
 
 
-def threshold_section(ps, synth, h, torch, sptr):
+def threshold_section(ps, synth, h, torch, sptr, peak_cmp):
     """Exhaustive vs learned vs bound-filtered thresholded 3-way search on
     8192 x 2048 vectors from 64 latent profiles (sigma 0.4), tau = 0.7.
 
@@ -363,7 +363,9 @@ def threshold_section(ps, synth, h, torch, sptr):
     torch.cuda.empty_cache()
     return {"workload": "3way threshold 8192x2048 f32, 64 latent profiles, sigma 0.4, tau 0.7",
             "comparisons_exhaustive": nf * nv * (nv - 1) * (nv - 2) // 6,
-            "exhaustive": {"seconds": t_ex, "triples": n_ex},
+            "exhaustive": {"seconds": t_ex, "triples": n_ex,
+                           "cmp_per_s": nf * nv * (nv - 1) * (nv - 2) // 6 / t_ex,
+                           "frac_of_alu_peak": nf * nv * (nv - 1) * (nv - 2) // 6 / t_ex / peak_cmp},
             "learned": held_out, "learned_subset_training": subset,
             "bound_lossless": {"search_seconds": t_b, "triples": n_b, "identical_to_exhaustive": exact_b,
                                "blocks_searched": kept_b, "speedup": t_ex / t_b}}
@@ -780,7 +782,7 @@ def main():
     # ---- thresholded 3-way search with proposals (8192 x 2048 latent profiles) ----
     thresh = None
     if not args.no_threshold and w["way"] == 2 and ws == 1:
-        thresh = threshold_section(ps, synth, h, torch, sptr)
+        thresh = threshold_section(ps, synth, h, torch, sptr, peak_cmp)
 
     # ---- CPU-baseline leg: the oracle timed on a bounded sample, and the
     # oracle's values for the sampled GPU outputs ----

@@ -490,7 +490,7 @@ ps_status threshold_blocks(ps_ctx* h, const VF32& v, const double* S, const int*
     PS_CUDA_TRY(h, cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st));
     {
       ScopedTimer tm(h, "threshold3", st);
-      PS_CUDA_TRY(h, launch_mgemm3_thresh(h, v, S, n2, dblk, nblocks, ta, st));
+      PS_CUDA_TRY(h, launch_mgemm3_thresh(h, v, S, n2, dblk, blk.data(), nblocks, ta, st));
     }
     unsigned long long c = 0;
     PS_CUDA_TRY(h, cudaMemcpyAsync(&c, counter, sizeof(c), cudaMemcpyDeviceToHost, st));

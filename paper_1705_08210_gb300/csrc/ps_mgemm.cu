@@ -333,8 +333,14 @@ cudaError_t launch_batched(ps_ctx* h, int code, const BatchProb* probs, int npro
 }
 
 cudaError_t launch_mgemm3_thresh(ps_ctx* h, const VF32& V, const double* S, const float* n2sq,
-                                 const int* blocks, int64_t nblocks, const ThreshArgs& ta,
-                                 cudaStream_t st) {
+                                 const int* blocks, const int* blocks_host, int64_t nblocks,
+                                 const ThreshArgs& ta, cudaStream_t st) {
+  if (h->mgemm3_feed_tma && V.nf > 0) {
+    // the TMA-fed pipeline of the 3-way kernel (default)
+    int* err = async_err_word(h);
+    if (!err) return cudaErrorMemoryAllocation;
+    return launch_mgemm3_thresh_tma(h, V, S, n2sq, blocks, blocks_host, nblocks, ta, err, st);
+  }
   return launch_thresh_t128(h->num_sms, V, S, n2sq, blocks, nblocks, ta, st);
 }
 

@@ -26,6 +26,7 @@
 
 #include <algorithm>
 #include <mutex>
+#include <vector>
 
 namespace ps {
 namespace {
@@ -72,12 +73,16 @@ __device__ __forceinline__ void item3(int2 w, int& j, int& row0, int& col0) {
   col0 = (w.y & 0xffff) * C::BN;
 }
 
-template <int BK, int STAGES, int KU, bool DYN>
+// THRESH: the thresholded search instead of the slab output: every triple
+// i < j < k of the item with c3 >= tau is appended as in
+// mgemm3_thresh_kernel (same values, same keys).
+template <int BK, int STAGES, int KU, bool DYN, bool THRESH = false>
 __global__ void __launch_bounds__(C::NT, 1)
     mgemm3_tma_kernel(const __grid_constant__ CUtensorMap mapV, const __grid_constant__ CUtensorMap mapP,
                       int nv, int nf, const double* __restrict__ S, const float* __restrict__ n2sq,
                       const int2* __restrict__ items, int jb, float* __restrict__ out, int64_t ntiles,
-                      int* err, unsigned long long* __restrict__ item_ctr, unsigned long long wait_ns) {
+                      int* err, unsigned long long* __restrict__ item_ctr, unsigned long long wait_ns,
+                      ThreshArgs ta) {
   static_assert(mg::FOLD * mg::BK % BK == 0 && BK % NW == 0, "slice shape");
   constexpr int FOLD_SLICES = mg::FOLD * mg::BK / BK;
   constexpr int ROWS_PER_WARP = BK / NW;  // field rows of a slice each warp min-s with the pivot
@@ -222,6 +227,10 @@ __global__ void __launch_bounds__(C::NT, 1)
     }
     if (!ok) break;
     acc.fold();
+    if constexpr (THRESH) {
+      mg::thresh_append3(acc, L, row0, col0, j, nv, S, n2sq, ta);
+      continue;
+    }
     // Section 2.2 eq. (1) into pivot j's slab block (rows i < j, columns k > j)
     const int64_t w = nv - 1 - j;
     const int64_t base = mg::slab_offset(nv, jb, j);
@@ -253,18 +262,19 @@ __global__ void __launch_bounds__(C::NT, 1)
 }
 
 // ---- host side ----
-template <int BK, int STAGES, int KU, bool DYN>
+template <int BK, int STAGES, int KU, bool DYN, bool THRESH = false>
 struct Tma3Launch {
   static constexpr size_t smem = sizeof(Smem3<BK, STAGES>);
   static cudaError_t run(ps_ctx* h, const VF32& V, const double* S, const float* n2sq, const int2* items, int jb,
-                         float* out, int64_t ntiles, int* err, unsigned long long* item_ctr, cudaStream_t st) {
+                         float* out, int64_t ntiles, int* err, unsigned long long* item_ctr, cudaStream_t st,
+                         const ThreshArgs& ta = ThreshArgs{}) {
     static std::mutex mu;
     static uint64_t attr_done = 0;
     {
       std::lock_guard<std::mutex> lk(mu);
       const uint64_t bit = 1ull << (h->device & 63);
       if (!(attr_done & bit)) {
-        const cudaError_t e = cudaFuncSetAttribute(mgemm3_tma_kernel<BK, STAGES, KU, DYN>,
+        const cudaError_t e = cudaFuncSetAttribute(mgemm3_tma_kernel<BK, STAGES, KU, DYN, THRESH>,
                                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         attr_done |= bit;
@@ -279,13 +289,69 @@ struct Tma3Launch {
       if (e != cudaSuccess) return e;
     }
     const unsigned grid = (unsigned)std::min<int64_t>(ntiles, (int64_t)h->num_sms);
-    mgemm3_tma_kernel<BK, STAGES, KU, DYN><<<grid, C::NT, smem, st>>>(mapV, mapP, V.nv, V.nf, S, n2sq, items, jb,
-                                                                      out, ntiles, err, item_ctr, h->wait_ns);
+    mgemm3_tma_kernel<BK, STAGES, KU, DYN, THRESH><<<grid, C::NT, smem, st>>>(mapV, mapP, V.nv, V.nf, S, n2sq, items, jb,
+                                                                      out, ntiles, err, item_ctr, h->wait_ns, ta);
     return cudaGetLastError();
   }
 };
 
+// Work items of the thresholded search: block b = (I, Jt, K) of 128-vector
+// tiles contributes pivots j of tile Jt with rows i < j in tile I and
+// columns k > j in tile K, the range j in [jlo, jhi] (first[b] items before
+// it); one CTA of 128 threads per block.
+__global__ void __launch_bounds__(128) thresh_items_kernel(const int* __restrict__ blocks,
+                                                           const int64_t* __restrict__ first, int nv,
+                                                           int2* __restrict__ items) {
+  const int b = blockIdx.x;
+  const int I = blocks[3 * b], Jt = blocks[3 * b + 1], K = blocks[3 * b + 2];
+  const int jlo = max(Jt * 128, I * 128 + 1), jhi = min(min(Jt * 128 + 127, nv - 1), K * 128 + 126);
+  const int j = Jt * 128 + (int)threadIdx.x;
+  if (j >= jlo && j <= jhi) items[first[b] + (j - jlo)] = make_int2(j, (I << 16) | K);
+}
+
 }  // namespace
+
+cudaError_t launch_mgemm3_thresh_tma(ps_ctx* h, const VF32& V, const double* S, const float* n2sq,
+                                     const int* blocks, const int* blocks_host, int64_t nblocks, const ThreshArgs& ta,
+                                     int* err, cudaStream_t st) {
+  if ((uintptr_t)V.p % 16 != 0 || V.ld % 4 != 0 || V.nv < 1 || V.nf < 1) return cudaErrorInvalidValue;
+  // item offsets of every block (host: the block list is built there)
+  const int nv = V.nv;
+  std::vector<int64_t> first((size_t)nblocks + 1, 0);
+  for (int64_t b = 0; b < nblocks; ++b) {
+    const int I = blocks_host[3 * b], Jt = blocks_host[3 * b + 1], K = blocks_host[3 * b + 2];
+    const int jlo = std::max(Jt * 128, I * 128 + 1), jhi = std::min(std::min(Jt * 128 + 127, nv - 1), K * 128 + 126);
+    first[(size_t)b + 1] = first[(size_t)b] + std::max(0, jhi - jlo + 1);
+  }
+  const int64_t nitems = first[(size_t)nblocks];
+  if (nitems == 0) return cudaSuccess;
+  if (nitems >= ((int64_t)1 << 31) ||
+      (double)ceil_div(nitems, h->num_sms) * (double)ceil_div(V.nf, 16) >= 4294967295.0)
+    return cudaErrorInvalidValue;
+  int64_t* dfirst = static_cast<int64_t*>(ws_get(h, WS_AUX0, ((size_t)nblocks + 1) * sizeof(int64_t)));
+  int2* items = static_cast<int2*>(ws_get(h, WS_ITEMS, (size_t)nitems * sizeof(int2)));
+  unsigned* sync = static_cast<unsigned*>(ws_get(h, WS_SYNC, 256));
+  if (!dfirst || !items || !sync) return cudaErrorMemoryAllocation;
+  cudaError_t e = cudaMemcpyAsync(dfirst, first.data(), ((size_t)nblocks + 1) * sizeof(int64_t),
+                                  cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return e;
+  thresh_items_kernel<<<(unsigned)nblocks, 128, 0, st>>>(blocks, dfirst, nv, items);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  // the host vector must outlive the asynchronous copy
+  e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return e;
+  unsigned long long* ctr = reinterpret_cast<unsigned long long*>(sync + 4);
+  const int bk = V.nf <= 16 ? 16 : (V.nf <= 32 ? 32 : 64);
+#define PS_TMA3T_RUN(...)                                                                                      \
+  (h->mgemm3_dynamic                                                                                          \
+       ? Tma3Launch<__VA_ARGS__, true, true>::run(h, V, S, n2sq, items, 0, nullptr, nitems, err, ctr, st, ta)  \
+       : Tma3Launch<__VA_ARGS__, false, true>::run(h, V, S, n2sq, items, 0, nullptr, nitems, err, ctr, st, ta))
+  if (bk == 16) return PS_TMA3T_RUN(16, 8, 8);
+  if (bk == 32) return PS_TMA3T_RUN(32, 4, 16);
+  return PS_TMA3T_RUN(64, 3, 16);
+#undef PS_TMA3T_RUN
+}
 
 cudaError_t launch_mgemm3_tma(ps_ctx* h, const VF32& V, const double* S, const float* n2sq, const int2* items,
                               int jb, float* out, int64_t ntiles, int* err, cudaStream_t st) {

@@ -841,6 +841,49 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
   }
 }
 
+// Epilogue of a thresholded 3-way item (pivot j, tile origin row0, col0):
+// every triple i < j < k < nv of this lane with c3 >= tau is appended as a
+// lexicographic key of ORIGINAL indices (ta.perm maps a reordered index to
+// its original one) and its value.  The three vectors are taken in
+// increasing original index, so the sums of eq. (1) are formed in the same
+// order as without a reordering and every value is bit-identical to the
+// exhaustive search.
+template <class LN, class ACC>
+__device__ __forceinline__ void thresh_append3(const ACC& acc, const LN& L, int row0, int col0, int j, int nv,
+                                               const double* __restrict__ S, const float* __restrict__ n2sq,
+                                               const ThreshArgs& ta) {
+  const int* __restrict__ perm = ta.perm;
+  const int oj = perm ? perm[j] : j;
+#pragma unroll
+  for (int r = 0; r < 8; ++r) {
+    const int i = row0 + L.row(r);
+    if (i >= j) continue;
+    const int oi = perm ? perm[i] : i;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int k = col0 + L.col(c);
+      if (k <= j || k >= nv) continue;
+      int pa = i, pb = j, pc = k, a = oi, bb = oj, cc = perm ? perm[k] : k;
+      if (perm) {
+        if (a > bb) { int x = a; a = bb; bb = x; x = pa; pa = pb; pb = x; }
+        if (bb > cc) { int x = bb; bb = cc; cc = x; x = pb; pb = pc; pc = x; }
+        if (a > bb) { int x = a; a = bb; bb = x; x = pa; pa = pb; pb = x; }
+      }
+      const float v = c3_value(acc.hl(r, c), n2sq[(int64_t)pa * nv + pb], n2sq[(int64_t)pa * nv + pc],
+                               n2sq[(int64_t)pb * nv + pc],
+                               __fadd_rn(__fadd_rn((float)S[pa], (float)S[pb]), (float)S[pc]));
+      if (v >= ta.tau) {
+        const unsigned long long pos = atomicAdd(ta.counter, 1ull);
+        if (pos < (unsigned long long)ta.cap) {
+          ta.keys[pos] = ((unsigned long long)a << (2 * ta.bits)) | ((unsigned long long)bb << ta.bits) |
+                         (unsigned long long)cc;
+          ta.vals[pos] = v;
+        }
+      }
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Thresholded 3-way over an explicit list of 128-tile blocks (I, Jt, K),
 // I <= Jt <= K: work item = (block, pivot j in tile Jt).  Every triple
@@ -856,7 +899,6 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
   const Lanes<C> L;
   Acc<PACKED, C::NJ> acc;
   const int nv = V.nv;
-  const int* __restrict__ perm = ta.perm;
   constexpr int B = C::BM;
   for (int64_t t = blockIdx.x; t < nitems; t += gridDim.x) {
     const int64_t b = t / B;
@@ -870,38 +912,7 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
     // its sub-partition for the other warp (the pivot's partial row tile)
     tile_minsum<C, true, PACKED, KU>(sm, V, row0, col0, j, L.am, L.bn, acc,
                                      row0 + (int)(threadIdx.x >> 5) / C::WN * 64 < j);
-    const int oj = perm ? perm[j] : j;
-#pragma unroll
-    for (int r = 0; r < 8; ++r) {
-      const int i = row0 + L.row(r);
-      if (i >= j) continue;
-      const int oi = perm ? perm[i] : i;
-#pragma unroll
-      for (int c = 0; c < C::NJ; ++c) {
-        const int k = col0 + L.col(c);
-        if (k <= j || k >= nv) continue;
-        // the three vectors in increasing ORIGINAL index (a, b, c): the sums of
-        // eq. (1) are then formed in the same order as without a reordering,
-        // so every value is bit-identical to the exhaustive search
-        int pa = i, pb = j, pc = k, a = oi, bb = oj, cc = perm ? perm[k] : k;
-        if (perm) {
-          if (a > bb) { int x = a; a = bb; bb = x; x = pa; pa = pb; pb = x; }
-          if (bb > cc) { int x = bb; bb = cc; cc = x; x = pb; pb = pc; pc = x; }
-          if (a > bb) { int x = a; a = bb; bb = x; x = pa; pa = pb; pb = x; }
-        }
-        const float v = c3_value(acc.hl(r, c), n2sq[(int64_t)pa * nv + pb], n2sq[(int64_t)pa * nv + pc],
-                                 n2sq[(int64_t)pb * nv + pc],
-                                 __fadd_rn(__fadd_rn((float)S[pa], (float)S[pb]), (float)S[pc]));
-        if (v >= ta.tau) {
-          const unsigned long long pos = atomicAdd(ta.counter, 1ull);
-          if (pos < (unsigned long long)ta.cap) {
-            ta.keys[pos] = ((unsigned long long)a << (2 * ta.bits)) |
-                           ((unsigned long long)bb << ta.bits) | (unsigned long long)cc;
-            ta.vals[pos] = v;
-          }
-        }
-      }
-    }
+    thresh_append3(acc, L, row0, col0, j, nv, S, n2sq, ta);
   }
 }
 
