@@ -86,3 +86,28 @@ def test_threshold_consistent_with_slab_output(ps, handle):
     assert st == ps.PS_OK
     assert count == int((full >= tau).sum())
     np.testing.assert_array_equal(vals, full[slab_index(nv, 0, trip[:, 0], trip[:, 1], trip[:, 2])])
+
+
+@pytest.mark.parametrize("nv,nf", [(300, 16), (260, 40), (400, 100)])
+@pytest.mark.parametrize("use_proposal", [0, 2])
+def test_threshold_pipelines_identical(ps, nv, nf, use_proposal):
+    # the thresholded search on the TMA-fed 3-way pipeline (default; items
+    # from a counter, and the static schedule) and on the cp.async kernel:
+    # the same sorted triples and bit-identical values, exhaustively and
+    # with the lossless bound filter; 16-, 32- and 64-field slices
+    V, _ = synth.latent_profiles(nv, nf, synth.seed_for(5, 300 + nf), n_profiles=8, sigma=0.3)
+    res = {}
+    for key, fields in (("tma", {}), ("tma-static", dict(mgemm3_schedule=2)), ("cpasync", dict(mgemm3_feed=2))):
+        h = ps.Handle(0, **fields)
+        try:
+            n = nv * (nv - 1) * (nv - 2) // 6
+            st, count, trip, vals = threshold_3way(ps, h, V, 0.6, capacity=n, use_proposal=use_proposal)
+            assert st == ps.PS_OK
+            res[key] = (count, trip, vals)
+        finally:
+            h.close()
+    assert res["cpasync"][0] > 0
+    for key in ("tma", "tma-static"):
+        assert res[key][0] == res["cpasync"][0], key
+        np.testing.assert_array_equal(res[key][1], res["cpasync"][1], err_msg=key)
+        np.testing.assert_array_equal(res[key][2], res["cpasync"][2], err_msg=key)
