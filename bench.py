@@ -544,15 +544,34 @@ def main():
         hstep()
         if ws > 1:
             torch.distributed.barrier()
+        # (the library's event pairs around the min-product launches: the
+        # kernel's share of the end-to-end step)
+        ps.check(ps.ps_timing_enable(h.h, 1), h.h)
         t0 = time.perf_counter()
         for _ in range(args.steps):
             hstep()
         dt = (time.perf_counter() - t0) / args.steps
+        n_e, k_e = ctypes.c_int64(), ctypes.c_double()
+        ps.check(ps.ps_timing_read(h.h, (b"mgemm3" if w["way"] == 3 else b"mgemm2"), ctypes.byref(n_e),
+                                   ctypes.byref(k_e)), h.h)
+        ps.check(ps.ps_timing_enable(h.h, 0), h.h)
+        # one plain copy of the step's input from the same pinned buffer
+        Vd = torch.empty(Vh.shape, dtype=Vh.dtype, device="cuda")
+        c0 = torch.cuda.Event(enable_timing=True)
+        c1 = torch.cuda.Event(enable_timing=True)
+        Vd.copy_(Vh, non_blocking=True)
+        c0.record()
+        Vd.copy_(Vh, non_blocking=True)
+        c1.record()
+        torch.cuda.synchronize()
+        h2d_ms = c0.elapsed_time(c1)
+        del Vd
         if ws > 1:
             t = torch.tensor([dt], device="cuda", dtype=torch.float64)
             torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
             dt = float(t.item())
         e2e = {"value": (cmp_per_step if strong else ws * cmp_per_step) / dt, "unit": UNIT, "ms_per_step": dt * 1e3,
+               "kernel_ms_per_step": k_e.value / args.steps, "h2d_copy_ms": h2d_ms,
                "h2d_bytes_per_step": int(Vh.numel() * Vh.element_size()),
                "d2h_bytes_per_step": int(outh.numel() * outh.element_size())}
         if w["way"] == 2 and ws == 1:

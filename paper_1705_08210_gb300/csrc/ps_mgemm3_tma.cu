@@ -228,7 +228,7 @@ __global__ void __launch_bounds__(C::NT, 1)
     if (!ok) break;
     acc.fold();
     if constexpr (THRESH) {
-      mg::thresh_append3(acc, L, row0, col0, j, nv, S, n2sq, ta);
+      mg::thresh_append3<C::NJ>(acc, L, row0, col0, j, nv, S, n2sq, ta);
       continue;
     }
     // Section 2.2 eq. (1) into pivot j's slab block (rows i < j, columns k > j)

@@ -847,8 +847,8 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
 // its original one) and its value.  The three vectors are taken in
 // increasing original index, so the sums of eq. (1) are formed in the same
 // order as without a reordering and every value is bit-identical to the
-// exhaustive search.
-template <class LN, class ACC>
+// exhaustive search.  NJ: the lane's columns.
+template <int NJ, class LN, class ACC>
 __device__ __forceinline__ void thresh_append3(const ACC& acc, const LN& L, int row0, int col0, int j, int nv,
                                                const double* __restrict__ S, const float* __restrict__ n2sq,
                                                const ThreshArgs& ta) {
@@ -860,7 +860,7 @@ __device__ __forceinline__ void thresh_append3(const ACC& acc, const LN& L, int 
     if (i >= j) continue;
     const int oi = perm ? perm[i] : i;
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
+    for (int c = 0; c < NJ; ++c) {
       const int k = col0 + L.col(c);
       if (k <= j || k >= nv) continue;
       int pa = i, pb = j, pc = k, a = oi, bb = oj, cc = perm ? perm[k] : k;
@@ -912,7 +912,7 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
     // its sub-partition for the other warp (the pivot's partial row tile)
     tile_minsum<C, true, PACKED, KU>(sm, V, row0, col0, j, L.am, L.bn, acc,
                                      row0 + (int)(threadIdx.x >> 5) / C::WN * 64 < j);
-    thresh_append3(acc, L, row0, col0, j, nv, S, n2sq, ta);
+    thresh_append3<C::NJ>(acc, L, row0, col0, j, nv, S, n2sq, ta);
   }
 }
 
