@@ -233,11 +233,15 @@ def test_operand_feeds_bit_identical(ps, handle, nv, nf):
     ref = oracle.c2_packed(oracle.to_vector_major(V))
     results = {}
     for feed, bk, dyn in (("cpasync", "16", "1"), ("tma", "16", "1"), ("tma", "32", "1"), ("tma", "64", "1"),
-                          ("tma", "32", "0"), ("tma-mixed-adds", "32", "1")):
-        # dyn 0: static round-robin tiles; mixed adds: half of each lane's
-        # columns accumulated by scalar adds (n_f > 256 only)
+                          ("tma", "32", "0"), ("tma-packed-adds", "32", "1"), ("tma-scalar-adds", "32", "1"),
+                          ("tma-lookahead1", "32", "1")):
+        # dyn 0: static round-robin tiles; add forms other than the mixed
+        # default (n_f > 256 only): all packed, all scalar; a producer one
+        # slice ahead instead of three
+        adds = {"tma-packed-adds": 1, "tma-scalar-adds": 2}.get(feed, 0)
         h = ps.Handle(0, mgemm_feed=2 if feed == "cpasync" else 1, tma_slice=int(bk),
-                      tma_schedule=1 if dyn == "1" else 2, mgemm_add=3 if feed == "tma-mixed-adds" else 0)
+                      tma_schedule=1 if dyn == "1" else 2, mgemm_add=adds,
+                      tma_lookahead=1 if feed == "tma-lookahead1" else 0)
         try:
             r = [metrics_2way(ps, h, V), metrics_2way(ps, h, V, out_dtype=np.float64),
                  metrics_2way(ps, h, V, out_dtype=np.uint8)]
