@@ -684,6 +684,32 @@ def main():
     # ---- secondary: the 3-way workload ----
     secondary = None
     if not args.no_secondary and w["way"] == 2 and ws == 1:
+        # thresholded 2-way on the benchmark matrix: every pair with c2 >= tau
+        # (tau: the 0.9981 quantile of 10^6 sampled metrics, about 10^6 hits),
+        # sorted; device output buffers
+        torch.manual_seed(11)
+        samp = out[torch.randint(0, out.numel(), (1000000,), device="cuda")]
+        tau2 = float(torch.quantile(samp.float(), 0.9981))
+        cap2 = 4_000_000
+        tp = torch.empty((cap2, 3), dtype=torch.int32, device="cuda")
+        tc = torch.empty(1, dtype=torch.int64, device="cuda")
+        for _ in range(2):
+            ps.check(ps.ps_threshold_2way(h.h, ctypes.byref(m), tau2, tp.data_ptr(), cap2, tc.data_ptr(), sptr), h.h)
+        ps.check(ps.ps_timing_enable(h.h, 1), h.h)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(3):
+            ps.check(ps.ps_threshold_2way(h.h, ctypes.byref(m), tau2, tp.data_ptr(), cap2, tc.data_ptr(), sptr), h.h)
+        torch.cuda.synchronize()
+        mst = (time.perf_counter() - t0) / 3 * 1e3
+        ps.check(ps.ps_timing_read(h.h, b"threshold2", ctypes.byref(n_launch), ctypes.byref(k_ms)), h.h)
+        ps.check(ps.ps_timing_enable(h.h, 0), h.h)
+        kt2 = k_ms.value / max(n_launch.value, 1)
+        thr2 = {
+            "tau": tau2, "pairs": int(tc.item()), "ms_per_call": mst, "kernel_ms": kt2,
+            "frac_of_alu_peak": cmp_per_step / (kt2 / 1e3) / peak_cmp,
+            "note": "ps_threshold_2way with device buffers, sorted (i, j, c2); wall time per call (synchronising)"}
+        del tp, tc, samp
         del out
         torch.cuda.empty_cache()
         w3 = WORKLOADS["3way_2048x4096_f32"]
@@ -792,6 +818,7 @@ def main():
         sor["input"] = f"{nvb} x {nfb} bit-packed 0/1 (p_one 0.15), {words.nbytes / 1e6:.1f} MB"
         secondary["sorenson_b1_32768x8192"] = sor
         del Wb, ob
+        secondary["threshold_2way_32768x8192"] = thr2
 
     # ---- batched uneven instances (64 problems, one persistent graph launch) ----
     batched = None

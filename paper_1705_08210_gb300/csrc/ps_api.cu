@@ -986,7 +986,14 @@ ps_status ps_threshold_2way(ps_handle h, const ps_matrix* V, float tau, ps_pair*
     PS_CUDA_TRY(h, cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st));
     {
       ScopedTimer tm(h, "threshold2", st);
-      PS_CUDA_TRY(h, launch_mgemm2_thresh(h->num_sms, h->mgemm_band, P.f32, P.S, ta, st));
+      if (h->mgemm_feed_tma && V->nf > 0) {
+        // the TMA-fed pipeline (default); mgemm_feed = 2: the cp.async kernel
+        int* err = async_err_word(h);
+        if (!err) return PS_ERR_OOM;
+        PS_CUDA_TRY(h, launch_mgemm2_thresh_tma(h, P.f32, P.S, ta, st, err));
+      } else {
+        PS_CUDA_TRY(h, launch_mgemm2_thresh(h->num_sms, h->mgemm_band, P.f32, P.S, ta, st));
+      }
     }
     unsigned long long c = 0;
     PS_CUDA_TRY(h, cudaMemcpyAsync(&c, counter, sizeof(c), cudaMemcpyDeviceToHost, st));

@@ -663,6 +663,55 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
   }
 }
 
+// Epilogue of a thresholded 2-way tile: every pair i < j < nv of this lane
+// with c2 >= tau, the value computed exactly as store_tile2's FP32 output, is
+// appended warp-aggregated (one atomic per warp and output position) as key
+// i << bits | j; appends past `cap` are counted but not stored.  Every lane
+// of the warp takes part (the ballots).  NJ: the lane's columns.
+template <int NJ, class LN, class ACC>
+__device__ __forceinline__ void thresh_append2(const ACC& acc, const LN& L, int row0, int col0, int64_t nv,
+                                               const double* __restrict__ S, const ThreshArgs& ta) {
+  const int lane = threadIdx.x & 31;
+  float Sjf[NJ];
+#pragma unroll
+  for (int c = 0; c < NJ; ++c) {
+    const int j = col0 + L.col(c);
+    Sjf[c] = j < nv ? (float)S[j] : 0.0f;
+  }
+#pragma unroll
+  for (int r = 0; r < 8; ++r) {
+    const int i = row0 + L.row(r);
+    const float Sif = i < nv ? (float)S[i] : 0.0f;
+#pragma unroll
+    for (int c = 0; c < NJ; ++c) {
+      const int j = col0 + L.col(c);
+      float c2 = 0.0f;
+      bool hit = false;
+      if (i < nv && j > i && j < nv) {
+        const float2 hl = acc.hl(r, c);
+        const float n2 = __fadd_rn(hl.x, hl.y);
+        const float d = __fadd_rn(Sif, Sjf[c]);
+        c2 = (d == 0.0f) ? 0.0f : __fdiv_rn(2.0f * n2, d);
+        hit = c2 >= ta.tau;
+      }
+      const unsigned m = __ballot_sync(0xffffffffu, hit);
+      if (m) {
+        const int leader = __ffs(m) - 1;
+        unsigned long long base = 0;
+        if (lane == leader) base = atomicAdd(ta.counter, (unsigned long long)__popc(m));
+        base = __shfl_sync(0xffffffffu, base, leader);
+        if (hit) {
+          const unsigned long long pos = base + (unsigned)__popc(m & ((1u << lane) - 1u));
+          if (pos < (unsigned long long)ta.cap) {
+            ta.keys[pos] = ((unsigned long long)i << ta.bits) | (unsigned long long)j;
+            ta.vals[pos] = c2;
+          }
+        }
+      }
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Thresholded 2-way: every pair with c2 >= tau, the value computed exactly as
 // mgemm2_kernel's FP32 output.  Hits are appended warp-aggregated (one atomic
@@ -677,50 +726,12 @@ __global__ void __launch_bounds__(C::NT, C::MINB)
   const Lanes<C> L;
   Acc<PACKED, C::NJ> acc;
   const int64_t nv = V.nv;
-  const int lane = threadIdx.x & 31;
   for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
     int I, J;
     band_tile(t, T, 0, T, G, I, J);
     const int row0 = I * C::BM, col0 = J * C::BN;
     tile_minsum<C, false, PACKED, KU>(sm, V, row0, col0, 0, L.am, L.bn, acc);
-    float Sjf[C::NJ];
-#pragma unroll
-    for (int c = 0; c < C::NJ; ++c) {
-      const int j = col0 + L.col(c);
-      Sjf[c] = j < nv ? (float)S[j] : 0.0f;
-    }
-#pragma unroll
-    for (int r = 0; r < 8; ++r) {
-      const int i = row0 + L.row(r);
-      const float Sif = i < nv ? (float)S[i] : 0.0f;
-#pragma unroll
-      for (int c = 0; c < C::NJ; ++c) {
-        const int j = col0 + L.col(c);
-        float c2 = 0.0f;
-        bool hit = false;
-        if (i < nv && j > i && j < nv) {
-          const float2 hl = acc.hl(r, c);
-          const float n2 = __fadd_rn(hl.x, hl.y);
-          const float d = __fadd_rn(Sif, Sjf[c]);
-          c2 = (d == 0.0f) ? 0.0f : __fdiv_rn(2.0f * n2, d);
-          hit = c2 >= ta.tau;
-        }
-        const unsigned m = __ballot_sync(0xffffffffu, hit);
-        if (m) {
-          const int leader = __ffs(m) - 1;
-          unsigned long long base = 0;
-          if (lane == leader) base = atomicAdd(ta.counter, (unsigned long long)__popc(m));
-          base = __shfl_sync(0xffffffffu, base, leader);
-          if (hit) {
-            const unsigned long long pos = base + (unsigned)__popc(m & ((1u << lane) - 1u));
-            if (pos < (unsigned long long)ta.cap) {
-              ta.keys[pos] = ((unsigned long long)i << ta.bits) | (unsigned long long)j;
-              ta.vals[pos] = c2;
-            }
-          }
-        }
-      }
-    }
+    thresh_append2<C::NJ>(acc, L, row0, col0, nv, S, ta);
   }
 }
 

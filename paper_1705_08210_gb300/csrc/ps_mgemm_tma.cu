@@ -77,13 +77,17 @@ template <int ADDS>
 using AccT = std::conditional_t<ADDS == 1, mg::AccMix<C::NJ>,
                                 std::conditional_t<ADDS == 0, mg::Acc<true, C::NJ>, mg::Acc<false, C::NJ>>>;
 
-template <int BK, int STAGES, int KU, int EPI, bool DYN, int ADDS = 1>
+// THRESH: the thresholded search instead of the packed output: every pair
+// with c2 >= tau appended (mg::thresh_append2; values as the FP32 output).
+template <int BK, int STAGES, int KU, int EPI, bool DYN, int ADDS = 1, bool THRESH = false>
 __global__ void __launch_bounds__(C::NT, 1)
     mgemm2_tma_kernel(const __grid_constant__ CUtensorMap mapV, int nv, int nf,
                       const double* __restrict__ S, void* __restrict__ out, int mode, int T, int R0,
                       int R1, int G, int64_t ntiles, int* err, unsigned* __restrict__ sync, int sync_sl,
                       unsigned long long* __restrict__ tile_ctr, unsigned long long wait_ns,
-                      const float* __restrict__ Sf, const unsigned* __restrict__ lean_words, int look) {
+                      const float* __restrict__ Sf, const unsigned* __restrict__ lean_words, int look,
+                      ThreshArgs ta) {
+  static_assert(!THRESH || EPI == 0, "the thresholded search has the plain epilogue");
   static_assert(mg::FOLD * mg::BK % BK == 0, "a fold boundary ends a slice");
   constexpr int FOLD_SLICES = mg::FOLD * mg::BK / BK;  // 64 fields per compensated fold
   constexpr uint32_t SLICE_BYTES = 2u * BK * C::BM * sizeof(float);
@@ -233,6 +237,8 @@ __global__ void __launch_bounds__(C::NT, 1)
         mg::store_tile2_lean<C, true, true, EPI == 2>(acc, L, row0, col0, nv, Sfi, Sfj, out);
       else
         mg::store_tile2_lean<C, true, false, EPI == 2>(acc, L, row0, col0, nv, Sfi, Sfj, out);
+    } else if constexpr (THRESH) {
+      mg::thresh_append2<C::NJ>(acc, L, row0, col0, nv, S, ta);
     } else {
       mg::store_tile2<C, true>(acc, L, row0, col0, nv, S, out, mode);
     }
@@ -242,19 +248,19 @@ __global__ void __launch_bounds__(C::NT, 1)
 }
 
 // ---- host side ----
-template <int BK, int STAGES, int KU, int EPI = 0, bool DYN = false, int ADDS = 1>
+template <int BK, int STAGES, int KU, int EPI = 0, bool DYN = false, int ADDS = 1, bool THRESH = false>
 struct TmaLaunch {
   static constexpr size_t smem = sizeof(SmemT<BK, STAGES>);
   static cudaError_t run(ps_ctx* h, const VF32& V, const double* S, void* out, int mode, cudaStream_t st,
                          int T, int R0, int R1, int G, int64_t ntiles, int* err, unsigned* sync,
-                         const NarrowPrep& np) {
+                         const NarrowPrep& np, const ThreshArgs& ta = ThreshArgs{}) {
     static std::mutex mu;
     static uint64_t attr_done = 0;
     {
       std::lock_guard<std::mutex> lk(mu);
       const uint64_t bit = 1ull << (h->device & 63);
       if (!(attr_done & bit)) {
-        const cudaError_t e = cudaFuncSetAttribute(mgemm2_tma_kernel<BK, STAGES, KU, EPI, DYN, ADDS>,
+        const cudaError_t e = cudaFuncSetAttribute(mgemm2_tma_kernel<BK, STAGES, KU, EPI, DYN, ADDS, THRESH>,
                                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         attr_done |= bit;
@@ -281,9 +287,9 @@ struct TmaLaunch {
     attr[0].val.cooperative = sync_sl ? 1 : 0;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, mgemm2_tma_kernel<BK, STAGES, KU, EPI, DYN, ADDS>, map, (int)V.nv, (int)V.nf, S, out,
+    return cudaLaunchKernelEx(&cfg, mgemm2_tma_kernel<BK, STAGES, KU, EPI, DYN, ADDS, THRESH>, map, (int)V.nv, (int)V.nf, S, out,
                               mode, T, R0, R1, G, ntiles, err, sync, sync_sl, tile_ctr, h->wait_ns, np.Sf, np.words,
-                              h->tma_lookahead ? std::min(h->tma_lookahead, STAGES - 1) : STAGES - 1);
+                              h->tma_lookahead ? std::min(h->tma_lookahead, STAGES - 1) : STAGES - 1, ta);
   }
 };
 
@@ -343,6 +349,28 @@ cudaError_t launch_mgemm2_tma(ps_ctx* h, const VF32& V, const double* S, void* o
   if (ku == 32) return PS_TMA_RUN(32, 4, 32);
   return dyn ? PS_TMA_RUN(32, 4, 16, 0, true) : PS_TMA_RUN(32, 4, 16);
 #undef PS_TMA_RUN
+}
+
+// The thresholded 2-way search (every pair with c2 >= tau) on the TMA-fed
+// pipeline, over the whole upper triangle.
+cudaError_t launch_mgemm2_thresh_tma(ps_ctx* h, const VF32& V, const double* S, const ThreshArgs& ta,
+                                     cudaStream_t st, int* err) {
+  if ((uintptr_t)V.p % 16 != 0 || V.ld % 4 != 0 || V.nv < 1 || V.nf < 1) return cudaErrorInvalidValue;
+  const int T = (int)ceil_div(V.nv, C::BM);
+  const int64_t ntiles = (int64_t)T * (T + 1) / 2;
+  if (ntiles >= ((int64_t)1 << 31) ||
+      (double)ceil_div(ntiles, h->num_sms) * (double)ceil_div(V.nf, 16) >= 4294967295.0)
+    return cudaErrorInvalidValue;
+  unsigned* sync = static_cast<unsigned*>(ws_get(h, WS_SYNC, 256));
+  if (!sync) return cudaErrorMemoryAllocation;
+  const NarrowPrep np{nullptr, nullptr};
+  const int G = std::max(1, h->mgemm_band);
+  const bool dyn = h->mgemm_tma_dynamic && h->mgemm_tma_sync <= 0;
+#define PS_TMAT_RUN(...) \
+  TmaLaunch<__VA_ARGS__>::run(h, V, S, nullptr, OUT2_C2_F32, st, T, 0, T, G, ntiles, err, sync, np, ta)
+  if (V.nf <= 32) return dyn ? PS_TMAT_RUN(16, 8, 8, 0, true, 1, true) : PS_TMAT_RUN(16, 8, 8, 0, false, 1, true);
+  return dyn ? PS_TMAT_RUN(32, 4, 16, 0, true, 1, true) : PS_TMAT_RUN(32, 4, 16, 0, false, 1, true);
+#undef PS_TMAT_RUN
 }
 
 }  // namespace ps

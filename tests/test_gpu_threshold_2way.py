@@ -74,3 +74,26 @@ def test_threshold_2way_capacity_overflow_and_all_pairs(ps, handle):
     np.testing.assert_array_equal(p2, pairs[:1000])
     st, count, p3, _ = threshold_2way(ps, handle, V, 1.5, capacity=0)
     assert st == ps.PS_OK and count == 0
+
+
+@pytest.mark.parametrize("nv,nf", [(300, 16), (700, 40), (1300, 300)])
+def test_threshold_2way_pipelines_identical(ps, nv, nf):
+    # the thresholded 2-way search on the TMA-fed pipeline (default; tiles
+    # from a counter, and the static schedule) and on the cp.async kernel:
+    # the same sorted pairs and bit-identical values (16- and 32-field
+    # slices), equal to the packed FP32 output at those pairs
+    V = synth.zero_inflated(nv, nf, synth.seed_for(6, 400 + nf))
+    res = {}
+    for key, fields in (("tma", {}), ("tma-static", dict(tma_schedule=2)), ("cpasync", dict(mgemm_feed=2))):
+        h = ps.Handle(0, **fields)
+        try:
+            st, count, pairs, vals = threshold_2way(ps, h, V, 0.3, capacity=nv * (nv - 1) // 2)
+            assert st == ps.PS_OK
+            res[key] = (count, pairs, vals)
+        finally:
+            h.close()
+    assert res["cpasync"][0] > 0
+    for key in ("tma", "tma-static"):
+        assert res[key][0] == res["cpasync"][0], key
+        np.testing.assert_array_equal(res[key][1], res["cpasync"][1], err_msg=key)
+        np.testing.assert_array_equal(res[key][2], res["cpasync"][2], err_msg=key)
