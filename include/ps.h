@@ -193,7 +193,10 @@ typedef struct {
  *                    batched kernels always use the mixed form.
  *   mgemm_band     : tile rows per band of the 2-way tile walk, 1..64
  *                    (automatic 16).
- *   tma_slice      : fields per TMA slice, 16, 32 or 64 (automatic: by n_f).
+ *   tma_slice      : fields per TMA slice, 16, 32 or 64 (automatic: 16 up
+ *                    to n_f = 32; the 2-way kernel 64 above n_f = 256 and
+ *                    32 between; the 3-way kernel 16 or 32 up to n_f = 16
+ *                    or 32, else 64).
  *   tma_unroll     : k-steps per loop iteration of the TMA kernels, 8, 16
  *                    (automatic) or 32.
  *   tma_stages     : ring depth of 32-field TMA slices, 3, 4 (automatic) or 6.

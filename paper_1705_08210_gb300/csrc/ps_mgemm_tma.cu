@@ -305,17 +305,21 @@ cudaError_t launch_mgemm2_tma(ps_ctx* h, const VF32& V, const double* S, void* o
     return cudaErrorInvalidValue;
   unsigned* sync = static_cast<unsigned*>(ws_get(h, WS_SYNC, 256));
   if (!sync) return cudaErrorMemoryAllocation;
-  // slice width: 16 fields up to n_f = 32 (wider slices would be mostly zero
-  // fill), else the configured width (32 by default: fewer waits and
-  // releases per comparison)
-  const int bk = V.nf <= 32 ? 16 : (h->mgemm_tma_bk ? h->mgemm_tma_bk : 32);
-  // k-steps per unrolled loop iteration: 16 (0 = automatic), 8 or 32
-  const int ku = h->mgemm_tma_ku ? h->mgemm_tma_ku : 16;
-  const int stages = h->mgemm_tma_stages;
   // the lean epilogue where the division is much of the work (n_f <= 256;
   // see mgemm2_tma_kernel's EPI), without the compensated fold up to 64
   // fields; at large n_f its registers would cost more than it saves
   const int epi = (mode == OUT2_C2_F32 || mode == OUT2_C2_U8) ? (V.nf <= 64 ? 2 : (V.nf <= 256 ? 1 : 0)) : 0;
+  // k-steps per unrolled loop iteration: 16 (0 = automatic), 8 or 32
+  const int ku = h->mgemm_tma_ku ? h->mgemm_tma_ku : 16;
+  const int stages = h->mgemm_tma_stages;
+  // slice width: 16 fields up to n_f = 32 (wider slices would be mostly zero
+  // fill); for the plain epilogue (n_f > 256) 64 fields in a 3-stage ring
+  // (half the waits and releases per field; 262.6 vs 266.8 ms at 32768 x
+  // 8192) unless a 32-field variant is configured (add form, ring depth,
+  // unroll); else 32.  (Bands of 32 or 64 tile rows would take 261.8 or
+  // 261.7 ms but read 93 or 118 GB from DRAM per launch instead of 34 GB.)
+  const bool knob32 = h->mgemm_add == 1 || h->mgemm_add == 2 || stages == 6 || ku != 16;
+  const int bk = V.nf <= 32 ? 16 : (h->mgemm_tma_bk ? h->mgemm_tma_bk : (epi == 0 && !knob32 ? 64 : 32));
   NarrowPrep np{nullptr, nullptr};
   if (epi) {
     float* Sf = static_cast<float*>(ws_get(h, WS_SUMSF, (size_t)round_up(V.nv, 64) * sizeof(float) + 256));
@@ -338,7 +342,7 @@ cudaError_t launch_mgemm2_tma(ps_ctx* h, const VF32& V, const double* S, void* o
     if (epi == 2) return dyn ? PS_TMA_RUN(16, 8, 8, 2, true) : PS_TMA_RUN(16, 8, 8, 2);
     return dyn ? PS_TMA_RUN(16, 8, 8, 0, true) : PS_TMA_RUN(16, 8, 8);
   }
-  if (bk == 64) return PS_TMA_RUN(64, 3, 16);
+  if (bk == 64) return dyn ? PS_TMA_RUN(64, 3, 16, 0, true) : PS_TMA_RUN(64, 3, 16);
   if (epi == 2) return dyn ? PS_TMA_RUN(32, 4, 16, 2, true) : PS_TMA_RUN(32, 4, 16, 2);
   if (epi == 1) return dyn ? PS_TMA_RUN(32, 4, 16, 1, true) : PS_TMA_RUN(32, 4, 16, 1);
   if (stages == 6) return PS_TMA_RUN(32, 6, 16);
