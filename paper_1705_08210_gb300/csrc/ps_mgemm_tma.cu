@@ -372,7 +372,9 @@ cudaError_t launch_mgemm2_thresh_tma(ps_ctx* h, const VF32& V, const double* S, 
   const bool dyn = h->mgemm_tma_dynamic && h->mgemm_tma_sync <= 0;
 #define PS_TMAT_RUN(...) \
   TmaLaunch<__VA_ARGS__>::run(h, V, S, nullptr, OUT2_C2_F32, st, T, 0, T, G, ntiles, err, sync, np, ta)
+  // slice widths as the packed-output kernel's
   if (V.nf <= 32) return dyn ? PS_TMAT_RUN(16, 8, 8, 0, true, 1, true) : PS_TMAT_RUN(16, 8, 8, 0, false, 1, true);
+  if (V.nf > 256) return dyn ? PS_TMAT_RUN(64, 3, 16, 0, true, 1, true) : PS_TMAT_RUN(64, 3, 16, 0, false, 1, true);
   return dyn ? PS_TMAT_RUN(32, 4, 16, 0, true, 1, true) : PS_TMAT_RUN(32, 4, 16, 0, false, 1, true);
 #undef PS_TMAT_RUN
 }
