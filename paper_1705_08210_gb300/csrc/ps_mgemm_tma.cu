@@ -316,10 +316,14 @@ cudaError_t launch_mgemm2_tma(ps_ctx* h, const VF32& V, const double* S, void* o
   // fill); for the plain epilogue (n_f > 256) 64 fields in a 3-stage ring
   // (half the waits and releases per field; 262.6 vs 266.8 ms at 32768 x
   // 8192) unless a 32-field variant is configured (add form, ring depth,
-  // unroll); else 32.  (Bands of 32 or 64 tile rows would take 261.8 or
-  // 261.7 ms but read 93 or 118 GB from DRAM per launch instead of 34 GB.)
+  // unroll) or the last 64-field slice would be mostly zero fill (n_f mod 64
+  // in 1..32, below 2048 fields); else 32.  (Bands of 32 or 64 tile rows
+  // would take 261.8 or 261.7 ms but read 93 or 118 GB from DRAM per launch
+  // instead of 34 GB.)
   const bool knob32 = h->mgemm_add == 1 || h->mgemm_add == 2 || stages == 6 || ku != 16;
-  const int bk = V.nf <= 32 ? 16 : (h->mgemm_tma_bk ? h->mgemm_tma_bk : (epi == 0 && !knob32 ? 64 : 32));
+  const bool fill64 = V.nf >= 2048 || V.nf % 64 == 0 || V.nf % 64 > 32;
+  const int bk =
+      V.nf <= 32 ? 16 : (h->mgemm_tma_bk ? h->mgemm_tma_bk : (epi == 0 && !knob32 && fill64 ? 64 : 32));
   NarrowPrep np{nullptr, nullptr};
   if (epi) {
     float* Sf = static_cast<float*>(ws_get(h, WS_SUMSF, (size_t)round_up(V.nv, 64) * sizeof(float) + 256));
@@ -373,8 +377,10 @@ cudaError_t launch_mgemm2_thresh_tma(ps_ctx* h, const VF32& V, const double* S, 
 #define PS_TMAT_RUN(...) \
   TmaLaunch<__VA_ARGS__>::run(h, V, S, nullptr, OUT2_C2_F32, st, T, 0, T, G, ntiles, err, sync, np, ta)
   // slice widths as the packed-output kernel's
+  const bool fill64 = V.nf >= 2048 || V.nf % 64 == 0 || V.nf % 64 > 32;
   if (V.nf <= 32) return dyn ? PS_TMAT_RUN(16, 8, 8, 0, true, 1, true) : PS_TMAT_RUN(16, 8, 8, 0, false, 1, true);
-  if (V.nf > 256) return dyn ? PS_TMAT_RUN(64, 3, 16, 0, true, 1, true) : PS_TMAT_RUN(64, 3, 16, 0, false, 1, true);
+  if (V.nf > 256 && fill64)
+    return dyn ? PS_TMAT_RUN(64, 3, 16, 0, true, 1, true) : PS_TMAT_RUN(64, 3, 16, 0, false, 1, true);
   return dyn ? PS_TMAT_RUN(32, 4, 16, 0, true, 1, true) : PS_TMAT_RUN(32, 4, 16, 0, false, 1, true);
 #undef PS_TMAT_RUN
 }
