@@ -141,9 +141,9 @@ __device__ __forceinline__ void kloop(const NLanes& L, const float* As, const fl
     float a[8], b[4];
     L.load(As, Bs, kk, a, b);
 #pragma unroll
-    for (int r = 0; r < 8; ++r)
+    for (int p = 0; p < 2; ++p)
 #pragma unroll
-      for (int p = 0; p < 2; ++p) acc[r][p] = mg::f2_add(acc[r][p], fminf(a[r], b[2 * p]), fminf(a[r], b[2 * p + 1]));
+      for (int r = 0; r < 8; ++r) acc[r][p] = mg::f2_add(acc[r][p], fminf(a[r], b[2 * p]), fminf(a[r], b[2 * p + 1]));
     constexpr int K0 = BK / 4, KE = BK - K0;
     if (kk >= K0) {
 #pragma unroll
