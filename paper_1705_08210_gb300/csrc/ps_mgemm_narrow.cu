@@ -129,9 +129,11 @@ __device__ __forceinline__ void store_prev(const Prev& pv, int e, bool on, void*
 }
 
 // BK k-steps of the micro-kernel on a landed slice, with the previous tile's
-// 32 outputs spread over the last 3/4 of them (stores predicated on `on`;
-// the first quarter gives the previous tile's sums, loaded at its end, time
-// to arrive).
+// 32 outputs spread over all but the first 64 / BK of them (stores
+// predicated on `on`; the first k-steps give the previous tile's sums,
+// loaded at its end, time to arrive: at n_f = 16 a delay of 4 of 16 k-steps
+// measured 1.001 ms against 1.008 with 2 and 1.012 with none; at n_f = 64
+// none or one of 64 is best, 2.627 ms against 2.655 with 16).
 template <int BK, bool U8, bool LEAN>
 __device__ __forceinline__ void kloop(const NLanes& L, const float* As, const float* Bs,
                                       unsigned long long (&acc)[8][2], const Prev& pv, bool on,
@@ -144,7 +146,7 @@ __device__ __forceinline__ void kloop(const NLanes& L, const float* As, const fl
     for (int p = 0; p < 2; ++p)
 #pragma unroll
       for (int r = 0; r < 8; ++r) acc[r][p] = mg::f2_add(acc[r][p], fminf(a[r], b[2 * p]), fminf(a[r], b[2 * p + 1]));
-    constexpr int K0 = BK / 4, KE = BK - K0;
+    constexpr int K0 = 64 / BK, KE = BK - K0;
     if (kk >= K0) {
 #pragma unroll
       for (int e = (kk - K0) * 32 / KE; e < (kk - K0 + 1) * 32 / KE; ++e) store_prev<U8, LEAN>(pv, e, on, out);
