@@ -111,6 +111,18 @@ __device__ __forceinline__ float metric(float n2, float d) {
   return LEAN ? div_rn_lean(n2, d) : __fdiv_rn(__fadd_rn(n2, n2), d);
 }
 
+// One-byte code of c2 (c2_code).  On the lean path its clamp at 255 never
+// acts: with v >= 0, n2 <= min(S_i, S_j) <= (S_i + S_j) / 2, and the FP32 n2 (a
+// sum of at most 64 mins) and the halved FP32 sums are within 64 and 3 units
+// of 2^-24 of their exact values, so c2 <= 1 + 2^-17 and 255 c2 < 255.5,
+// which rounds to the clamped code 255 anyway.  Dropping it saves an ALU-pipe
+// instruction per output.
+template <bool LEAN>
+__device__ __forceinline__ unsigned char code_of(float q) {
+  if (!LEAN) return c2_code(q);
+  return (unsigned char)(__float_as_uint(__fadd_rn(__fmul_rn(255.0f, q), 8388608.0f)) & 0xffu);
+}
+
 // Output e (row e / 4, column e % 4) of the previous tile.  Row i + k starts
 // k (nv - i - 2) - k (k - 1) / 2 positions after row i in the packed
 // triangle (pair (i, j) at P(i) - i - 1 + j).
@@ -122,18 +134,26 @@ __device__ __forceinline__ void store_prev(const Prev& pv, int e, bool on, void*
   const float q = metric<LEAN>(n2_of(pv.n2, r, c), __fadd_rn(pv.Sfi[r], pv.Sfj[c]));
   if (on) {
     if (U8)
-      static_cast<unsigned char*>(out)[o] = c2_code(q);
+      static_cast<unsigned char*>(out)[o] = code_of<LEAN>(q);
     else
       static_cast<float*>(out)[o] = q;
   }
 }
 
+__device__ __forceinline__ unsigned long long f2_pack(float x, float y) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(x), "f"(y));
+  return r;
+}
+
 // BK k-steps of the micro-kernel on a landed slice, with the previous tile's
-// 32 outputs spread over all but the first 64 / BK of them (stores
-// predicated on `on`; the first k-steps give the previous tile's sums,
-// loaded at its end, time to arrive: at n_f = 16 a delay of 4 of 16 k-steps
-// measured 1.001 ms against 1.008 with 2 and 1.012 with none; at n_f = 64
-// none or one of 64 is best, 2.627 ms against 2.655 with 16).
+// 32 outputs spread over all but the first K0 of them (stores predicated on
+// `on`; the first k-steps give the previous tile's sums, loaded at its end,
+// time to arrive: at 32768 vectors and n_f = 16 a delay of 4 of 16 k-steps
+// measured 0.900 ms against 0.907 with 2 and 0.921 with 6; at n_f = 64 no
+// delay 2.451 ms against 2.474 with 1).  The first k-step sets the sums
+// instead of adding to zeros (0 + m = m for the mins m >= 0), which saves
+// the zeroing and one packed add per pair of outputs.
 template <int BK, bool U8, bool LEAN>
 __device__ __forceinline__ void kloop(const NLanes& L, const float* As, const float* Bs,
                                       unsigned long long (&acc)[8][2], const Prev& pv, bool on,
@@ -145,8 +165,10 @@ __device__ __forceinline__ void kloop(const NLanes& L, const float* As, const fl
 #pragma unroll
     for (int p = 0; p < 2; ++p)
 #pragma unroll
-      for (int r = 0; r < 8; ++r) acc[r][p] = mg::f2_add(acc[r][p], fminf(a[r], b[2 * p]), fminf(a[r], b[2 * p + 1]));
-    constexpr int K0 = 64 / BK, KE = BK - K0;
+      for (int r = 0; r < 8; ++r)
+        acc[r][p] = kk == 0 ? f2_pack(fminf(a[r], b[2 * p]), fminf(a[r], b[2 * p + 1]))
+                            : mg::f2_add(acc[r][p], fminf(a[r], b[2 * p]), fminf(a[r], b[2 * p + 1]));
+    constexpr int K0 = BK >= 64 ? 0 : 64 / BK, KE = BK - K0;
     if (kk >= K0) {
 #pragma unroll
       for (int e = (kk - K0) * 32 / KE; e < (kk - K0 + 1) * 32 / KE; ++e) store_prev<U8, LEAN>(pv, e, on, out);
@@ -164,6 +186,7 @@ __device__ __forceinline__ void narrow_body(NarrowSmem<BK, STAGES>& sm, const CU
   const int lane = threadIdx.x & 31;
   const bool producer = threadIdx.x == 0;
   unsigned long long next_claim = 0;
+  const int64_t tiles_before = (int64_t)R0 * T - (int64_t)R0 * (R0 - 1) / 2;  // tiles in rows [0, R0)
   if (producer) next_claim = atomicAdd(tile_ctr, 1ull);
   // producer: loads the next tile (waiting until its ring stage is free);
   // false on abort
@@ -181,8 +204,15 @@ __device__ __forceinline__ void narrow_body(NarrowSmem<BK, STAGES>& sm, const CU
       sm.p_done = 1;
       return true;
     }
+    // tile walk: banded (band_tile) for 16- and 32-field slices; row-major
+    // for 64-field ones, whose tiles take four times longer (at 32768 vectors
+    // n_f = 16: 0.900 ms banded against 0.913 row-major, n_f = 64: 2.452
+    // against 2.406).  V fits in L2 at these widths either way.
     int I, J;
-    mg::band_tile((int64_t)t, T, R0, R1, G, I, J);
+    if (BK >= 64)
+      mg::tri_tile(tiles_before + (int64_t)t, T, I, J);
+    else
+      mg::band_tile((int64_t)t, T, R0, R1, G, I, J);
     sm.tile_of[s] = make_int2(I, J);
     sy::bar_arrive_tx(&sm.full[s], SLICE_BYTES);
     sy::tma_load_2d(&sm.A[s][0][0], mapV, I * BM, 0, &sm.full[s]);
@@ -213,8 +243,6 @@ __device__ __forceinline__ void narrow_body(NarrowSmem<BK, STAGES>& sm, const CU
     }
     const int2 ij = sm.tile_of[s];
     if (ij.x < 0) return false;  // no tile left
-#pragma unroll
-    for (int r = 0; r < 8; ++r) nx.n2[r][0] = nx.n2[r][1] = 0ull;
     kloop<BK, U8, LEAN>(L, &sm.A[s][0][0], &sm.B[s][0][0], nx.n2, pv, have, out);
     __syncwarp();
     if (lane == 0) sy::bar_arrive(&sm.empty[s]);
@@ -243,7 +271,7 @@ __device__ __forceinline__ void narrow_body(NarrowSmem<BK, STAGES>& sm, const CU
         if (j <= i || j >= nv) continue;
         const float q = metric<LEAN>(n2_of(nx.n2, r, c), __fadd_rn(Sfi, sum_in<LEAN>(Sf, j)));
         if (U8)
-          static_cast<unsigned char*>(out)[base + j] = c2_code(q);
+          static_cast<unsigned char*>(out)[base + j] = code_of<LEAN>(q);
         else
           static_cast<float*>(out)[base + j] = q;
       }
