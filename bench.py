@@ -49,6 +49,8 @@ WORKLOADS = {
     "2way_32768x16_f32": dict(way=2, nv=32768, nf=16, number=2),
     "2way_32768x64_f32": dict(way=2, nv=32768, nf=64, number=2),
     "2way_32768x385_f32": dict(way=2, nv=32768, nf=385, number=2),
+    # the single-GPU kernel timing of the paper's Table 1 (n_v = 10,240, n_f = 12,288)
+    "2way_10240x12288_f32": dict(way=2, nv=10240, nf=12288, number=2),
 }
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 
@@ -734,6 +736,33 @@ def main():
         secondary = {"3way_2048x4096_f32": {"value": c3 / (ms3 / 1e3), "unit": UNIT, "ms_per_step": ms3,
                                             "mgemm3_ms": k3, "frac_of_peak": c3 / (k3 / 1e3) / peak_cmp}}
         del o3, X3
+        torch.cuda.empty_cache()
+        # the shape of the paper's Table 1 kernel timing (10,240 vectors of
+        # 12,288 fields, FP32), one more point of the same min-product kernel
+        wt = WORKLOADS["2way_10240x12288_f32"]
+        Vt = synth.zero_inflated(wt["nv"], wt["nf"], synth.seed_for(2, 1050))
+        Xt = torch.from_numpy(Vt).cuda()
+        mt = ps.matrix(Xt)
+        ot = torch.empty(wt["nv"] * (wt["nv"] - 1) // 2, dtype=torch.float32, device="cuda")
+        for _ in range(2):
+            ps.check(ps.ps_metrics_2way(h.h, ctypes.byref(mt), ps.PS_PATH_FP32, 0, ot.data_ptr(), 0, sptr), h.h)
+        ps.check(ps.ps_timing_enable(h.h, 1), h.h)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(5):
+            ps.check(ps.ps_metrics_2way(h.h, ctypes.byref(mt), ps.PS_PATH_FP32, 0, ot.data_ptr(), 0, sptr), h.h)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        mst_ = e0.elapsed_time(e1) / 5
+        ps.check(ps.ps_timing_read(h.h, b"mgemm2", ctypes.byref(n_launch), ctypes.byref(k_ms)), h.h)
+        ps.check(ps.ps_timing_enable(h.h, 0), h.h)
+        kt = k_ms.value / max(n_launch.value, 1)
+        ct = comparisons(wt)
+        secondary["2way_10240x12288_f32"] = {
+            "value": ct / (mst_ / 1e3), "unit": UNIT, "ms_per_step": mst_, "mgemm2_ms": kt,
+            "frac_of_peak": ct / (kt / 1e3) / peak_cmp,
+            "note": "upper triangle (i < j), the paper's Table 1 shape; inputs larger than L2 (0.50 GB in)"}
+        del ot, Xt
         torch.cuda.empty_cache()
         # output-bound shapes: 32768 vectors with few fields, FP32 output
         # (2.15 GB per call) against the measured HBM copy bandwidth
