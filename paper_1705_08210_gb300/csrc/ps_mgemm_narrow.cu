@@ -248,8 +248,13 @@ __device__ __forceinline__ void narrow_body(NarrowSmem<BK, STAGES>& sm, const CU
     if (lane == 0) sy::bar_arrive(&sm.empty[s]);
     const int row0 = ij.x * BM, col0 = ij.y * BN;
     if (col0 >= row0 + BM && col0 + BN <= nv) {
+      // the lane's 8 rows are consecutive and start at a multiple of 8: two
+      // 16-byte loads (rows below col0 < nv, so in bounds)
+      const float4 s0 = __ldg(reinterpret_cast<const float4*>(Sf + row0 + L.ra));
+      const float4 s1 = __ldg(reinterpret_cast<const float4*>(Sf + row0 + L.ra + 4));
+      const float sr[8] = {s0.x, s0.y, s0.z, s0.w, s1.x, s1.y, s1.z, s1.w};
 #pragma unroll
-      for (int r = 0; r < 8; ++r) nx.Sfi[r] = sum_in<LEAN>(Sf, row0 + L.ra + L.kr(r));
+      for (int r = 0; r < 8; ++r) nx.Sfi[r] = LEAN ? __fmul_rn(0.5f, sr[L.kr(r)]) : sr[L.kr(r)];
 #pragma unroll
       for (int c = 0; c < 4; ++c) nx.Sfj[c] = sum_in<LEAN>(Sf, col0 + L.cb + L.cs(c));
       const int64_t i = row0 + L.ra;
